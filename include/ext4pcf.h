@@ -1,0 +1,152 @@
+/*
+ * ext4pcf.h -- C ABI of the GB300 (sm_103a) implementation of the quadratic-scaling
+ * multipole estimator of the shear four-point correlation function of Porth,
+ * Silvestre-Rosello, Schneider & Larma, arXiv:2509.07974 ("the paper").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Positions are flat-sky (x, y) in any angular unit; radial bin edges use the same unit.
+ *  - Shears are Cartesian (gamma_1, gamma_2), gamma_c = gamma_1 + i gamma_2 (paper Sect. 2.1).
+ *  - Complex values are interleaved (re, im) doubles.
+ *  - Multipole output ("upsilon") layout, row-major:
+ *        [n_cat][9][2N+1][2N+1][nb][nb][nb][2]
+ *    index 0..7 along the second axis are the natural components Upsilon_mu of the
+ *    x-projection (paper Eq. 4PCFUpsilon0 and the seven equations after it), index 8 is
+ *    the normalisation N_n (Eq. Nnmultipoles); the next two axes are n2+N and n3+N
+ *    (N = n_max); the three bin axes are Theta1, Theta2, Theta3.  Every ordered bin triple
+ *    is stored.
+ *  - Outputs are ACCUMULATED INTO: the caller zeroes them before the first call; results of
+ *    several calls (patches, checkpointed chunks of a catalogue) add up.
+ *  - Ownership: the caller owns every input and output buffer; the context owns its
+ *    scratch memory (grown on demand, released by ext4pcf_destroy).
+ *  - Pointers documented as "device or host" may point to either; host buffers are copied
+ *    to the device inside the call (and host outputs copied back), which makes the call
+ *    synchronous.  Device-only calls are stream-ordered on the configured stream and
+ *    return after enqueueing unless `stats` is requested (then they synchronise).
+ *  - Errors: every entry point returns EXT4PCF_OK (0) or a negative code; no exception
+ *    crosses the ABI.  ext4pcf_last_error() gives a message for the last failure.  A
+ *    context may be used by one host thread at a time.
+ */
+#ifndef EXT4PCF_H
+#define EXT4PCF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EXT4PCF_API __attribute__((visibility("default")))
+#else
+#define EXT4PCF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ext4pcf_ctx ext4pcf_ctx;
+
+enum {
+  EXT4PCF_OK = 0,
+  EXT4PCF_E_INVALID_ARG = -1, /* bad sizes, unsorted or non-positive bins, n_max < 0 ... */
+  EXT4PCF_E_OOM = -2,         /* device allocation failed */
+  EXT4PCF_E_CUDA = -3,        /* a CUDA runtime call failed */
+  EXT4PCF_E_TIMEOUT = -4,     /* a bounded device-side wait gave up (status word set) */
+  EXT4PCF_E_UNSUPPORTED = -5  /* no sm_103 device, or a size beyond a kernel's limits */
+};
+
+/* Arithmetic of ext4pcf_measure. */
+typedef enum {
+  EXT4PCF_FP64 = 0,      /* FP64 gather, FP64 contraction and corrections (CUDA cores) */
+  EXT4PCF_FP32 = 1,      /* FP32 gather and contraction, FP64 accumulation across waves */
+  EXT4PCF_TF32 = 2,      /* FP32 gather, tensor-core contraction (tcgen05 kind::tf32) */
+  EXT4PCF_3XTF32 = 3,    /* as TF32 with hi/lo split operands, three passes */
+  EXT4PCF_SPLIT_BF16 = 4 /* tensor-core contraction (kind::f16, bf16 hi/lo, three passes) */
+} ext4pcf_precision;
+
+typedef struct {
+  int device;              /* CUDA device ordinal */
+  void* stream;            /* cudaStream_t to enqueue on (NULL = legacy default stream) */
+  int precision;           /* ext4pcf_precision */
+  int autotune;            /* 1: pick wave / tile shapes by timing on first use */
+  int64_t workspace_bytes; /* soft cap on context scratch (0 = no cap) */
+  int64_t timeout_cycles;  /* bound on every device-side wait (0 = default) */
+  int deterministic;       /* 1: fixed summation order (always honoured at present) */
+  int wave_centres;        /* centres per contraction wave (0 = automatic) */
+} ext4pcf_config;
+
+typedef struct {
+  int64_t pairs;   /* (centre, neighbour) pairs with separation inside the radial bins */
+  int64_t centres; /* galaxies that acted as centres */
+  int64_t waves;   /* contraction waves launched */
+  double ms_grid, ms_gather, ms_contract, ms_correct, ms_total; /* CUDA-event times */
+} ext4pcf_stats;
+
+/* Create a context on cfg->device.  Fails with EXT4PCF_E_UNSUPPORTED unless the device is
+ * compute capability 10.3 (GB300).  *out receives the handle. */
+EXT4PCF_API int ext4pcf_create(ext4pcf_ctx** out, const ext4pcf_config* cfg);
+
+/* Release the context and all its scratch memory (synchronises its stream). */
+EXT4PCF_API int ext4pcf_destroy(ext4pcf_ctx* ctx);
+
+/* Multipoles of the shear 4PCF (paper Sect. 3.1 and App. A.1).
+ * For every centre galaxy i and radial bin Theta, the neighbour multipoles
+ *   G_n(theta_i, Theta) = sum_j w_j gamma_c,j e^{i n phi_ij}, W_n likewise with w_j
+ * (phi_ij the polar angle of theta_j - theta_i, bin membership Theta_lo^2 <= r^2 <
+ * Theta_hi^2) are accumulated, contracted into Upsilon_{mu,n}(Theta1,Theta2,Theta3) and
+ * N_n (Eq. 4PCFUpsilon0 ff., Eq. Nnmultipoles) and the double- and triple-counting terms
+ * of Table tab:4PCFMCCorr are removed, so that only quadruplets of distinct galaxy indices
+ * remain.
+ *   positions   device or host, double [n_gal][2]
+ *   shears      device or host, double [n_gal][2]
+ *   weights     device or host, double [n_gal]
+ *   n_gal       total galaxies over all catalogues (>= 0)
+ *   radial_bins host, double [n_bins+1], strictly increasing, radial_bins[0] > 0
+ *   n_bins      1..32;  n_max >= 0 (<= 40)
+ *   cat_offsets host, int64 [n_cat+1] or NULL: catalogue k is galaxies
+ *               [cat_offsets[k], cat_offsets[k+1]); NULL means one catalogue (n_cat = 1)
+ *   centre_mask device or host, uint8 [n_gal] or NULL: only galaxies with a non-zero entry
+ *               act as centres (all galaxies act as neighbours)
+ *   upsilon     device or host, double, layout above, accumulated into
+ *   xi_acc      device or host, double [n_cat][n_bins][3][2] or NULL: accumulates
+ *               (sum_i x_i^* G_0, sum_i x_i G_-4, sum_i w_i W_0) per bin, x_i = w_i gamma_c,i
+ *               (xi_+ and xi_- are the first two over the third)
+ *   stats       host or NULL */
+EXT4PCF_API int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                    const double* weights, int64_t n_gal, const double* radial_bins,
+                    int n_bins, int n_max, const int64_t* cat_offsets, int n_cat,
+                    const uint8_t* centre_mask, double* upsilon, double* xi_acc,
+                    ext4pcf_stats* stats);
+
+/* Multipoles -> real space (paper Eq. Multipole2RealConversion, FP64).  The angular
+ * density is integrated over n_phi uniform bins of [0, 2 pi) on each of phi_12, phi_13,
+ * giving per bin the quadruplet sums of Eq. QuadrupletUpsilon / Eq. TripletNorm; their
+ * ratio is the estimator of Eq. 4PCF_quadrupletestimator.
+ *   upsilon device, one catalogue, layout above
+ *   gamma   device, double [8][nb][nb][nb][n_phi][n_phi][2], accumulated: Upsilon / N
+ *           (0 where N == 0)
+ *   norm    device, double [nb][nb][nb][n_phi][n_phi], accumulated: N per bin */
+EXT4PCF_API int ext4pcf_to_real_space(ext4pcf_ctx* ctx, const double* upsilon, int n_bins, int n_max,
+                          int n_phi, double* gamma, double* norm);
+
+/* Fourth-order aperture measures for the filter of Eq. CrittendenQ (paper Sect. 5, FP64).
+ * The real-space 4PCF is formed on the fly (never stored) and integrated with the
+ * closed-form kernel of Eq. 4PCF2M4 (aperture centre integrated analytically) over the
+ * radial bins (area element (hi^2 - lo^2)/2 at the r-weighted mean radius) and n_phi
+ * angular bins.
+ *   upsilon     device, one catalogue
+ *   radial_bins host [n_bins+1];  ap_radii host [n_ap]
+ *   xi_pm       host [n_bins][4] (xi+ re, im, xi- re, im) or NULL
+ *   m4          host [n_ap][8][2]: the correlators of Eq. M4Ordering (accumulated)
+ *   map4_eb     host [n_ap][16]: E/B moments in the order of Eq. 4PCF_rawcomponents
+ *   map4_disc   host [n_ap][16] or NULL: Gaussian part from xi_pm (Wick pairs of
+ *               <M M> and <M M^*>) in the same order; connected = map4_eb - map4_disc */
+EXT4PCF_API int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radial_bins,
+                    int n_bins, int n_max, int n_phi, const double* ap_radii, int n_ap,
+                    const double* xi_pm, double* m4, double* map4_eb, double* map4_disc);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next call. */
+EXT4PCF_API const char* ext4pcf_last_error(const ext4pcf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EXT4PCF_H */

@@ -1,0 +1,500 @@
+// C ABI of libext4pcf: argument checking, scratch management and the per-catalogue
+// pipeline  grid build -> [gather -> contraction -> correction sums] per centre wave ->
+// correction application.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ext4pcf {
+cudaError_t scan_exclusive(unsigned* data, size_t n, unsigned* tmp, cudaStream_t s);
+cudaError_t real_space(const double* ups, int nb, int N, int nphi, double* gamma, double* norm,
+                       double* scratch_norm, double* E_scratch, cudaStream_t s);
+size_t real_space_smem(int N, int nphi);
+cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, int N, int nphi,
+                          const double* ap_host, int n_ap, double* E_scratch, double* norm_chunk,
+                          double* gam_chunk, int chunk_tri, double* partial, cudaStream_t s);
+cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const double* d_xipm,
+                               const double* d_tb, const double* d_area, int nb, const double* d_ap,
+                               double* d_m4, double* d_eb, double* d_disc, cudaStream_t s);
+}  // namespace ext4pcf
+
+using namespace ext4pcf;
+
+namespace {
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+__global__ void mask_flags(const uint8_t* __restrict__ mask, const int* __restrict__ perm, int n,
+                           unsigned* __restrict__ flag) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) flag[p] = mask ? (mask[perm[p]] != 0) : 1u;
+}
+__global__ void mask_compact(const unsigned* __restrict__ flag_scan, const uint8_t* __restrict__ mask,
+                             const int* __restrict__ perm, int n, int* __restrict__ centres,
+                             int* __restrict__ count) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && (!mask || mask[perm[p]] != 0)) centres[flag_scan[p]] = p;
+  if (p == n - 1) *count = (int)flag_scan[p] + ((!mask || mask[perm[p]] != 0) ? 1 : 0);
+}
+__global__ void iota(int* a, int n) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) a[p] = p;
+}
+
+}  // namespace
+
+struct ext4pcf_ctx {
+  ext4pcf_config cfg{};
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  std::string err;
+  // inputs staged from host memory
+  DBuf in_pos, in_shear, in_w, in_mask, io_ups, io_xi;
+  // grid
+  DBuf keys, keys_alt, perm, perm_alt, cell_start, hist, px, py, xr, xi, w, p4, s4, bbox;
+  // waves
+  DBuf centres, flags, rec, xw, corr, counter, ncen;
+  // transforms
+  DBuf t_norm, t_gam, t_E, t_part, t_small;
+  cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+int fail(ext4pcf_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(ext4pcf_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? EXT4PCF_E_OOM : EXT4PCF_E_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+int ensure(ext4pcf_ctx* ctx, DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return EXT4PCF_OK;
+  if (b.p) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return fail(ctx, EXT4PCF_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    want = bytes;
+  }
+  b.bytes = want;
+  return EXT4PCF_OK;
+}
+
+#define ENSURE(buf, bytes)                           \
+  do {                                               \
+    int r_ = ensure(ctx, (buf), (bytes));            \
+    if (r_ != EXT4PCF_OK) return r_;                 \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// cell side: about a eighth of the largest separation, at most ~4000 cells per axis, and
+// with 12 significant bits so that (cell index) * cell is exact in float
+double choose_cell(double rmax, double extent) {
+  double c = rmax / 8.0;
+  if (extent / 4000.0 > c) c = extent / 4000.0;
+  int ex;
+  double m = std::frexp(c, &ex);          // c = m 2^ex, m in [0.5, 1)
+  m = std::floor(m * 4096.0) / 4096.0;    // 12 significant bits
+  return std::ldexp(m, ex);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ext4pcf_create(ext4pcf_ctx** out, const ext4pcf_config* cfg) {
+  if (!out || !cfg) return EXT4PCF_E_INVALID_ARG;
+  *out = nullptr;
+  if (std::getenv("EXT4PCF_FAULT") && std::strcmp(std::getenv("EXT4PCF_FAULT"), "alloc") == 0)
+    return EXT4PCF_E_OOM;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return EXT4PCF_E_UNSUPPORTED;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, cfg->device) != cudaSuccess) return EXT4PCF_E_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return EXT4PCF_E_UNSUPPORTED;
+  if (cfg->precision < EXT4PCF_FP64 || cfg->precision > EXT4PCF_SPLIT_BF16) return EXT4PCF_E_INVALID_ARG;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return EXT4PCF_E_CUDA;
+  ext4pcf_ctx* ctx = new ext4pcf_ctx;
+  ctx->cfg = *cfg;
+  ctx->stream = static_cast<cudaStream_t>(cfg->stream);
+  ctx->sm_count = prop.multiProcessorCount;
+  for (auto& e : ctx->ev) cudaEventCreate(&e);
+  *out = ctx;
+  return EXT4PCF_OK;
+}
+
+int ext4pcf_destroy(ext4pcf_ctx* ctx) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  cudaSetDevice(ctx->cfg.device);
+  cudaStreamSynchronize(ctx->stream);
+  DBuf* all[] = {&ctx->in_pos, &ctx->in_shear, &ctx->in_w, &ctx->in_mask, &ctx->io_ups, &ctx->io_xi,
+                 &ctx->keys, &ctx->keys_alt, &ctx->perm, &ctx->perm_alt, &ctx->cell_start, &ctx->hist,
+                 &ctx->px, &ctx->py, &ctx->xr, &ctx->xi, &ctx->w, &ctx->p4, &ctx->s4, &ctx->bbox,
+                 &ctx->centres, &ctx->flags, &ctx->rec, &ctx->xw, &ctx->corr, &ctx->counter, &ctx->ncen,
+                 &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small};
+  for (DBuf* b : all)
+    if (b->p) cudaFree(b->p);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+  return EXT4PCF_OK;
+}
+
+const char* ext4pcf_last_error(const ext4pcf_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                    const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
+                    int n_max, const int64_t* cat_offsets, int n_cat, const uint8_t* centre_mask,
+                    double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  ctx->err.clear();
+  if (std::getenv("EXT4PCF_FAULT") && std::strcmp(std::getenv("EXT4PCF_FAULT"), "arg") == 0)
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "fault injection: argument check");
+  if (n_gal < 0 || n_gal > (int64_t)2000000000) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_gal out of range");
+  if (n_bins < 1 || n_bins > 32) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_bins must be in 1..32");
+  if (n_max < 0 || n_max > 40) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_max must be in 0..40");
+  if (!radial_bins || !upsilon) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null radial_bins or upsilon");
+  if (n_gal > 0 && (!positions || !shears || !weights)) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null input");
+  if (!(radial_bins[0] > 0.0) || !std::isfinite(radial_bins[n_bins]))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "radial_bins[0] must be > 0 and finite");
+  for (int b = 0; b < n_bins; ++b)
+    if (!(radial_bins[b + 1] > radial_bins[b])) return fail(ctx, EXT4PCF_E_INVALID_ARG, "radial_bins must increase");
+  if (cat_offsets) {
+    if (n_cat < 1) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_cat < 1");
+    if (cat_offsets[0] != 0 || cat_offsets[n_cat] != n_gal)
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "cat_offsets must span [0, n_gal]");
+    for (int k = 0; k < n_cat; ++k)
+      if (cat_offsets[k + 1] < cat_offsets[k]) return fail(ctx, EXT4PCF_E_INVALID_ARG, "cat_offsets decrease");
+  } else {
+    n_cat = 1;
+  }
+  const int prec = ctx->cfg.precision;
+  if (prec >= EXT4PCF_TF32 && !tc_supported(Layout::make(n_max, n_bins), prec))
+    return fail(ctx, EXT4PCF_E_UNSUPPORTED, "tensor-core contraction does not support this size");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = ctx->stream;
+  const bool f64 = prec == EXT4PCF_FP64;
+  const Layout L = Layout::make(n_max, n_bins);
+  const size_t ups_elems = (size_t)9 * (2 * n_max + 1) * (2 * n_max + 1) * n_bins * n_bins * n_bins;
+  const size_t ups_bytes = ups_elems * 16;
+
+  // ---- stage host inputs / outputs
+  const size_t n = (size_t)n_gal;
+  const double* d_pos = positions;
+  const double* d_sh = shears;
+  const double* d_w = weights;
+  const uint8_t* d_mask = centre_mask;
+  double* d_ups = upsilon;
+  double* d_xi = xi_acc;
+  const bool host_ups = !is_device_ptr(upsilon);
+  const bool host_xi = xi_acc && !is_device_ptr(xi_acc);
+  if (n > 0 && !is_device_ptr(positions)) {
+    ENSURE(ctx->in_pos, n * 16);
+    CK(cudaMemcpyAsync(ctx->in_pos.p, positions, n * 16, cudaMemcpyHostToDevice, s));
+    d_pos = (const double*)ctx->in_pos.p;
+  }
+  if (n > 0 && !is_device_ptr(shears)) {
+    ENSURE(ctx->in_shear, n * 16);
+    CK(cudaMemcpyAsync(ctx->in_shear.p, shears, n * 16, cudaMemcpyHostToDevice, s));
+    d_sh = (const double*)ctx->in_shear.p;
+  }
+  if (n > 0 && !is_device_ptr(weights)) {
+    ENSURE(ctx->in_w, n * 8);
+    CK(cudaMemcpyAsync(ctx->in_w.p, weights, n * 8, cudaMemcpyHostToDevice, s));
+    d_w = (const double*)ctx->in_w.p;
+  }
+  if (n > 0 && centre_mask && !is_device_ptr(centre_mask)) {
+    ENSURE(ctx->in_mask, n);
+    CK(cudaMemcpyAsync(ctx->in_mask.p, centre_mask, n, cudaMemcpyHostToDevice, s));
+    d_mask = (const uint8_t*)ctx->in_mask.p;
+  }
+  if (host_ups) {
+    ENSURE(ctx->io_ups, ups_bytes * n_cat);
+    CK(cudaMemcpyAsync(ctx->io_ups.p, upsilon, ups_bytes * n_cat, cudaMemcpyHostToDevice, s));
+    d_ups = (double*)ctx->io_ups.p;
+  }
+  const size_t xi_bytes = (size_t)n_bins * 6 * 8;
+  if (host_xi) {
+    ENSURE(ctx->io_xi, xi_bytes * n_cat);
+    CK(cudaMemcpyAsync(ctx->io_xi.p, xi_acc, xi_bytes * n_cat, cudaMemcpyHostToDevice, s));
+    d_xi = (double*)ctx->io_xi.p;
+  }
+
+  Bins bins;
+  bins.nb = n_bins;
+  for (int b = 0; b <= n_bins; ++b) {
+    bins.e2[b] = radial_bins[b] * radial_bins[b];
+    bins.e2f[b] = (float)bins.e2[b];
+  }
+  bins.rmax = radial_bins[n_bins];
+
+  const bool timing = stats != nullptr;
+  float ms_grid = 0, ms_gather = 0, ms_contract = 0, ms_correct = 0, ms_total = 0;
+  int64_t tot_centres = 0, tot_waves = 0;
+  if (timing) CK(cudaEventRecord(ctx->ev[0], s));
+  ENSURE(ctx->counter, 16);
+  CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
+  ENSURE(ctx->ncen, 16);
+  ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
+
+  for (int k = 0; k < n_cat; ++k) {
+    const int64_t c0 = cat_offsets ? cat_offsets[k] : 0;
+    const int nk = (int)((cat_offsets ? cat_offsets[k + 1] : n_gal) - c0);
+    double* ups_k = d_ups + 2 * ups_elems * (size_t)k;
+    double* xi_k = d_xi ? d_xi + (size_t)n_bins * 6 * k : nullptr;
+    if (nk == 0) continue;
+    const double* pos_k = d_pos + 2 * c0;
+    const double* sh_k = d_sh + 2 * c0;
+    const double* w_k = d_w + c0;
+    const uint8_t* mask_k = d_mask ? d_mask + c0 : nullptr;
+    if (timing) CK(cudaEventRecord(ctx->ev[1], s));
+    // ---- grid
+    CK(grid_bbox(pos_k, nk, (double*)ctx->bbox.p, s));
+    double bb[4];
+    CK(cudaMemcpyAsync(bb, ctx->bbox.p, 32, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!std::isfinite(bb[0]) || !std::isfinite(bb[1]) || !std::isfinite(bb[2]) || !std::isfinite(bb[3]))
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "non-finite positions");
+    const double extent = std::fmax(bb[2] - bb[0], bb[3] - bb[1]);
+    const double cell = choose_cell(bins.rmax, extent);
+    const int ncx = (int)std::floor((bb[2] - bb[0]) / cell) + 1;
+    const int ncy = (int)std::floor((bb[3] - bb[1]) / cell) + 1;
+    const size_t ncells = (size_t)ncx * ncy;
+    const int ntiles = (nk + 2047) / 2048;
+    ENSURE(ctx->keys, (size_t)nk * 4); ENSURE(ctx->keys_alt, (size_t)nk * 4);
+    ENSURE(ctx->perm, (size_t)nk * 4); ENSURE(ctx->perm_alt, (size_t)nk * 4);
+    ENSURE(ctx->cell_start, (ncells + 1) * 4);
+    ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
+    ENSURE(ctx->px, (size_t)nk * 8); ENSURE(ctx->py, (size_t)nk * 8);
+    ENSURE(ctx->xr, (size_t)nk * 8); ENSURE(ctx->xi, (size_t)nk * 8); ENSURE(ctx->w, (size_t)nk * 8);
+    if (!f64) { ENSURE(ctx->p4, (size_t)nk * 16); ENSURE(ctx->s4, (size_t)nk * 16); }
+    GridBuffers gb;
+    gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+    gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+    gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ncells + 1;
+    gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+    gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
+    gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
+    gb.p4 = (float4*)ctx->p4.p; gb.s4 = (float4*)ctx->s4.p; gb.bbox = (double*)ctx->bbox.p;
+    SortedCat cat;
+    CK(grid_sort(pos_k, sh_k, w_k, nk, bb[0], bb[1], cell, ncx, ncy, !f64, gb, cat, s));
+    // ---- centre list (sorted positions of the centres)
+    ENSURE(ctx->centres, (size_t)nk * 4);
+    int n_cen = nk;
+    if (mask_k) {
+      ENSURE(ctx->flags, ((size_t)nk + (size_t)nk / 1000 + 4096) * 4);
+      unsigned* flag = (unsigned*)ctx->flags.p;
+      mask_flags<<<(nk + 255) / 256, 256, 0, s>>>(mask_k, cat.perm, nk, flag);
+      unsigned* tmp = (unsigned*)ctx->hist.p;  // reuse as scan scratch
+      CK(scan_exclusive(flag, (size_t)nk, tmp, s));
+      mask_compact<<<(nk + 255) / 256, 256, 0, s>>>(flag, mask_k, cat.perm, nk, (int*)ctx->centres.p,
+                                                   (int*)ctx->ncen.p);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&n_cen, ctx->ncen.p, 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    } else {
+      iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
+      CK(cudaGetLastError());
+    }
+    tot_centres += n_cen;
+    if (timing) CK(cudaEventRecord(ctx->ev[2], s));
+    // ---- waves
+    const size_t cbytes = f64 ? sizeof(double2) : sizeof(float2);
+    int T = ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres : (f64 ? 4096 : 8192);
+    if (T > n_cen) T = n_cen;
+    if (T < 1) T = 1;
+    ENSURE(ctx->rec, (size_t)T * L.rec * cbytes);
+    ENSURE(ctx->xw, (size_t)T * 2 * cbytes);
+    const size_t corr_doubles = corrections_size(L);
+    ENSURE(ctx->corr, corr_doubles * 8);
+    CK(cudaMemsetAsync(ctx->corr.p, 0, corr_doubles * 8, s));
+    for (int w0 = 0; w0 < n_cen; w0 += T) {
+      const int Tw = std::min(T, n_cen - w0);
+      const int* cl = (const int*)ctx->centres.p + w0;
+      if (timing) CK(cudaEventRecord(ctx->ev[3], s));
+      if (f64) {
+        CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      } else {
+        CK(gather_wave<float>(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+                              (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      }
+      if (timing) CK(cudaEventRecord(ctx->ev[4], s));
+      if (f64) {
+        CK(contract_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, ups_k, s));
+      } else if (prec == EXT4PCF_FP32) {
+        CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, s));
+      } else {
+        return fail(ctx, EXT4PCF_E_UNSUPPORTED, "tensor-core contraction not available");
+      }
+      if (timing) CK(cudaEventRecord(ctx->ev[5], s));
+      if (f64) {
+        CK(corrections_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw,
+                                    (double*)ctx->corr.p, xi_k, s));
+      } else {
+        CK(corrections_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw,
+                                   (double*)ctx->corr.p, xi_k, s));
+      }
+      if (timing) {
+        CK(cudaEventRecord(ctx->ev[6], s));
+        CK(cudaEventSynchronize(ctx->ev[6]));
+        float a = 0, b = 0, c = 0;
+        cudaEventElapsedTime(&a, ctx->ev[3], ctx->ev[4]);
+        cudaEventElapsedTime(&b, ctx->ev[4], ctx->ev[5]);
+        cudaEventElapsedTime(&c, ctx->ev[5], ctx->ev[6]);
+        ms_gather += a; ms_contract += b; ms_correct += c;
+      }
+      ++tot_waves;
+    }
+    CK(corrections_apply(L, (const double*)ctx->corr.p, ups_k, s));
+    if (timing) {
+      CK(cudaEventRecord(ctx->ev[7], s));
+      CK(cudaEventSynchronize(ctx->ev[7]));
+      float g = 0;
+      cudaEventElapsedTime(&g, ctx->ev[1], ctx->ev[2]);
+      ms_grid += g;
+    }
+  }
+  if (host_ups) CK(cudaMemcpyAsync(upsilon, d_ups, ups_bytes * n_cat, cudaMemcpyDeviceToHost, s));
+  if (host_xi) CK(cudaMemcpyAsync(xi_acc, d_xi, xi_bytes * n_cat, cudaMemcpyDeviceToHost, s));
+  if (host_ups || host_xi) CK(cudaStreamSynchronize(s));
+  if (timing) {
+    unsigned long long pairs = 0;
+    CK(cudaMemcpyAsync(&pairs, ctx->counter.p, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev[7], s));
+    CK(cudaEventSynchronize(ctx->ev[7]));
+    cudaEventElapsedTime(&ms_total, ctx->ev[0], ctx->ev[7]);
+    stats->pairs = (int64_t)pairs;
+    stats->centres = tot_centres;
+    stats->waves = tot_waves;
+    stats->ms_grid = ms_grid;
+    stats->ms_gather = ms_gather;
+    stats->ms_contract = ms_contract;
+    stats->ms_correct = ms_correct;
+    stats->ms_total = ms_total;
+  }
+  CK(cudaGetLastError());
+  return EXT4PCF_OK;
+}
+
+int ext4pcf_to_real_space(ext4pcf_ctx* ctx, const double* upsilon, int n_bins, int n_max, int n_phi,
+                          double* gamma, double* norm) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  ctx->err.clear();
+  if (!upsilon || !gamma || !norm) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null pointer");
+  if (n_bins < 1 || n_bins > 32 || n_max < 0 || n_max > 40 || n_phi < 1 || n_phi > 1024)
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "sizes out of range");
+  if (!is_device_ptr(upsilon) || !is_device_ptr(gamma) || !is_device_ptr(norm))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "to_real_space takes device pointers");
+  if (real_space_smem(n_max, n_phi) > 227 * 1024) return fail(ctx, EXT4PCF_E_UNSUPPORTED, "n_max * n_phi too large");
+  CK(cudaSetDevice(ctx->cfg.device));
+  const size_t ntri = (size_t)n_bins * n_bins * n_bins;
+  ENSURE(ctx->t_norm, ntri * n_phi * n_phi * 8);
+  ENSURE(ctx->t_E, (size_t)(2 * n_max + 1) * n_phi * 16);
+  CK(real_space(upsilon, n_bins, n_max, n_phi, gamma, norm, (double*)ctx->t_norm.p, (double*)ctx->t_E.p,
+                ctx->stream));
+  return EXT4PCF_OK;
+}
+
+int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radial_bins, int n_bins,
+                    int n_max, int n_phi, const double* ap_radii, int n_ap, const double* xi_pm, double* m4,
+                    double* map4_eb, double* map4_disc) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  ctx->err.clear();
+  if (!upsilon || !radial_bins || !ap_radii || !m4 || !map4_eb)
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "null pointer");
+  if (n_bins < 1 || n_bins > 32 || n_max < 0 || n_max > 40 || n_phi < 1 || n_phi > 1024 || n_ap < 1 || n_ap > 64)
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "sizes out of range");
+  for (int b = 0; b < n_bins; ++b)
+    if (!(radial_bins[b + 1] > radial_bins[b]) || !(radial_bins[0] > 0))
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "radial_bins must increase from > 0");
+  if (!is_device_ptr(upsilon)) return fail(ctx, EXT4PCF_E_INVALID_ARG, "upsilon must be a device pointer");
+  if (real_space_smem(n_max, n_phi) > 227 * 1024) return fail(ctx, EXT4PCF_E_UNSUPPORTED, "n_max * n_phi too large");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = ctx->stream;
+  const int ntri = n_bins * n_bins * n_bins;
+  const size_t nph2 = (size_t)n_phi * n_phi;
+  int chunk = (int)std::max<size_t>(1, (size_t)(256u << 20) / (nph2 * 8 * 16));
+  if (chunk > ntri) chunk = ntri;
+  ENSURE(ctx->t_norm, (size_t)chunk * nph2 * 8);
+  ENSURE(ctx->t_gam, (size_t)chunk * nph2 * 8 * 16);
+  ENSURE(ctx->t_E, (size_t)(2 * n_max + 1) * n_phi * 16);
+  ENSURE(ctx->t_part, (size_t)ntri * n_ap * 8 * 16);
+  // small buffer: xi_pm [nb*4], tb [nb], area [nb], ap [n_ap], m4 [n_ap*16], eb [n_ap*16], disc [n_ap*16]
+  const size_t small = (size_t)n_bins * 6 + n_ap * 49;
+  ENSURE(ctx->t_small, small * 8);
+  std::vector<double> hs(small, 0.0);
+  double* h_xi = hs.data();
+  double* h_tb = h_xi + 4 * n_bins;
+  double* h_area = h_tb + n_bins;
+  double* h_ap = h_area + n_bins;
+  for (int b = 0; b < n_bins; ++b) {
+    const double lo = radial_bins[b], hi = radial_bins[b + 1];
+    h_tb[b] = (2.0 / 3.0) * (hi * hi * hi - lo * lo * lo) / (hi * hi - lo * lo);
+    h_area[b] = 0.5 * (hi * hi - lo * lo);
+    if (xi_pm) for (int k = 0; k < 4; ++k) h_xi[4 * b + k] = xi_pm[4 * b + k];
+  }
+  for (int k = 0; k < n_ap; ++k) h_ap[k] = ap_radii[k];
+  double* d_small = (double*)ctx->t_small.p;
+  CK(cudaMemcpyAsync(d_small, hs.data(), small * 8, cudaMemcpyHostToDevice, s));
+  CK(map4_partials(upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n_ap, (double*)ctx->t_E.p,
+                   (double*)ctx->t_norm.p, (double*)ctx->t_gam.p, chunk, (double*)ctx->t_part.p, s));
+  double* d_m4 = d_small + 6 * n_bins + n_ap;
+  double* d_eb = d_m4 + 16 * n_ap;
+  double* d_disc = d_eb + 16 * n_ap;
+  CK(map4_finish_launch((const double*)ctx->t_part.p, ntri, n_ap, xi_pm ? d_small : nullptr, d_small + 4 * n_bins,
+                        d_small + 5 * n_bins, n_bins, d_small + 6 * n_bins, d_m4, d_eb, d_disc, s));
+  std::vector<double> res((size_t)48 * n_ap);
+  CK(cudaMemcpyAsync(res.data(), d_m4, res.size() * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < 16 * n_ap; ++k) {
+    m4[k] += res[k];
+    map4_eb[k] += res[16 * n_ap + k];
+    if (map4_disc && xi_pm) map4_disc[k] += res[32 * n_ap + k];
+  }
+  return EXT4PCF_OK;
+}
+
+}  // extern "C"

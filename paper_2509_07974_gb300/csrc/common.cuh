@@ -1,0 +1,137 @@
+// Internal declarations shared by the CUDA translation units of libext4pcf.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "ext4pcf.h"
+
+namespace ext4pcf {
+
+// ---------------------------------------------------------------------------------------
+// Complex helpers on float2 / double2 (re, im).
+// ---------------------------------------------------------------------------------------
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+template <typename R> using cplx_t = typename C2<R>::T;
+
+template <typename V> __host__ __device__ __forceinline__ V cmk(decltype(V::x) a, decltype(V::x) b) {
+  V v; v.x = a; v.y = b; return v;
+}
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+
+// ---------------------------------------------------------------------------------------
+// Sizes of the per-centre multipole record (one centre, all radial bins).  Index ranges:
+//   G  : n in [-2N-3, 2N-1]   sum_j x_j u^n            (x = w gamma_c, u = e^{i phi_ij})
+//   W  : m in [0, 2N]         sum_j w_j u^m            (W_{-m} = conj W_m)
+//   XX : n in [-2N-6, 2N-2]   sum_j x_j^2 u^n
+//   XA : m in [0, 2N+2]       sum_j |x_j|^2 u^m        (conjugate-symmetric)
+//   WW : m in [0, 2N]         sum_j w_j^2 u^m          (conjugate-symmetric)
+//   TR : 5 values             x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3
+// Each array is [n][nb] (bin fastest); the record is G|W|XX|XA|WW|TR.
+// ---------------------------------------------------------------------------------------
+struct Layout {
+  int N, nb;
+  int nG, nW, nXX, nXA;
+  int oG, oW, oXX, oXA, oWW, oTR;  // complex-element offsets within a record
+  int rec;                         // complex elements per centre record
+  int max_pow;                     // largest |power| of u needed
+  __host__ __device__ static Layout make(int N, int nb) {
+    Layout L;
+    L.N = N; L.nb = nb;
+    L.nG = 4 * N + 3; L.nW = 2 * N + 1; L.nXX = 4 * N + 5; L.nXA = 2 * N + 3;
+    L.oG = 0;
+    L.oW = L.oG + L.nG * nb;
+    L.oXX = L.oW + L.nW * nb;
+    L.oXA = L.oXX + L.nXX * nb;
+    L.oWW = L.oXA + L.nXA * nb;
+    L.oTR = L.oWW + L.nW * nb;
+    L.rec = L.oTR + 5 * nb;
+    L.max_pow = 2 * N + 6;
+    return L;
+  }
+  // element index of G_n(b), W_m(b) ... inside a record
+  __host__ __device__ int G(int n, int b) const { return oG + (n + 2 * N + 3) * nb + b; }
+  __host__ __device__ int W(int m, int b) const { return oW + m * nb + b; }
+  __host__ __device__ int XX(int n, int b) const { return oXX + (n + 2 * N + 6) * nb + b; }
+  __host__ __device__ int XA(int m, int b) const { return oXA + m * nb + b; }
+  __host__ __device__ int WW(int m, int b) const { return oWW + m * nb + b; }
+  __host__ __device__ int TR(int k, int b) const { return oTR + k * nb + b; }
+};
+
+// ---------------------------------------------------------------------------------------
+// A catalogue sorted by cell (built by the grid kernels).
+// ---------------------------------------------------------------------------------------
+struct SortedCat {
+  int n;            // galaxies
+  int ncx, ncy;     // cells per axis
+  double x0, y0;    // grid origin (double)
+  double cell;      // cell side (few significant bits, so cx*cell is exact in float)
+  float cellf;
+  const int* cell_start;  // [ncx*ncy + 1]
+  const int* perm;        // sorted position -> original index (within the catalogue)
+  const double* px;       // sorted positions (double)
+  const double* py;
+  const double* xr;       // sorted x = w gamma_c (double), w
+  const double* xi;
+  const double* w;
+  const float4* p4;       // (cx*cell, cy*cell, x - cx*cell, y - cy*cell) as float
+  const float4* s4;       // (x_re, x_im, w, 0) as float
+};
+
+struct Bins {
+  int nb;
+  double e2[65];   // squared edges (double)
+  float e2f[65];   // squared edges (float)
+  double rmax;
+};
+
+// ---------------------------------------------------------------------------------------
+// Kernel launchers (implemented in the .cu files).
+// ---------------------------------------------------------------------------------------
+struct GridScratch;  // opaque, in grid.cu
+
+// grid.cu: sort one catalogue (device arrays of n galaxies) into cells.  Writes the sorted
+// arrays into caller-provided buffers and fills `out`.  Returns a cudaError_t.
+struct GridBuffers {
+  int* keys; int* keys_alt; int* perm; int* perm_alt; int* cell_start; size_t cell_cap;
+  unsigned* hist; size_t hist_cap;
+  double* px; double* py; double* xr; double* xi; double* w;
+  float4* p4; float4* s4;
+  double* bbox;  // [4] device
+};
+cudaError_t grid_bbox(const double* pos, int n, double* d_bbox, cudaStream_t s);
+cudaError_t grid_sort(const double* pos, const double* shear, const double* wts, int n,
+                      double x0, double y0, double cell, int ncx, int ncy, bool want_f32,
+                      GridBuffers& gb, SortedCat& out, cudaStream_t s);
+
+// gather.cu: per-centre multipole records for centres[c0 .. c0+T) (sorted positions).
+template <typename R>
+cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
+                        const int* centres, int T, cplx_t<R>* rec, cplx_t<R>* xw,
+                        unsigned long long* pair_count, int sm_count, cudaStream_t s);
+
+// contract.cu
+template <typename R>
+cudaError_t contract_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
+                          double* ups, cudaStream_t s);
+template <typename R>
+cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
+                             double* corr, double* xi_acc, cudaStream_t s);
+cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, cudaStream_t s);
+size_t corrections_size(const Layout& L);  // doubles
+
+// contract_tc.cu (tensor cores)
+bool tc_supported(const Layout& L, int precision);
+cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T,
+                             double* ups, int precision, void* scratch, size_t scratch_bytes,
+                             int* status, long long timeout, cudaStream_t s);
+size_t contract_tc_scratch(const Layout& L, int T);
+
+}  // namespace ext4pcf

@@ -1,0 +1,338 @@
+// Contraction of a wave of per-centre multipole records into the 4PCF multipoles
+//   Upsilon_{mu,n}(Theta1,Theta2,Theta3) += sum_i xt_i A_i(Theta1) B_i(Theta2) C_i(Theta3)
+// (paper Eq. 4PCFUpsilon0 and the seven equations after it; Eq. Nnmultipoles), and of the
+// multiple-counting terms of Table tab:4PCFMCCorr (App. A.1).  CUDA-core version, templated
+// on the arithmetic type: FP64 throughout, or FP32 within a wave with the wave totals added
+// into the FP64 output.
+#include "common.cuh"
+
+namespace ext4pcf {
+
+namespace {
+
+// Which per-centre array a factor reads and how its index follows from (s, n2, n3).
+enum Arr { kG = 0, kW = 1, kXX = 2, kXA = 3, kWW = 4 };
+struct Factor {
+  signed char arr, sgn, off, conj;
+};
+struct Comp {
+  signed char xconj;  // 0: x_i, 1: x_i^*, 2: w_i
+  Factor A, B, C;     // A(Theta1; s), B(Theta2; n2), C(Theta3; n3)
+};
+
+// Upsilon_0..7 (x-projection) and N: xt * A[s] * B[n2] * C[n3].
+__constant__ Comp kComp[9] = {
+    {0, {kG, 1, -3, 0}, {kG, -1, -2, 0}, {kG, -1, -3, 0}},
+    {1, {kG, 1, -1, 0}, {kG, -1, -2, 0}, {kG, -1, -1, 0}},
+    {0, {kG, -1, -1, 1}, {kG, -1, -2, 0}, {kG, -1, -3, 0}},
+    {0, {kG, 1, -3, 0}, {kG, 1, -2, 1}, {kG, -1, -3, 0}},
+    {0, {kG, 1, -3, 0}, {kG, -1, -2, 0}, {kG, 1, -1, 1}},
+    {1, {kG, -1, -3, 1}, {kG, -1, -2, 0}, {kG, -1, -1, 0}},
+    {1, {kG, 1, -1, 0}, {kG, 1, -2, 1}, {kG, -1, -1, 0}},
+    {1, {kG, 1, -1, 0}, {kG, -1, -2, 0}, {kG, 1, -3, 1}},
+    {2, {kW, 1, 0, 0}, {kW, -1, 0, 0}, {kW, -1, 0, 0}},
+};
+
+// Double-counting terms: xt * P(merged slots; bin Theta_a) * O(remaining slot; Theta_b).
+// kind 0: Theta1 = Theta2 (index n3), kind 1: Theta1 = Theta3 (index n2),
+// kind 2: Theta2 = Theta3 (index s).
+struct Corr {
+  Factor P, O;
+};
+__constant__ Corr kCorr[3][9] = {
+    {// Theta1 = Theta2: P[n3], O = C(Theta3)[n3]
+     {{kXX, 1, -5, 0}, {kG, -1, -3, 0}},
+     {{kXX, 1, -3, 0}, {kG, -1, -1, 0}},
+     {{kXA, 1, -1, 0}, {kG, -1, -3, 0}},
+     {{kXA, 1, -1, 0}, {kG, -1, -3, 0}},
+     {{kXX, 1, -5, 0}, {kG, 1, -1, 1}},
+     {{kXA, 1, 1, 0}, {kG, -1, -1, 0}},
+     {{kXA, 1, 1, 0}, {kG, -1, -1, 0}},
+     {{kXX, 1, -3, 0}, {kG, 1, -3, 1}},
+     {{kWW, 1, 0, 0}, {kW, -1, 0, 0}}},
+    {// Theta1 = Theta3: P[n2], O = B(Theta2)[n2]
+     {{kXX, 1, -6, 0}, {kG, -1, -2, 0}},
+     {{kXX, 1, -2, 0}, {kG, -1, -2, 0}},
+     {{kXA, 1, -2, 0}, {kG, -1, -2, 0}},
+     {{kXX, 1, -6, 0}, {kG, 1, -2, 1}},
+     {{kXA, 1, -2, 0}, {kG, -1, -2, 0}},
+     {{kXA, 1, 2, 0}, {kG, -1, -2, 0}},
+     {{kXX, 1, -2, 0}, {kG, 1, -2, 1}},
+     {{kXA, 1, 2, 0}, {kG, -1, -2, 0}},
+     {{kWW, 1, 0, 0}, {kW, -1, 0, 0}}},
+    {// Theta2 = Theta3: P[s], O = A(Theta1)[s]
+     {{kXX, -1, -5, 0}, {kG, 1, -3, 0}},
+     {{kXX, -1, -3, 0}, {kG, 1, -1, 0}},
+     {{kXX, -1, -5, 0}, {kG, -1, -1, 1}},
+     {{kXA, -1, -1, 0}, {kG, 1, -3, 0}},
+     {{kXA, -1, -1, 0}, {kG, 1, -3, 0}},
+     {{kXX, -1, -3, 0}, {kG, -1, -3, 1}},
+     {{kXA, -1, 1, 0}, {kG, 1, -1, 0}},
+     {{kXA, -1, 1, 0}, {kG, 1, -1, 0}},
+     {{kWW, -1, 0, 0}, {kW, 1, 0, 0}}}};
+// Triple term: TR index per component (x^3 u^-8, x^3 u^-4, x^2x^* u^-4, x^2x^*, w^3)
+__constant__ signed char kTriple[9] = {0, 1, 2, 2, 2, 3, 3, 3, 4};
+
+template <typename Cx>
+__device__ __forceinline__ Cx fetch(const Cx* __restrict__ rec, const Layout& L, Factor f, int var,
+                                    int b) {
+  const int n = f.sgn * var + f.off;
+  Cx v;
+  bool cj = f.conj != 0;
+  switch (f.arr) {
+    case kG: v = rec[L.G(n, b)]; break;
+    case kXX: v = rec[L.XX(n, b)]; break;
+    case kW: v = rec[L.W(n >= 0 ? n : -n, b)]; cj ^= (n < 0); break;
+    case kXA: v = rec[L.XA(n >= 0 ? n : -n, b)]; cj ^= (n < 0); break;
+    default: v = rec[L.WW(n >= 0 ? n : -n, b)]; cj ^= (n < 0); break;
+  }
+  return cj ? cconj(v) : v;
+}
+
+template <typename Cx>
+__device__ __forceinline__ Cx centre_factor(const Cx* __restrict__ xw, int c, int xconj) {
+  Cx x = xw[2 * (size_t)c];
+  if (xconj == 1) return cconj(x);
+  if (xconj == 2) return xw[2 * (size_t)c + 1];
+  return x;
+}
+
+constexpr int kChunk = 32;
+
+// threads of a contraction block: one per (Theta2, Theta3), rounded up to whole warps
+constexpr int contract_threads(int nbt) {
+  return (nbt * nbt + 31) / 32 * 32 < 128 ? 128 : (nbt * nbt + 31) / 32 * 32;
+}
+
+// Block (mu, n2, n3); thread (b2, b3); registers hold Theta1 = 0..NBT-1.
+template <typename R, int NBT>
+__global__ void __launch_bounds__(contract_threads(NBT))
+contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx_t<R>* __restrict__ xw,
+                   int T, double* __restrict__ ups) {
+  using Cx = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cx* sx = reinterpret_cast<Cx*>(smem_raw);
+  Cx* sA = sx + kChunk;
+  Cx* sB = sA + kChunk * NBT;
+  Cx* sC = sB + kChunk * NBT;
+  const int N = L.N, nb = L.nb, nn = 2 * N + 1;
+  const int mu = blockIdx.x / (nn * nn);
+  const int n2 = (blockIdx.x / nn) % nn - N, n3 = blockIdx.x % nn - N, s = n2 + n3;
+  const Comp cp = kComp[mu];
+  const int tid = threadIdx.x;
+  const int b2 = tid / nb, b3 = tid % nb;
+  const bool active = tid < nb * nb;
+  Cx acc[NBT];
+#pragma unroll
+  for (int k = 0; k < NBT; ++k) acc[k] = cmk<Cx>(R(0), R(0));
+  for (int c0 = 0; c0 < T; c0 += kChunk) {
+    const int nc = min(kChunk, T - c0);
+    for (int k = tid; k < nc * (3 * nb + 1); k += blockDim.x) {
+      const int cc = k / (3 * nb + 1), r = k % (3 * nb + 1);
+      const Cx* rc = rec + (size_t)(c0 + cc) * L.rec;
+      if (r == 0) sx[cc] = centre_factor(xw, c0 + cc, cp.xconj);
+      else if (r <= nb) sA[cc * NBT + r - 1] = fetch(rc, L, cp.A, s, r - 1);
+      else if (r <= 2 * nb) sB[cc * NBT + r - 1 - nb] = fetch(rc, L, cp.B, n2, r - 1 - nb);
+      else sC[cc * NBT + r - 1 - 2 * nb] = fetch(rc, L, cp.C, n3, r - 1 - 2 * nb);
+    }
+    __syncthreads();
+    if (active) {
+      for (int cc = 0; cc < nc; ++cc) {
+        const Cx kr = cmul(cmul(sx[cc], sB[cc * NBT + b2]), sC[cc * NBT + b3]);
+#pragma unroll
+        for (int k = 0; k < NBT; ++k) {
+          if (k < nb) {
+            const Cx a = sA[cc * NBT + k];
+            acc[k].x += a.x * kr.x - a.y * kr.y;
+            acc[k].y += a.x * kr.y + a.y * kr.x;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (active) {
+    const size_t nb3 = (size_t)nb * nb * nb;
+    const size_t base = (((size_t)mu * nn + (n2 + N)) * nn + (n3 + N)) * nb3 + (size_t)b2 * nb + b3;
+#pragma unroll
+    for (int k = 0; k < NBT; ++k) {
+      if (k < nb) {
+        double* o = ups + 2 * (base + (size_t)k * nb * nb);
+        o[0] += (double)acc[k].x;
+        o[1] += (double)acc[k].y;
+      }
+    }
+  }
+}
+
+// Correction sums over the wave: block (mu, kind, index); thread (ba, bb).
+template <typename R>
+__global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
+                                   const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ corr) {
+  using Cx = cplx_t<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = L.N, nb = L.nb, nn = 2 * N + 1, ns = 4 * N + 1;
+  const int per_mu = 2 * nn + ns;  // index rows of the three double-counting kinds
+  const int mu = blockIdx.x / (per_mu + 1);
+  const int row = blockIdx.x % (per_mu + 1);
+  Cx* sx = reinterpret_cast<Cx*>(smem_raw);
+  Cx* sP = sx + kChunk;
+  Cx* sO = sP + kChunk * nb;
+  const int tid = threadIdx.x;
+  const Comp cp = kComp[mu];
+  const size_t nb2 = (size_t)nb * nb;
+  const size_t mu_base = (size_t)mu * ((size_t)per_mu * nb2 + nb);
+  if (row < per_mu) {
+    int kind, var;
+    if (row < nn) { kind = 0; var = row - N; }
+    else if (row < 2 * nn) { kind = 1; var = row - nn - N; }
+    else { kind = 2; var = row - 2 * nn - 2 * N; }
+    const Corr cr = kCorr[kind][mu];
+    const int ba = tid / nb, bb = tid % nb;
+    const bool active = tid < nb * nb;
+    Cx acc = cmk<Cx>(R(0), R(0));
+    for (int c0 = 0; c0 < T; c0 += kChunk) {
+      const int nc = min(kChunk, T - c0);
+      for (int k = tid; k < nc * (2 * nb + 1); k += blockDim.x) {
+        const int cc = k / (2 * nb + 1), r = k % (2 * nb + 1);
+        const Cx* rc = rec + (size_t)(c0 + cc) * L.rec;
+        if (r == 0) sx[cc] = centre_factor(xw, c0 + cc, cp.xconj);
+        else if (r <= nb) sP[cc * nb + r - 1] = fetch(rc, L, cr.P, var, r - 1);
+        else sO[cc * nb + r - 1 - nb] = fetch(rc, L, cr.O, var, r - 1 - nb);
+      }
+      __syncthreads();
+      if (active)
+        for (int cc = 0; cc < nc; ++cc) acc = cadd(acc, cmul(cmul(sx[cc], sP[cc * nb + ba]), sO[cc * nb + bb]));
+      __syncthreads();
+    }
+    if (active) {
+      double* o = corr + 2 * (mu_base + (size_t)row * nb2 + (size_t)ba * nb + bb);
+      o[0] += (double)acc.x;
+      o[1] += (double)acc.y;
+    }
+  } else {
+    // triple term, thread = bin
+    const int b = tid;
+    Cx acc = cmk<Cx>(R(0), R(0));
+    if (b < nb) {
+      const int k = kTriple[mu];
+      for (int c = 0; c < T; ++c) {
+        const Cx* rc = rec + (size_t)c * L.rec;
+        acc = cadd(acc, cmul(centre_factor(xw, c, cp.xconj), rc[L.TR(k, b)]));
+      }
+      double* o = corr + 2 * (mu_base + (size_t)per_mu * nb2 + b);
+      o[0] += (double)acc.x;
+      o[1] += (double)acc.y;
+    }
+  }
+}
+
+// xi accumulators per bin: (sum conj(x) G_0, sum x G_-4, sum w W_0), FP64, fixed order.
+template <typename R>
+__global__ void xi_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
+                          const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ xi) {
+  __shared__ double red[6][256];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = tid; c < T; c += blockDim.x) {
+    const cplx_t<R>* rc = rec + (size_t)c * L.rec;
+    const double xr = xw[2 * (size_t)c].x, xim = xw[2 * (size_t)c].y, w = xw[2 * (size_t)c + 1].x;
+    const double g0r = rc[L.G(0, b)].x, g0i = rc[L.G(0, b)].y;
+    const double g4r = rc[L.G(-4, b)].x, g4i = rc[L.G(-4, b)].y;
+    const double w0r = rc[L.W(0, b)].x, w0i = rc[L.W(0, b)].y;
+    v[0] += xr * g0r + xim * g0i; v[1] += xr * g0i - xim * g0r;
+    v[2] += xr * g4r - xim * g4i; v[3] += xr * g4i + xim * g4r;
+    v[4] += w * w0r; v[5] += w * w0i;
+  }
+  for (int k = 0; k < 6; ++k) red[k][tid] = v[k];
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st)
+      for (int k = 0; k < 6; ++k) red[k][tid] += red[k][tid + st];
+    __syncthreads();
+  }
+  if (tid < 6) xi[6 * b + tid] += red[tid][0];
+}
+
+__global__ void apply_corrections(const Layout L, const double* __restrict__ corr, double* __restrict__ ups) {
+  const int N = L.N, nb = L.nb, nn = 2 * N + 1, ns = 4 * N + 1, per_mu = 2 * nn + ns;
+  const size_t nb2 = (size_t)nb * nb, nb3 = nb2 * nb;
+  const size_t total = (size_t)9 * nn * nn * nb3;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b3 = (int)(e % nb), b2 = (int)((e / nb) % nb), b1 = (int)((e / nb2) % nb);
+    if (b1 != b2 && b1 != b3 && b2 != b3) continue;
+    const size_t r = e / nb3;
+    const int n3 = (int)(r % nn) - N, n2 = (int)((r / nn) % nn) - N, mu = (int)(r / ((size_t)nn * nn));
+    const int s = n2 + n3;
+    const double* cm = corr + 2 * ((size_t)mu * ((size_t)per_mu * nb2 + nb));
+    double vr = 0, vi = 0;
+    if (b1 == b2) { const double* t = cm + 2 * ((size_t)(n3 + N) * nb2 + (size_t)b1 * nb + b3); vr += t[0]; vi += t[1]; }
+    if (b1 == b3) { const double* t = cm + 2 * ((size_t)(nn + n2 + N) * nb2 + (size_t)b1 * nb + b2); vr += t[0]; vi += t[1]; }
+    if (b2 == b3) { const double* t = cm + 2 * ((size_t)(2 * nn + s + 2 * N) * nb2 + (size_t)b2 * nb + b1); vr += t[0]; vi += t[1]; }
+    if (b1 == b2 && b1 == b3) { const double* t = cm + 2 * ((size_t)per_mu * nb2 + b1); vr -= 2.0 * t[0]; vi -= 2.0 * t[1]; }
+    ups[2 * e] -= vr;
+    ups[2 * e + 1] -= vi;
+  }
+}
+
+template <typename R, int NBT>
+cudaError_t launch_contract(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
+                            double* ups, cudaStream_t s) {
+  const int nn = 2 * L.N + 1;
+  const int threads = contract_threads(NBT);
+  const size_t smem = (size_t)kChunk * (1 + 3 * NBT) * sizeof(cplx_t<R>);
+  cudaError_t e = cudaFuncSetAttribute(contract_cuda_core<R, NBT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  contract_cuda_core<R, NBT><<<9 * nn * nn, threads, smem, s>>>(L, rec, xw, T, ups);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t contract_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
+                          double* ups, cudaStream_t s) {
+  if (T <= 0) return cudaSuccess;
+  if (L.nb <= 4) return launch_contract<R, 4>(L, rec, xw, T, ups, s);
+  if (L.nb <= 8) return launch_contract<R, 8>(L, rec, xw, T, ups, s);
+  if (L.nb <= 12) return launch_contract<R, 12>(L, rec, xw, T, ups, s);
+  if (L.nb <= 16) return launch_contract<R, 16>(L, rec, xw, T, ups, s);
+  if (L.nb <= 24) return launch_contract<R, 24>(L, rec, xw, T, ups, s);
+  if (L.nb <= 32) return launch_contract<R, 32>(L, rec, xw, T, ups, s);
+  return cudaErrorInvalidValue;
+}
+
+size_t corrections_size(const Layout& L) {
+  const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
+  return (size_t)2 * 9 * ((size_t)(2 * nn + ns) * L.nb * L.nb + L.nb);
+}
+
+template <typename R>
+cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
+                             double* corr, double* xi_acc, cudaStream_t s) {
+  if (T <= 0) return cudaSuccess;
+  const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
+  const int blocks = 9 * (2 * nn + ns + 1);
+  const int threads = max(64, (L.nb * L.nb + 31) / 32 * 32);
+  const size_t smem = (size_t)kChunk * (1 + 2 * L.nb) * sizeof(cplx_t<R>);
+  corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, T, corr);
+  if (xi_acc) xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, T, xi_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, cudaStream_t s) {
+  const int nn = 2 * L.N + 1;
+  const size_t total = (size_t)9 * nn * nn * L.nb * L.nb * L.nb;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 65536) blocks = 65536;
+  apply_corrections<<<blocks, 256, 0, s>>>(L, corr, ups);
+  return cudaGetLastError();
+}
+
+template cudaError_t contract_wave<float>(const Layout&, const float2*, const float2*, int, double*, cudaStream_t);
+template cudaError_t contract_wave<double>(const Layout&, const double2*, const double2*, int, double*, cudaStream_t);
+template cudaError_t corrections_wave<float>(const Layout&, const float2*, const float2*, int, double*, double*, cudaStream_t);
+template cudaError_t corrections_wave<double>(const Layout&, const double2*, const double2*, int, double*, double*, cudaStream_t);
+
+}  // namespace ext4pcf

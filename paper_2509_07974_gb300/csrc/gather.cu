@@ -1,0 +1,455 @@
+// Neighbour gather: for each centre galaxy i of a wave, the spin-weighted multipoles
+//   G_n(theta_i, Theta) = sum_j x_j e^{i n phi_ij},   x_j = w_j gamma_c,j
+// of its neighbours in every radial bin, plus W_n and the quantities that the
+// multiple-counting corrections need (paper Eq. 4PCFUpsilon0 ff., Table tab:4PCFMCCorr).
+//
+// One CTA (8 warps) per centre:
+//   (a) the rows of cells that can hold partners are contiguous ranges of the cell-sorted
+//       catalogue; the CTA streams them, keeps pairs with Theta_lo^2 <= r^2 < Theta_hi^2,
+//       and buckets them by radial bin into a shared-memory chunk (stable order, so the
+//       summation order is deterministic).  Chunks hold up to `cap` pairs; long neighbour
+//       lists take several chunks.
+//   (b) warp k owns the powers m in [k*MB, k*MB+MB) of u = e^{i phi_ij}: each lane takes
+//       pairs of a bin, raises u to the block's first power (u^MB is stored per pair) and
+//       walks the block by recurrence in registers, accumulating the seven quantities
+//       x u^m, x u^-m, x^2 u^m, x^2 u^-m, w u^m, |x|^2 u^m, w^2 u^m.  At the end of a bin
+//       the 32 lanes' partial sums are combined by a transposed butterfly (each lane ends
+//       with V/32 totals) and added to the centre's record in shared memory.
+//   (c) the record is written to the wave buffer.
+// FP64 variant: positions and arithmetic in double; the bin decision r^2 = dx*dx + dy*dy is
+// evaluated with two rounded products and one rounded sum, as the FP64 definition reads.
+// FP32 variant: positions are cell-anchored floats (cell offset exact, in-cell offset
+// rounded), so dx is accurate to ~1e-7 of the cell size; pairs whose r^2 lies within a few
+// rounding errors of a bin edge are re-decided from the double positions.
+#include "common.cuh"
+
+namespace ext4pcf {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRows = 64;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+template <typename R, int MB> struct GCfg {
+  static constexpr int kRaw = 14 * MB + 10;
+  static constexpr int V = (kRaw + 31) / 32 * 32;
+};
+
+template <typename R>
+__device__ __forceinline__ void cpow(R br, R bi, int e, R& pr, R& pi) {
+  pr = R(1); pi = R(0);
+  while (e) {
+    if (e & 1) { R t = pr * br - pi * bi; pi = pr * bi + pi * br; pr = t; }
+    R t = br * br - bi * bi; bi = R(2) * br * bi; br = t;
+    e >>= 1;
+  }
+}
+
+// transposed butterfly: after the call lane l holds in a[0..V/32) the warp totals of the
+// original slots j + base(l), base(l) = sum_k bit_k(l) * V / 2^(5-k)
+template <typename R, int V, int OFF>
+__device__ __forceinline__ void rt_step(R* a, int lane) {
+  constexpr int H = V / 2;
+  const bool up = (lane & OFF) != 0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    R send = up ? a[j] : a[j + H];
+    R keep = up ? a[j + H] : a[j];
+    a[j] = keep + __shfl_xor_sync(kFull, send, OFF);
+  }
+}
+template <typename R, int V>
+__device__ __forceinline__ void reduce_transpose(R* a, int lane) {
+  rt_step<R, V, 16>(a, lane);
+  rt_step<R, V / 2, 8>(a, lane);
+  rt_step<R, V / 4, 4>(a, lane);
+  rt_step<R, V / 8, 2>(a, lane);
+  rt_step<R, V / 16, 1>(a, lane);
+}
+
+__device__ __forceinline__ int bin_search(const double* e2, int nb, double r2) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (r2 >= e2[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int bin_search_f(const float* e2, int nb, float r2) {
+  int lo = 0, hi = nb;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (r2 >= e2[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Exact FP64 decision, identical to the definition: two rounded products, one rounded sum.
+__device__ __forceinline__ int classify_f64(double dx, double dy, const double* e2, int nb) {
+  double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  if (!(r2 >= e2[0]) || !(r2 < e2[nb])) return -1;
+  return bin_search(e2, nb, r2);
+}
+
+struct CentreF64 { double x, y; };
+
+// Returns the bin of candidate q (or -1) and u = e^{i phi}.
+template <typename R> struct Pair;
+
+template <> struct Pair<double> {
+  __device__ static int classify(const SortedCat& cat, int q, double cx, double cy, const float4&,
+                                 const double* e2, const float*, const float*, int nb,
+                                 double& ur, double& ui) {
+    double dx = cat.px[q] - cx, dy = cat.py[q] - cy;
+    int b = classify_f64(dx, dy, e2, nb);
+    if (b >= 0) {
+      double rinv = 1.0 / sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+      ur = dx * rinv; ui = dy * rinv;
+    }
+    return b;
+  }
+  __device__ static void load_x(const SortedCat& cat, int q, double& xr, double& xi, double& w) {
+    xr = cat.xr[q]; xi = cat.xi[q]; w = cat.w[q];
+  }
+};
+
+template <> struct Pair<float> {
+  __device__ static int classify(const SortedCat& cat, int q, double cx, double cy, const float4& P,
+                                 const double* e2, const float* e2f, const float* win, int nb,
+                                 float& ur, float& ui) {
+    float4 Q = cat.p4[q];
+    float dx = (Q.x - P.x) + (Q.z - P.z);
+    float dy = (Q.y - P.y) + (Q.w - P.w);
+    float r2 = dx * dx + dy * dy;
+    int b;
+    // the float decision stands unless r2 is within the edge's rounding window
+    if (r2 < e2f[0] - win[0] || r2 >= e2f[nb] + win[nb]) return -1;
+    b = (r2 >= e2f[0]) ? ((r2 >= e2f[nb]) ? nb : bin_search_f(e2f, nb, r2)) : -1;
+    bool near = false;
+    if (b < 0) near = true;  // within win[0] of the inner edge
+    else if (b == nb) near = true;
+    else near = (r2 - e2f[b] < win[b]) || (e2f[b + 1] - r2 <= win[b + 1]);
+    if (near) b = classify_f64(cat.px[q] - cx, cat.py[q] - cy, e2, nb);
+    if (b >= 0) {
+      float rinv = rsqrtf(r2);
+      ur = dx * rinv; ui = dy * rinv;
+    }
+    return b;
+  }
+  __device__ static void load_x(const SortedCat& cat, int q, float& xr, float& xi, float& w) {
+    float4 s = cat.s4[q];
+    xr = s.x; xi = s.y; w = s.z;
+  }
+};
+
+struct GatherArgs {
+  SortedCat cat;
+  Bins bins;
+  float win[65];
+  Layout L;
+  const int* centres;
+  int T;
+  int cap;
+  int mb;    // powers per warp block (<= MB)
+  int nblk;  // power blocks
+  unsigned long long* pair_count;
+};
+
+template <typename R, int MB>
+__global__ void __launch_bounds__(kThreads, 1)
+gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __restrict__ xw) {
+  using Cx = cplx_t<R>;
+  constexpr int V = GCfg<R, MB>::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SortedCat& cat = args.cat;
+  const Layout L = args.L;
+  const int nb = args.bins.nb, cap = args.cap, mb = args.mb;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+
+  Cx* acc = reinterpret_cast<Cx*>(smem);
+  R* eur = reinterpret_cast<R*>(acc + L.rec);
+  R* eui = eur + cap;
+  R* evr = eui + cap;
+  R* evi = evr + cap;
+  R* exr = evi + cap;
+  R* exi = exr + cap;
+  R* ew = exi + cap;
+  double* e2 = reinterpret_cast<double*>(ew + cap);
+  float* e2f = reinterpret_cast<float*>(e2 + 65);
+  float* win = e2f + 65;
+  int* cnt = reinterpret_cast<int*>(win + 65);
+  int* off = cnt + 64;
+  int* run = off + 65;
+  int* wcnt = run + 64;
+  int* rstart = wcnt + kWarps * 64;
+  int* rpre = rstart + kMaxRows;
+  int* misc = rpre + kMaxRows + 1;
+
+  for (int b = tid; b <= nb; b += kThreads) {
+    e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b]; win[b] = args.win[b];
+  }
+  for (int k = tid; k < kWarps * 64; k += kThreads) wcnt[k] = 0;
+  __syncthreads();
+  const double rmax = args.bins.rmax * (1.0 + 1e-9) + 1e-12;
+  const double cell = cat.cell;
+
+  for (int c = blockIdx.x; c < args.T; c += gridDim.x) {
+    const int pi = args.centres[c];
+    const double pxi = cat.px[pi], pyi = cat.py[pi];
+    float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sizeof(R) == 4) Pi = cat.p4[pi];
+    if (tid == 0) {
+      const double xc = pxi - cat.x0, yc = pyi - cat.y0;
+      int cy0 = (int)floor((yc - rmax) / cell), cy1 = (int)floor((yc + rmax) / cell);
+      cy0 = max(cy0, 0); cy1 = min(cy1, cat.ncy - 1);
+      int nr = 0, tot = 0;
+      for (int cy = cy0; cy <= cy1 && nr < kMaxRows; ++cy) {
+        const double lo = cy * cell, hi = lo + cell;
+        const double gap = fmax(0.0, fmax(lo - yc, yc - hi));
+        if (gap > rmax) continue;
+        const double hw = sqrt(fmax(0.0, rmax * rmax - gap * gap));
+        int cx0 = (int)floor((xc - hw) / cell), cx1 = (int)floor((xc + hw) / cell);
+        cx0 = max(cx0, 0); cx1 = min(cx1, cat.ncx - 1);
+        if (cx0 > cx1) continue;
+        const int a = cat.cell_start[cy * cat.ncx + cx0];
+        const int b = cat.cell_start[cy * cat.ncx + cx1 + 1];
+        if (b <= a) continue;
+        rstart[nr] = a; rpre[nr] = tot; tot += b - a; ++nr;
+      }
+      rpre[nr] = tot;
+      misc[0] = nr; misc[1] = tot;
+    }
+    for (int k = tid; k < L.rec; k += kThreads) acc[k] = cmk<Cx>(R(0), R(0));
+    __syncthreads();
+    const int nr = misc[0], total = misc[1];
+    unsigned long long pairs_here = 0;
+
+    auto candidate = [&](int t) -> int {  // flattened candidate index -> sorted position
+      int lo = 0, hi = nr;
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (t >= rpre[mid]) lo = mid; else hi = mid;
+      }
+      return rstart[lo] + (t - rpre[lo]);
+    };
+
+    for (int cpos = 0; cpos < total;) {
+      // ---- pass 1: how many candidates fit the chunk, and per-bin counts
+      for (int b = tid; b < nb; b += kThreads) cnt[b] = 0;
+      __syncthreads();
+      int cend = cpos, chunk_pairs = 0;
+      while (cend < total && chunk_pairs + kThreads <= cap) {
+        const int t = cend + tid;
+        int b = -1;
+        if (t < total) {
+          R ur, ui;
+          b = Pair<R>::classify(cat, candidate(t), pxi, pyi, Pi, e2, e2f, win, nb, ur, ui);
+        }
+        const unsigned m = __ballot_sync(kFull, b >= 0);
+        if (b >= 0) {
+          const unsigned peers = __match_any_sync(m, b);
+          if ((peers & lt) == 0) atomicAdd(&cnt[b], __popc(peers));
+        }
+        __syncthreads();
+        int s = 0;
+        for (int k = 0; k < nb; ++k) s += cnt[k];
+        chunk_pairs = s;
+        cend = min(cend + kThreads, total);
+        __syncthreads();
+      }
+      if (tid == 0) {
+        int s = 0;
+        for (int b = 0; b < nb; ++b) { off[b] = s; s += cnt[b]; run[b] = 0; }
+        off[nb] = s;
+      }
+      __syncthreads();
+      // ---- pass 2: stable bucketing of the chunk's pairs by bin
+      for (int bs = cpos; bs < cend; bs += kThreads) {
+        const int t = bs + tid;
+        int b = -1;
+        R ur = 0, ui = 0, xr = 0, xi = 0, ww = 0;
+        if (t < cend) {
+          const int q = candidate(t);
+          b = Pair<R>::classify(cat, q, pxi, pyi, Pi, e2, e2f, win, nb, ur, ui);
+          if (b >= 0) Pair<R>::load_x(cat, q, xr, xi, ww);
+        }
+        const unsigned m = __ballot_sync(kFull, b >= 0);
+        unsigned rank = 0;
+        if (b >= 0) {
+          const unsigned peers = __match_any_sync(m, b);
+          rank = __popc(peers & lt);
+          if ((peers & lt) == 0) wcnt[warp * 64 + b] = __popc(peers);
+        }
+        __syncthreads();
+        if (b >= 0) {
+          int pre = 0;
+          for (int w2 = 0; w2 < warp; ++w2) pre += wcnt[w2 * 64 + b];
+          const int dst = off[b] + run[b] + pre + (int)rank;
+          R vr, vi;
+          cpow<R>(ur, ui, mb, vr, vi);
+          eur[dst] = ur; eui[dst] = ui; evr[dst] = vr; evi[dst] = vi;
+          exr[dst] = xr; exi[dst] = xi; ew[dst] = ww;
+        }
+        __syncthreads();
+        if (tid < nb) {
+          int s = 0;
+          for (int w2 = 0; w2 < kWarps; ++w2) { s += wcnt[w2 * 64 + tid]; wcnt[w2 * 64 + tid] = 0; }
+          run[tid] += s;
+        }
+        __syncthreads();
+      }
+      // ---- pass 3: accumulate the power blocks
+      for (int k = warp; k < args.nblk; k += kWarps) {
+        const int m0 = k * mb;
+        for (int b = 0; b < nb; ++b) {
+          const int s0 = off[b], s1 = off[b + 1];
+          if (s0 == s1) continue;
+          R a[V];
+#pragma unroll
+          for (int j = 0; j < V; ++j) a[j] = R(0);
+          for (int e = s0 + lane; e < s1; e += 32) {
+            const R ur = eur[e], ui = eui[e], xr = exr[e], xi = exi[e], ww = ew[e];
+            R pr, pim;
+            cpow<R>(evr[e], evi[e], k, pr, pim);
+            const R x2r = xr * xr - xi * xi, x2i = R(2) * xr * xi;
+            const R xa = xr * xr + xi * xi, w2 = ww * ww;
+#pragma unroll
+            for (int t = 0; t < MB; ++t) {
+              if (t < mb) {
+                a[14 * t + 0] += xr * pr - xi * pim;
+                a[14 * t + 1] += xr * pim + xi * pr;
+                a[14 * t + 2] += xr * pr + xi * pim;
+                a[14 * t + 3] += xi * pr - xr * pim;
+                a[14 * t + 4] += x2r * pr - x2i * pim;
+                a[14 * t + 5] += x2r * pim + x2i * pr;
+                a[14 * t + 6] += x2r * pr + x2i * pim;
+                a[14 * t + 7] += x2i * pr - x2r * pim;
+                a[14 * t + 8] += ww * pr;
+                a[14 * t + 9] += ww * pim;
+                a[14 * t + 10] += xa * pr;
+                a[14 * t + 11] += xa * pim;
+                a[14 * t + 12] += w2 * pr;
+                a[14 * t + 13] += w2 * pim;
+                const R nr2 = pr * ur - pim * ui;
+                pim = pr * ui + pim * ur;
+                pr = nr2;
+              }
+            }
+            if (m0 == 0) {
+              // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3
+              R u2r = ur * ur - ui * ui, u2i = R(2) * ur * ui;
+              R u4r = u2r * u2r - u2i * u2i, u4i = R(2) * u2r * u2i;
+              R u8r = u4r * u4r - u4i * u4i, u8i = R(2) * u4r * u4i;
+              R x3r = x2r * xr - x2i * xi, x3i = x2r * xi + x2i * xr;
+              R xcr = xa * xr, xci = xa * xi;  // x^2 x^* = |x|^2 x
+              constexpr int o = 14 * MB;
+              a[o + 0] += x3r * u8r + x3i * u8i;  // x3 * conj(u8)
+              a[o + 1] += x3i * u8r - x3r * u8i;
+              a[o + 2] += x3r * u4r + x3i * u4i;
+              a[o + 3] += x3i * u4r - x3r * u4i;
+              a[o + 4] += xcr * u4r + xci * u4i;
+              a[o + 5] += xci * u4r - xcr * u4i;
+              a[o + 6] += xcr;
+              a[o + 7] += xci;
+              a[o + 8] += w2 * ww;
+            }
+          }
+          reduce_transpose<R, V>(a, lane);
+          const int base = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
+                           (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
+          R* accr = reinterpret_cast<R*>(acc);
+#pragma unroll
+          for (int j = 0; j < V / 32; ++j) {
+            const int slot = base + j;
+            int idx = -1, comp = slot & 1;
+            if (slot < 14 * MB) {
+              const int t = slot / 14, q = slot % 14, m = m0 + t;
+              if (t < mb) {
+                switch (q >> 1) {
+                  case 0: if (m <= 2 * L.N - 1) idx = L.G(m, b); break;
+                  case 1: if (m >= 1 && m <= 2 * L.N + 3) idx = L.G(-m, b); break;
+                  case 2: if (m <= 2 * L.N - 2) idx = L.XX(m, b); break;
+                  case 3: if (m >= 1 && m <= 2 * L.N + 6) idx = L.XX(-m, b); break;
+                  case 4: if (m <= 2 * L.N) idx = L.W(m, b); break;
+                  case 5: if (m <= 2 * L.N + 2) idx = L.XA(m, b); break;
+                  default: if (m <= 2 * L.N) idx = L.WW(m, b); break;
+                }
+              }
+            } else if (slot < 14 * MB + 10 && m0 == 0) {
+              idx = L.TR((slot - 14 * MB) >> 1, b);
+            }
+            if (idx >= 0) accr[2 * idx + comp] += a[j];
+          }
+        }
+      }
+      __syncthreads();
+      pairs_here += (unsigned long long)off[nb];
+      cpos = cend;
+      __syncthreads();
+    }
+    // ---- (c) write the record
+    Cx* dst = rec + (size_t)c * L.rec;
+    for (int k = tid; k < L.rec; k += kThreads) dst[k] = acc[k];
+    if (tid == 0) {
+      R xr, xi, ww;
+      Pair<R>::load_x(cat, pi, xr, xi, ww);
+      xw[2 * (size_t)c] = cmk<Cx>(xr, xi);
+      xw[2 * (size_t)c + 1] = cmk<Cx>(ww, R(0));
+      atomicAdd(args.pair_count, pairs_here);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R> constexpr int kMB = sizeof(R) == 4 ? 6 : 3;
+
+}  // namespace
+
+template <typename R>
+cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
+                        const int* centres, int T, cplx_t<R>* rec, cplx_t<R>* xw,
+                        unsigned long long* pair_count, int sm_count, cudaStream_t s) {
+  if (T <= 0) return cudaSuccess;
+  constexpr int MB = kMB<R>;
+  GatherArgs a;
+  a.cat = cat; a.bins = bins; a.L = L; a.centres = centres; a.T = T; a.pair_count = pair_count;
+  // rounding window of the float bin decision: |dx| carries ~2 ulp of max(cell, r)
+  for (int b = 0; b <= bins.nb; ++b) {
+    const double e = sqrt(bins.e2[b]);
+    const double err = 4.0 * 1.2e-7 * (cat.cell + e);
+    a.win[b] = (float)(2.0 * e * err + err * err);
+  }
+  const int npow = L.max_pow + 1;
+  int nblk = (npow + MB - 1) / MB;
+  nblk = (nblk + kWarps - 1) / kWarps * kWarps;
+  a.mb = (npow + nblk - 1) / nblk;
+  a.nblk = (npow + a.mb - 1) / a.mb;
+  const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
+                       (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64;
+  const size_t budget = 227 * 1024;
+  if (fixed + 7 * sizeof(R) * kThreads > budget) return cudaErrorInvalidConfiguration;
+  int cap = (int)((budget - fixed) / (7 * sizeof(R)));
+  cap = cap / kThreads * kThreads;
+  if (cap > 8192) cap = 8192;
+  a.cap = cap;
+  const size_t smem = fixed + (size_t)cap * 7 * sizeof(R);
+  cudaError_t e = cudaFuncSetAttribute(gather_kernel<R, MB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = T;
+  gather_kernel<R, MB><<<grid, kThreads, smem, s>>>(a, rec, xw);
+  (void)sm_count;
+  return cudaGetLastError();
+}
+
+template cudaError_t gather_wave<float>(const SortedCat&, const Bins&, const Layout&, const int*,
+                                        int, float2*, float2*, unsigned long long*, int,
+                                        cudaStream_t);
+template cudaError_t gather_wave<double>(const SortedCat&, const Bins&, const Layout&, const int*,
+                                         int, double2*, double2*, unsigned long long*, int,
+                                         cudaStream_t);
+
+}  // namespace ext4pcf

@@ -1,0 +1,264 @@
+// Cell-list grid: every galaxy gets the key cy*ncx + cx of its cell, the (key, index) pairs
+// are sorted with a stable least-significant-digit radix sort (8-bit digits), and the
+// catalogue is rewritten in cell order.  The neighbour search of the gather kernel then
+// reads each row of candidate cells as one contiguous range.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace ext4pcf {
+
+namespace {
+
+constexpr int kTileThreads = 256;
+constexpr int kTileItems = 8;  // keys per thread
+constexpr int kTile = kTileThreads * kTileItems;
+
+// ------------------------------------------------------------------------ bounding box
+__global__ void bbox_partial(const double* __restrict__ pos, int n, double* __restrict__ part) {
+  __shared__ double s[4][256];
+  double mnx = DBL_MAX, mny = DBL_MAX, mxx = -DBL_MAX, mxy = -DBL_MAX;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x = pos[2 * i], y = pos[2 * i + 1];
+    mnx = fmin(mnx, x); mxx = fmax(mxx, x);
+    mny = fmin(mny, y); mxy = fmax(mxy, y);
+  }
+  s[0][threadIdx.x] = mnx; s[1][threadIdx.x] = mny; s[2][threadIdx.x] = mxx; s[3][threadIdx.x] = mxy;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      s[0][threadIdx.x] = fmin(s[0][threadIdx.x], s[0][threadIdx.x + st]);
+      s[1][threadIdx.x] = fmin(s[1][threadIdx.x], s[1][threadIdx.x + st]);
+      s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + st]);
+      s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + st]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[4 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void bbox_final(const double* __restrict__ part, int np, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double v[4] = {DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int b = 0; b < np; ++b) {
+    v[0] = fmin(v[0], part[4 * b + 0]);
+    v[1] = fmin(v[1], part[4 * b + 1]);
+    v[2] = fmax(v[2], part[4 * b + 2]);
+    v[3] = fmax(v[3], part[4 * b + 3]);
+  }
+  for (int k = 0; k < 4; ++k) out[k] = v[k];
+}
+
+// ------------------------------------------------------------------------ keys
+__global__ void make_keys(const double* __restrict__ pos, int n, double x0, double y0,
+                          double inv_cell, int ncx, int ncy, int* __restrict__ keys,
+                          int* __restrict__ idx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int cx = (int)floor((pos[2 * i] - x0) * inv_cell);
+  int cy = (int)floor((pos[2 * i + 1] - y0) * inv_cell);
+  cx = min(max(cx, 0), ncx - 1);
+  cy = min(max(cy, 0), ncy - 1);
+  keys[i] = cy * ncx + cx;
+  idx[i] = i;
+}
+
+// ------------------------------------------------------------------------ radix sort
+__global__ void radix_hist(const int* __restrict__ keys, int n, int shift,
+                           unsigned* __restrict__ hist, int ntiles) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kTile;
+  for (int k = 0; k < kTileItems; ++k) {
+    int i = base + k * kTileThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[((unsigned)keys[i] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: warp w of a tile owns items [w*256, w*256+256) of the tile, visited in
+// order in rounds of 32, so ranks follow input order.
+__global__ void radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ val_in,
+                              int n, int shift, const unsigned* __restrict__ offs, int ntiles,
+                              int* __restrict__ keys_out, int* __restrict__ val_out) {
+  __shared__ unsigned wcnt[kTileThreads / 32][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = threadIdx.x; d < (kTileThreads / 32) * 256; d += kTileThreads)
+    (&wcnt[0][0])[d] = 0;
+  __syncthreads();
+  const int wbase = blockIdx.x * kTile + warp * (32 * kTileItems);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kTileItems; ++r) {
+    int i = wbase + r * 32 + lane;
+    bool valid = i < n;
+    unsigned valid_mask = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+      unsigned d = ((unsigned)keys_in[i] >> shift) & 0xFFu;
+      unsigned peers = __match_any_sync(valid_mask, d);
+      if ((peers & lt) == 0) wcnt[warp][d] += __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // exclusive prefix over warps, per digit
+    unsigned d = threadIdx.x;
+    unsigned run = 0;
+    for (int w = 0; w < kTileThreads / 32; ++w) {
+      unsigned t = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < kTileItems; ++r) {
+    int i = wbase + r * 32 + lane;
+    bool valid = i < n;
+    unsigned valid_mask = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+      int key = keys_in[i];
+      unsigned d = ((unsigned)key >> shift) & 0xFFu;
+      unsigned peers = __match_any_sync(valid_mask, d);
+      unsigned rank = __popc(peers & lt);
+      unsigned pos = offs[(size_t)d * ntiles + blockIdx.x] + wcnt[warp][d] + rank;
+      keys_out[pos] = key;
+      val_out[pos] = val_in[i];
+      __syncwarp(valid_mask);
+      if ((peers & lt) == 0) wcnt[warp][d] += __popc(peers);
+    }
+    __syncwarp();
+  }
+}
+
+// exclusive scan of unsigned values: block scan + recursive scan of block totals
+constexpr int kScanBlock = 1024;
+
+__global__ void scan_block(unsigned* __restrict__ data, size_t n, unsigned* __restrict__ totals) {
+  __shared__ unsigned s[kScanBlock];
+  size_t i = (size_t)blockIdx.x * kScanBlock + threadIdx.x;
+  unsigned v = i < n ? data[i] : 0u;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < kScanBlock; off <<= 1) {
+    unsigned t = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0u;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) data[i] = s[threadIdx.x] - v;
+  if (threadIdx.x == kScanBlock - 1) totals[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void scan_add(unsigned* __restrict__ data, size_t n, const unsigned* __restrict__ totals) {
+  size_t i = (size_t)blockIdx.x * kScanBlock + threadIdx.x;
+  if (i < n) data[i] += totals[blockIdx.x];
+}
+
+}  // namespace
+
+cudaError_t scan_exclusive(unsigned* data, size_t n, unsigned* tmp, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  size_t nb = (n + kScanBlock - 1) / kScanBlock;
+  scan_block<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, tmp);
+  if (nb > 1) {
+    cudaError_t e = scan_exclusive(tmp, nb, tmp + nb, s);
+    if (e != cudaSuccess) return e;
+    scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, tmp);
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+
+// ------------------------------------------------------------------------ cell offsets
+__global__ void cell_bounds(const int* __restrict__ keys, int n, int ncells, int* __restrict__ start) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > n) return;
+  int lo = (p == 0) ? -1 : keys[p - 1];
+  int hi = (p == n) ? ncells : keys[p];
+  for (int c = lo + 1; c <= hi; ++c) start[c] = p;
+}
+
+__global__ void fill_start_empty(int* start, int ncells) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c <= ncells) start[c] = 0;
+}
+
+// ------------------------------------------------------------------------ sorted arrays
+__global__ void build_sorted(const double* __restrict__ pos, const double* __restrict__ shear,
+                             const double* __restrict__ wts, const int* __restrict__ perm,
+                             const int* __restrict__ keys, int n, int ncx, double x0, double y0,
+                             double cell, float cellf, bool want_f32, double* __restrict__ px,
+                             double* __restrict__ py, double* __restrict__ xr,
+                             double* __restrict__ xi, double* __restrict__ w,
+                             float4* __restrict__ p4, float4* __restrict__ s4) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int i = perm[p];
+  double x = pos[2 * i], y = pos[2 * i + 1], ww = wts[i];
+  double gr = ww * shear[2 * i], gi = ww * shear[2 * i + 1];
+  px[p] = x; py[p] = y; xr[p] = gr; xi[p] = gi; w[p] = ww;
+  if (want_f32) {
+    int key = keys[p];
+    int cx = key % ncx, cy = key / ncx;
+    // cx*cell and cy*cell are exact in float (cell has few significant bits)
+    float ax = (float)cx * cellf, ay = (float)cy * cellf;
+    float lx = (float)((x - x0) - (double)cx * cell);
+    float ly = (float)((y - y0) - (double)cy * cell);
+    p4[p] = make_float4(ax, ay, lx, ly);
+    s4[p] = make_float4((float)gr, (float)gi, (float)ww, 0.f);
+  }
+}
+
+}  // namespace
+
+cudaError_t grid_bbox(const double* pos, int n, double* d_bbox, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int nblk = (n + 255) / 256;
+  if (nblk > 512) nblk = 512;
+  // partials go after the 4 result slots
+  bbox_partial<<<nblk, 256, 0, s>>>(pos, n, d_bbox + 4);
+  bbox_final<<<1, 32, 0, s>>>(d_bbox + 4, nblk, d_bbox);
+  return cudaGetLastError();
+}
+
+cudaError_t grid_sort(const double* pos, const double* shear, const double* wts, int n,
+                      double x0, double y0, double cell, int ncx, int ncy, bool want_f32,
+                      GridBuffers& gb, SortedCat& out, cudaStream_t s) {
+  const int ncells = ncx * ncy;
+  out.n = n; out.ncx = ncx; out.ncy = ncy; out.x0 = x0; out.y0 = y0;
+  out.cell = cell; out.cellf = (float)cell;
+  out.cell_start = gb.cell_start;
+  out.perm = gb.perm;
+  out.px = gb.px; out.py = gb.py; out.xr = gb.xr; out.xi = gb.xi; out.w = gb.w;
+  out.p4 = gb.p4; out.s4 = gb.s4;
+  if (n == 0) {
+    fill_start_empty<<<(ncells + 256) / 256, 256, 0, s>>>(gb.cell_start, ncells);
+    return cudaGetLastError();
+  }
+  make_keys<<<(n + 255) / 256, 256, 0, s>>>(pos, n, x0, y0, 1.0 / cell, ncx, ncy, gb.keys, gb.perm);
+  int bits = 1;
+  while ((1 << bits) < ncells) ++bits;
+  const int ntiles = (n + kTile - 1) / kTile;
+  int* kin = gb.keys; int* kout = gb.keys_alt;
+  int* vin = gb.perm; int* vout = gb.perm_alt;
+  unsigned* hist = gb.hist;
+  unsigned* tmp = gb.hist + (size_t)256 * ntiles;
+  for (int shift = 0; shift < bits; shift += 8) {
+    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
+    cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
+    int* t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+  }
+  out.perm = vin;
+  cell_bounds<<<(n + 1 + 255) / 256, 256, 0, s>>>(kin, n, ncells, gb.cell_start);
+  build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, ncx, x0, y0, cell,
+                                               (float)cell, want_f32, gb.px, gb.py, gb.xr, gb.xi,
+                                               gb.w, gb.p4, gb.s4);
+  return cudaGetLastError();
+}
+
+}  // namespace ext4pcf

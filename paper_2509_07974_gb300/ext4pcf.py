@@ -1,0 +1,222 @@
+"""ctypes binding of libext4pcf (include/ext4pcf.h): argument marshalling only.
+
+The functions ``ext4pcf_create``, ``ext4pcf_destroy``, ``ext4pcf_measure``,
+``ext4pcf_to_real_space``, ``ext4pcf_to_map4`` and ``ext4pcf_last_error`` mirror the C ABI
+one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
+integer addresses or None.  ``Estimator`` wraps them for torch users: it allocates outputs
+and passes the current CUDA stream.  Every computation happens in the CUDA library; there
+is no fallback, and loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libext4pcf.so")
+
+EXT4PCF_OK = 0
+EXT4PCF_E_INVALID_ARG = -1
+EXT4PCF_E_OOM = -2
+EXT4PCF_E_CUDA = -3
+EXT4PCF_E_TIMEOUT = -4
+EXT4PCF_E_UNSUPPORTED = -5
+
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16x3": 4}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("workspace_bytes", ctypes.c_int64),
+                ("timeout_cycles", ctypes.c_int64), ("deterministic", ctypes.c_int),
+                ("wave_centres", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("centres", ctypes.c_int64), ("waves", ctypes.c_int64),
+                ("ms_grid", ctypes.c_double), ("ms_gather", ctypes.c_double),
+                ("ms_contract", ctypes.c_double), ("ms_correct", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Ext4pcfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("ext4pcf error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libext4pcf.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libext4pcf.so not found at %s; run paper_2509_07974_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.ext4pcf_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Config)]
+    lib.ext4pcf_destroy.argtypes = [P]
+    lib.ext4pcf_measure.argtypes = [P, P, P, P, I64, P, I, I, P, I, P, P, P, ctypes.POINTER(Stats)]
+    lib.ext4pcf_to_real_space.argtypes = [P, P, I, I, I, P, P]
+    lib.ext4pcf_to_map4.argtypes = [P, P, P, I, I, I, P, I, P, P, P, P]
+    lib.ext4pcf_last_error.argtypes = [P]
+    lib.ext4pcf_last_error.restype = ctypes.c_char_p
+    for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_to_real_space",
+              "ext4pcf_to_map4"):
+        getattr(lib, f).restype = I
+    _lib = lib
+    return lib
+
+
+def _addr(x):
+    """Address of a torch tensor / numpy array / int (None -> None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+# ---- the C ABI, one to one ------------------------------------------------------------
+def ext4pcf_create(config: Config) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    rc = lib.ext4pcf_create(ctypes.byref(h), ctypes.byref(config))
+    if rc != EXT4PCF_OK:
+        raise Ext4pcfError(rc, "ext4pcf_create failed")
+    return h.value
+
+
+def ext4pcf_destroy(ctx: int) -> int:
+    return load().ext4pcf_destroy(ctx)
+
+
+def ext4pcf_last_error(ctx: int) -> str:
+    r = load().ext4pcf_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def _check(ctx, rc):
+    if rc != EXT4PCF_OK:
+        raise Ext4pcfError(rc, ext4pcf_last_error(ctx))
+    return rc
+
+
+def ext4pcf_measure(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max,
+                    cat_offsets=None, n_cat=1, centre_mask=None, upsilon=None, xi_acc=None,
+                    stats: Stats | None = None) -> int:
+    lib = load()
+    rc = lib.ext4pcf_measure(ctx, _addr(positions), _addr(shears), _addr(weights), int(n_gal),
+                             _addr(radial_bins), int(n_bins), int(n_max), _addr(cat_offsets),
+                             int(n_cat), _addr(centre_mask), _addr(upsilon), _addr(xi_acc),
+                             ctypes.byref(stats) if stats is not None else None)
+    return _check(ctx, rc)
+
+
+def ext4pcf_to_real_space(ctx, upsilon, n_bins, n_max, n_phi, gamma, norm) -> int:
+    rc = load().ext4pcf_to_real_space(ctx, _addr(upsilon), int(n_bins), int(n_max), int(n_phi),
+                                      _addr(gamma), _addr(norm))
+    return _check(ctx, rc)
+
+
+def ext4pcf_to_map4(ctx, upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n_ap, xi_pm,
+                    m4, map4_eb, map4_disc) -> int:
+    rc = load().ext4pcf_to_map4(ctx, _addr(upsilon), _addr(radial_bins), int(n_bins), int(n_max),
+                                int(n_phi), _addr(ap_radii), int(n_ap), _addr(xi_pm), _addr(m4),
+                                _addr(map4_eb), _addr(map4_disc))
+    return _check(ctx, rc)
+
+
+# ---- torch convenience wrapper ---------------------------------------------------------
+class Estimator:
+    """One context on one device.  Inputs are torch tensors (float64); outputs are
+    allocated as torch float64 tensors on the same device (complex values interleaved;
+    ``as_complex`` gives a complex128 view)."""
+
+    def __init__(self, device: int = 0, precision: str = "fp64", stream=None,
+                 wave_centres: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        cfg = Config(device=device, stream=stream.cuda_stream, precision=PRECISION[precision],
+                     autotune=0, workspace_bytes=0, timeout_cycles=0, deterministic=1,
+                     wave_centres=wave_centres)
+        self.ctx = ext4pcf_create(cfg)
+
+    def close(self):
+        if self.ctx:
+            ext4pcf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def ups_shape(n_bins, n_max, n_cat=1):
+        nn = 2 * n_max + 1
+        return (n_cat, 9, nn, nn, n_bins, n_bins, n_bins, 2)
+
+    def measure(self, positions, shears, weights, radial_bins, n_max, cat_offsets=None,
+                centre_mask=None, upsilon=None, xi_acc=None, want_stats=False):
+        torch = self.torch
+        import numpy as np
+        edges = np.ascontiguousarray(np.asarray(radial_bins, dtype=np.float64))
+        nb = edges.size - 1
+        n_gal = positions.shape[0]
+        n_cat = 1
+        offs = None
+        if cat_offsets is not None:
+            offs = np.ascontiguousarray(np.asarray(cat_offsets, dtype=np.int64))
+            n_cat = offs.size - 1
+        if upsilon is None:
+            upsilon = torch.zeros(self.ups_shape(nb, n_max, n_cat), dtype=torch.float64,
+                                  device=positions.device)
+        st = Stats() if want_stats else None
+        ext4pcf_measure(self.ctx, positions, shears, weights, n_gal, edges, nb, n_max, offs, n_cat,
+                        centre_mask, upsilon, xi_acc, st)
+        return (upsilon, st.as_dict()) if want_stats else upsilon
+
+    def to_real_space(self, upsilon, n_phi):
+        torch = self.torch
+        nb = upsilon.shape[-2]
+        n_max = (upsilon.shape[-5] - 1) // 2
+        gamma = torch.zeros((8, nb, nb, nb, n_phi, n_phi, 2), dtype=torch.float64, device=upsilon.device)
+        norm = torch.zeros((nb, nb, nb, n_phi, n_phi), dtype=torch.float64, device=upsilon.device)
+        ext4pcf_to_real_space(self.ctx, upsilon, nb, n_max, n_phi, gamma, norm)
+        return gamma, norm
+
+    def to_map4(self, upsilon, radial_bins, n_phi, ap_radii, xi_pm=None):
+        import numpy as np
+        edges = np.ascontiguousarray(np.asarray(radial_bins, dtype=np.float64))
+        nb = edges.size - 1
+        n_max = (upsilon.shape[-5] - 1) // 2
+        ap = np.ascontiguousarray(np.asarray(ap_radii, dtype=np.float64))
+        n_ap = ap.size
+        m4 = np.zeros((n_ap, 8, 2))
+        eb = np.zeros((n_ap, 16))
+        disc = np.zeros((n_ap, 16))
+        xi = None if xi_pm is None else np.ascontiguousarray(np.asarray(xi_pm, dtype=np.float64))
+        ext4pcf_to_map4(self.ctx, upsilon, edges, nb, n_max, n_phi, ap, n_ap, xi, m4, eb, disc)
+        return m4[..., 0] + 1j * m4[..., 1], eb, disc
+
+
+def as_complex(t):
+    """complex128 view of an interleaved float64 tensor (last axis 2)."""
+    import torch
+    return torch.view_as_complex(t)

@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (floor-relative error |a-b| / max(|b|, rms_{n2,n3}|b|) per component):
+  FP64 form: 1e-10;  FP32 form: 1e-4.
+Bin decisions must agree exactly (the FP32 form re-decides near-edge pairs in FP64).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+
+
+def rel_err(a, b):
+    floor = np.sqrt(np.mean(np.abs(b) ** 2, axis=(1, 2), keepdims=True))
+    den = np.maximum(np.abs(b), floor)
+    den = np.where(den > 0, den, 1.0)
+    return np.abs(a - b) / den
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_07974_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def small(oracle):
+    import synth
+    pos, sh, w, edges, nmax = synth.small_workload()
+    w = np.random.default_rng(3).uniform(0.5, 1.5, len(w))
+    ref, xi = oracle.measure(pos, sh, w, edges, nmax, with_xi=True)
+    return dict(pos=pos, sh=sh, w=w, edges=edges, nmax=nmax, ref=ref, xi=xi)
+
+
+def run_gpu(torch, pos, sh, w, edges, nmax, prec="fp64", wave=0, mask=None, offsets=None,
+            host=False, stats=False, xi=False):
+    from paper_2509_07974_gb300 import ext4pcf
+    est = ext4pcf.Estimator(0, prec, wave_centres=wave)
+    dev = torch.device("cuda:0")
+    if host:
+        tp, ts, tw = (np.ascontiguousarray(a, dtype=np.float64) for a in (pos, sh, w))
+        tm = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    else:
+        tp, ts, tw = (torch.tensor(np.asarray(a, dtype=np.float64), device=dev) for a in (pos, sh, w))
+        tm = None if mask is None else torch.tensor(np.asarray(mask, dtype=np.uint8), device=dev)
+    nb = len(edges) - 1
+    n_cat = 1 if offsets is None else len(offsets) - 1
+    shape = ext4pcf.Estimator.ups_shape(nb, nmax, n_cat)
+    if host:
+        ups = np.zeros(shape)
+        xia = np.zeros((n_cat, nb, 3, 2)) if xi else None
+    else:
+        ups = torch.zeros(shape, dtype=torch.float64, device=dev)
+        xia = torch.zeros((n_cat, nb, 3, 2), dtype=torch.float64, device=dev) if xi else None
+    st = ext4pcf.Stats()
+    ext4pcf.ext4pcf_measure(est.ctx, tp, ts, tw, len(w), np.ascontiguousarray(edges, dtype=np.float64),
+                            nb, nmax, None if offsets is None else np.asarray(offsets, dtype=np.int64),
+                            n_cat, tm, ups, xia, st)
+    torch.cuda.synchronize()
+    est.close()
+    if not host:
+        ups = ups.cpu().numpy()
+        xia = None if xia is None else xia.cpu().numpy()
+    out = ups[..., 0] + 1j * ups[..., 1]
+    res = [out if offsets is not None else out[0]]
+    if xi:
+        x = xia[..., 0] + 1j * xia[..., 1]
+        res.append(x if offsets is not None else x[0])
+    if stats:
+        res.append(st.as_dict())
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_workload(torch_cuda, small, prec):
+    got, xi = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"],
+                      prec, xi=True)
+    assert np.abs(small["ref"]).max() > 0
+    assert rel_err(got, small["ref"]).max() < TOL[prec]
+    assert np.allclose(xi, small["xi"], rtol=TOL[prec], atol=TOL[prec] * np.abs(small["xi"]).max())
+
+
+@pytest.mark.parametrize("prec,wave", [("fp64", 37), ("fp32", 100), ("fp32", 1)])
+def test_ragged_waves(torch_cuda, small, prec, wave):
+    got = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"],
+                  prec, wave=wave)
+    assert rel_err(got, small["ref"]).max() < TOL[prec]
+
+
+def test_deterministic(torch_cuda, small):
+    a = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"], "fp32")
+    b = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"], "fp32")
+    assert np.array_equal(a, b)
+
+
+def test_pair_count(torch_cuda, small):
+    from scipy.spatial import cKDTree
+    _, st = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"],
+                    "fp32", stats=True)
+    t = cKDTree(small["pos"])
+    e = small["edges"]
+    n_hi = t.count_neighbors(t, np.nextafter(e[-1], 0))
+    n_lo = t.count_neighbors(t, np.nextafter(e[0], 0))
+    assert st["pairs"] == n_hi - n_lo
+    assert st["centres"] == len(small["w"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_centre_mask_and_host_pointers(torch_cuda, oracle, small, prec):
+    mask = (np.random.default_rng(8).uniform(size=len(small["w"])) < 0.3).astype(np.uint8)
+    ref = oracle.measure(small["pos"], small["sh"], small["w"], small["edges"], 6, centre_mask=mask)
+    got = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], 6, prec, mask=mask)
+    assert rel_err(got, ref).max() < TOL[prec]
+    got_h = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], 6, prec, mask=mask,
+                    host=True)
+    assert np.array_equal(got, got_h)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_catalogues(torch_cuda, oracle, prec):
+    import synth
+    sizes = [150, 0, 420, 1, 260]
+    cats = [synth.uniform_catalog(n, 25.0 + 5 * k, seed=40 + k, weights="uniform") for k, n in enumerate(sizes)]
+    edges = synth.log_edges(1.0, 9.0, 5)
+    nmax = 4
+    pos = np.concatenate([c[0] for c in cats])
+    sh = np.concatenate([c[1] for c in cats])
+    w = np.concatenate([c[2] for c in cats])
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, prec, offsets=offs)
+    for k, c in enumerate(cats):
+        if sizes[k] == 0:
+            assert np.abs(got[k]).max() == 0
+            continue
+        ref = oracle.measure(c[0], c[1], c[2], edges, nmax)
+        if np.abs(ref).max() == 0:
+            assert np.abs(got[k]).max() == 0
+        else:
+            assert rel_err(got[k], ref).max() < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_exact_bin_edge_separations(torch_cuda, oracle, prec):
+    """Integer lattice with integer bin edges: many separations sit exactly on an edge
+    (r^2 = 1, 4, 16 exactly); the bin decision must be that of the FP64 definition."""
+    g = np.arange(9.0)
+    X, Y = np.meshgrid(g, g)
+    pos = np.c_[X.ravel(), Y.ravel()] + 1000.0
+    rng = np.random.default_rng(9)
+    sh = rng.normal(0, 0.3, pos.shape)
+    w = rng.uniform(0.5, 1.5, len(pos))
+    edges = np.array([1.0, 2.0, 4.0, 5.0])
+    ref = oracle.measure(pos, sh, w, edges, 3)
+    got = run_gpu(torch_cuda, pos, sh, w, edges, 3, prec)
+    assert rel_err(got, ref).max() < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_duplicates_and_degenerate(torch_cuda, oracle, prec):
+    rng = np.random.default_rng(10)
+    pos = rng.uniform(0, 6, (40, 2))
+    pos = np.concatenate([pos, pos[:10], pos[:3]])
+    sh = rng.normal(0, 0.3, pos.shape)
+    w = rng.uniform(0.5, 1.5, len(pos))
+    edges = np.array([0.3, 1.0, 2.5, 4.0])
+    ref = oracle.measure(pos, sh, w, edges, 3)
+    got = run_gpu(torch_cuda, pos, sh, w, edges, 3, prec)
+    assert rel_err(got, ref).max() < TOL[prec]
+    # all galaxies at one point: no separation inside any bin
+    same = np.zeros((20, 2)) + 3.0
+    z = run_gpu(torch_cuda, same, sh[:20], w[:20], edges, 2, prec)
+    assert np.abs(z).max() == 0
+    one = run_gpu(torch_cuda, pos[:1], sh[:1], w[:1], edges, 2, prec)
+    assert np.abs(one).max() == 0
+    empty = run_gpu(torch_cuda, np.zeros((0, 2)), np.zeros((0, 2)), np.zeros(0), edges, 2, prec)
+    assert np.abs(empty).max() == 0
+
+
+@pytest.mark.parametrize("prec,nb,nmax", [("fp64", 1, 0), ("fp32", 1, 0), ("fp64", 32, 2),
+                                          ("fp32", 32, 2), ("fp64", 2, 40), ("fp32", 2, 40)])
+def test_extreme_shapes(torch_cuda, oracle, prec, nb, nmax):
+    rng = np.random.default_rng(11)
+    pos = rng.uniform(0, 10, (60, 2))
+    sh = rng.normal(0, 0.3, pos.shape)
+    w = rng.uniform(0.5, 1.5, 60)
+    edges = np.geomspace(0.4, 6.0, nb + 1)
+    ref = oracle.measure(pos, sh, w, edges, nmax)
+    got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, prec)
+    assert rel_err(got, ref).max() < TOL[prec]
+
+
+def test_invalid_arguments_are_rejected(torch_cuda):
+    from paper_2509_07974_gb300 import ext4pcf
+    est = ext4pcf.Estimator(0, "fp64")
+    dev = torch_cuda.device("cuda:0")
+    p = torch_cuda.zeros((4, 2), dtype=torch_cuda.float64, device=dev)
+    w = torch_cuda.ones(4, dtype=torch_cuda.float64, device=dev)
+    ups = torch_cuda.zeros(ext4pcf.Estimator.ups_shape(2, 1), dtype=torch_cuda.float64, device=dev)
+    for edges, nmax in ((np.array([0.0, 1.0, 2.0]), 1), (np.array([1.0, 0.5, 2.0]), 1), (np.array([1.0, 2.0, 3.0]), -1)):
+        with pytest.raises(ext4pcf.Ext4pcfError) as e:
+            ext4pcf.ext4pcf_measure(est.ctx, p, p, w, 4, edges, 2, nmax, None, 1, None, ups, None)
+        assert e.value.code == ext4pcf.EXT4PCF_E_INVALID_ARG
+    est.close()
+
+
+# --------------------------------------------------------------------------------------
+def test_real_space_matches_oracle(torch_cuda, oracle, small):
+    from paper_2509_07974_gb300 import ext4pcf
+    ref = oracle.measure(small["pos"], small["sh"], small["w"], small["edges"][:5], 4)
+    gam_o, nrm_o = oracle.to_real_space(ref, 13)
+    est = ext4pcf.Estimator(0, "fp64")
+    u = np.stack([ref.real, ref.imag], axis=-1)[None]
+    tu = torch_cuda.tensor(u, device="cuda:0")
+    gam, nrm = est.to_real_space(tu[0], 13)
+    torch_cuda.cuda.synchronize()
+    est.close()
+    g = gam.cpu().numpy()
+    g = g[..., 0] + 1j * g[..., 1]
+    assert np.allclose(nrm.cpu().numpy(), nrm_o, rtol=1e-12, atol=1e-12 * np.abs(nrm_o).max())
+    scale = np.abs(gam_o).max()
+    assert np.abs(g - gam_o).max() < 1e-9 * scale
+
+
+def test_map4_matches_oracle(torch_cuda, oracle, small):
+    from paper_2509_07974_gb300 import ext4pcf
+    edges = small["edges"][:5]
+    ref, xacc = oracle.measure(small["pos"], small["sh"], small["w"], edges, 4, with_xi=True)
+    xi = oracle.xi_from_acc(xacc)
+    ap = [3.0, 5.0]
+    m4_o, eb_o, disc_o = oracle.map4(ref, edges, 11, ap, xi)
+    est = ext4pcf.Estimator(0, "fp64")
+    tu = torch_cuda.tensor(np.stack([ref.real, ref.imag], axis=-1), device="cuda:0")
+    m4, eb, disc = est.to_map4(tu, edges, 11, ap, xi)
+    est.close()
+    assert np.abs(m4 - m4_o).max() < 1e-9 * np.abs(m4_o).max()
+    assert np.abs(eb - eb_o).max() < 1e-9 * np.abs(eb_o).max()
+    assert np.abs(disc - disc_o).max() < 1e-9 * np.abs(disc_o).max()
+
+
+# --------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def grf_full():
+    import synth
+    pos, sh, w, edges, nmax = synth.grf2e6_workload()
+    mask = np.zeros(len(w), np.uint8)
+    mask[np.random.default_rng(12).choice(len(w), 48, replace=False)] = 1
+    return pos, sh, w, edges, nmax, mask
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_sampled_centres(torch_cuda, oracle, grf_full, prec):
+    """The 2e6-galaxy, 10-bin, n_max = 20 workload at full size, every galaxy a neighbour,
+    48 sampled centres: the sum over those centres is exact, so the oracle can check it."""
+    pos, sh, w, edges, nmax, mask = grf_full
+    ref = oracle.measure(pos, sh, w, edges, nmax, centre_mask=mask)
+    got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, prec, mask=mask)
+    assert rel_err(got, ref).max() < TOL[prec]
