@@ -1,0 +1,408 @@
+"""Benchmark of the shear-4PCF multipole estimator on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one synthetic catalogue: cell grid and
+radix sort, neighbour gather of the multipoles, contraction into Upsilon_mu / N,
+multiple-counting corrections, and the fourth-order aperture measures (real space formed
+on the fly).  Workload: a Gaussian-random-field shear mock of 2e6 galaxies on a 10 deg x
+10 deg flat patch (power-law P(l) ~ l^-1.2 on a 4096^2 grid, Kaiser-Squires, shape noise
+0.26 per component, weights U[0.5, 1.5]), 10 log radial bins 0.5'-40', n_max = 20;
+aperture measures on 129 angular bins and 24 log-spaced aperture radii 1'-32'.
+
+Metric: galaxy pairs per second (pairs with separation inside the radial bins, counted by
+the kernels) over the whole step; the contraction TFLOP/s and the mixed-vs-FP64 comparison
+are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+N_PHI = 129
+AP_RADII = np.geomspace(1.0, 32.0, 24)
+METRIC = "galaxy pairs/s + Upsilon contraction TFLOP/s; mixed vs FP64 form at stated rel err"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["source"] = "fallback"
+    return d
+
+
+def gather_flop_per_pair(nmax):
+    """Algorithmic FP32 work of one (centre, neighbour) pair in the gather: complex
+    accumulations x u^n (4N+3 values) and x^2 u^n (4N+5), real-weighted w u^m (2N+1),
+    |x|^2 u^m (2N+3), w^2 u^m (2N+1), the powers u^1..u^{2N+6} and ~40 for the triple terms."""
+    N = nmax
+    return 8 * (4 * N + 3) + 8 * (4 * N + 5) + 4 * ((2 * N + 1) + (2 * N + 3) + (2 * N + 1)) + 6 * (2 * N + 6) + 40
+
+
+def contraction_flop(n_centres, nmax, nb):
+    """One complex multiply-add per output element per centre: 8 * centres * 9 (2N+1)^2 nb^3."""
+    return 8.0 * n_centres * 9 * (2 * nmax + 1) ** 2 * nb ** 3
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, sm_max_default):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": sm_max_default, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for k, name in enumerate(names):
+            if any(r[5 + k].lower() in ("active", "1") for r in rows):
+                reasons.append(name)
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else sm_max_default, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def make_workload(seed_offset=0, n=None):
+    import synth
+    c = dict(synth.GRF2E6)
+    pos, sh, w = synth.grf_catalog(n or c["n"], c["side"], c["seed"] + seed_offset, grid=c["grid"])
+    edges = synth.log_edges(c["lo"], c["hi"], c["nb"])
+    return pos, sh, w, edges, c["nmax"], c
+
+
+def dist_setup(want_gpu):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if want_gpu else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+def oracle_sample(pos, sh, w, edges, nmax, n_centres, seed=0):
+    """A bounded sample of the workload for the CPU oracle: n_centres random centres (every
+    galaxy stays a neighbour).  Returns (mask, seconds, threads)."""
+    import oracle
+    oracle.build()
+    mask = np.zeros(len(w), np.uint8)
+    mask[np.random.default_rng(1234 + seed).choice(len(w), n_centres, replace=False)] = 1
+    t0 = time.perf_counter()
+    oracle.measure(pos, sh, w, edges, nmax, centre_mask=mask)
+    return mask, time.perf_counter() - t0, os.cpu_count()
+
+
+def pairs_of_mask(pos, edges, mask):
+    """Pairs of the sampled centres, counted with a k-d tree (for the oracle's rate)."""
+    from scipy.spatial import cKDTree
+    t = cKDTree(pos)
+    cen = pos[mask.astype(bool)]
+    tc = cKDTree(cen)
+    hi = tc.count_neighbors(t, np.nextafter(edges[-1], 0))
+    lo = tc.count_neighbors(t, np.nextafter(edges[0], 0))
+    return int(hi - lo)
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU program) on a bounded sample of the same workload."""
+    world, rank, _ = dist_setup(False)
+    if rank != 0:
+        return
+    pos, sh, w, edges, nmax, c = make_workload()
+    n_c = args.oracle_centres
+    mask, _, _ = oracle_sample(pos, sh, w, edges, nmax, n_c)  # warm-up build and page-in
+    pairs = pairs_of_mask(pos, edges, mask)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(pos, sh, w, edges, nmax, n_c, seed=1)
+    times = []
+    for k in range(args.steps):
+        _, dt, cores = oracle_sample(pos, sh, w, edges, nmax, n_c, seed=0)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = pairs / t
+    sample = "%d random centres of the %d-galaxy catalogue (all galaxies as neighbours), %d pairs" % (
+        n_c, len(w), pairs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": c["name"], "n_gal": len(w), "n_bins": c["nb"], "n_max": nmax,
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2509_07974_gb300 import build, ext4pcf
+
+    world, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    pk = peaks()
+    pos, sh, w, edges, nmax, c = make_workload(seed_offset=rank)
+    nb = len(edges) - 1
+    tp = torch.tensor(pos, device=dev)
+    ts = torch.tensor(sh, device=dev)
+    tw = torch.tensor(w, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    est = ext4pcf.Estimator(local, args.precision, stream=stream)
+    ups = torch.zeros(ext4pcf.Estimator.ups_shape(nb, nmax), dtype=torch.float64, device=dev)
+    xia = torch.zeros((1, nb, 3, 2), dtype=torch.float64, device=dev)
+    edges_c = np.ascontiguousarray(edges)
+    ap = np.ascontiguousarray(AP_RADII)
+    m4 = np.zeros((len(ap), 8, 2))
+    eb = np.zeros((len(ap), 16))
+    disc = np.zeros((len(ap), 16))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(stats=None):
+        ups.zero_()
+        xia.zero_()
+        ext4pcf.ext4pcf_measure(est.ctx, tp, ts, tw, len(w), edges_c, nb, nmax, None, 1, None, ups, xia, stats)
+        ext4pcf.ext4pcf_to_map4(est.ctx, ups, edges_c, nb, nmax, N_PHI, ap, len(ap), xia, m4, eb, disc)
+
+    # kernel-level breakdown (per-wave events; outside the timed region)
+    st = ext4pcf.Stats()
+    step(st)
+    torch.cuda.synchronize()
+    bd = st.as_dict()
+    pairs = bd["pairs"]
+    log("rank %d: stats %s" % (rank, bd))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed between steps (outside the per-step events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    dev_ms_max = max_over_ranks(dev_ms, world, dev)
+    pairs_all = sum_over_ranks(float(pairs) * args.steps, world, dev)
+    value = pairs_all / (dev_ms_max / 1e3)
+    clocks = cs.summary(pk.get("sm_max_mhz", 2070.0))
+
+    # end to end through the C ABI: inputs from pinned host buffers (copied inside the call),
+    # results of the step (aperture measures) read back to the host
+    hp = torch.tensor(pos).pin_memory()
+    hs = torch.tensor(sh).pin_memory()
+    hw = torch.tensor(w).pin_memory()
+    e2e_t = []
+    for k in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ups.zero_()
+        xia.zero_()
+        ext4pcf.ext4pcf_measure(est.ctx, hp, hs, hw, len(w), edges_c, nb, nmax, None, 1, None, ups, xia, None)
+        ext4pcf.ext4pcf_to_map4(est.ctx, ups, edges_c, nb, nmax, N_PHI, ap, len(ap), xia, m4, eb, disc)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = sum(e2e_t) / len(e2e_t)
+    h2d = hp.numel() * 8 + hs.numel() * 8 + hw.numel() * 8
+    d2h = m4.nbytes + eb.nbytes + disc.nbytes
+
+    # roofline of the dominant kernel (the gather): FP32 pipe, algorithmic FLOP per launch
+    flop_pair = gather_flop_per_pair(nmax)
+    gather_ms_per_launch = bd["ms_gather"] / max(1, bd["waves"])
+    achieved = flop_pair * pairs / max(1, bd["waves"]) / (gather_ms_per_launch / 1e3) / 1e12
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    c_flop = contraction_flop(bd["centres"], nmax, nb)
+    contraction_tflops = c_flop / (bd["ms_contract"] / 1e3) / 1e12 if bd["ms_contract"] > 0 else None
+
+    fp64_info = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_baselines:
+        # FP64 GPU form on a sample of centres, for the mixed-vs-FP64 comparison
+        mask = np.zeros(len(w), np.uint8)
+        mask[np.random.default_rng(77).choice(len(w), args.fp64_centres, replace=False)] = 1
+        tm = torch.tensor(mask, device=dev)
+        e64 = ext4pcf.Estimator(local, "fp64", stream=stream)
+        u64 = torch.zeros_like(ups)
+        s64 = ext4pcf.Stats()
+        ext4pcf.ext4pcf_measure(e64.ctx, tp, ts, tw, len(w), edges_c, nb, nmax, None, 1, tm, u64, None, s64)
+        torch.cuda.synchronize()
+        s64 = s64.as_dict()
+        umx = torch.zeros_like(ups)
+        smx = ext4pcf.Stats()
+        ext4pcf.ext4pcf_measure(est.ctx, tp, ts, tw, len(w), edges_c, nb, nmax, None, 1, tm, umx, None, smx)
+        torch.cuda.synchronize()
+        smx = smx.as_dict()
+        a = torch.view_as_complex(umx).cpu().numpy()
+        b = torch.view_as_complex(u64).cpu().numpy()[0]
+        a = a[0]
+        floor = np.sqrt(np.mean(np.abs(b) ** 2, axis=(1, 2), keepdims=True))
+        scale = np.abs(b).reshape(9, -1).max(axis=1).reshape(9, 1, 1, 1, 1, 1)
+        den = np.maximum(np.maximum(np.abs(b), floor), 1e-12 * scale)
+        err = float((np.abs(a - b) / np.where(den > 0, den, 1)).max())
+        fp64_info = {"centres": args.fp64_centres, "pairs": s64["pairs"],
+                     "fp64_pairs_per_s": s64["pairs"] / (s64["ms_total"] / 1e3),
+                     "mixed_pairs_per_s_same_sample": smx["pairs"] / (smx["ms_total"] / 1e3),
+                     "speedup_mixed_vs_fp64": (s64["ms_total"] / smx["ms_total"]),
+                     "max_rel_err_mixed_vs_fp64": err}
+        e64.close()
+        # CPU oracle on a bounded sample
+        omask, odt, cores = oracle_sample(pos, sh, w, edges, nmax, args.oracle_centres)
+        opairs = pairs_of_mask(pos, edges, omask)
+        cpu = {"value": opairs / odt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": "%d random centres of the %d-galaxy catalogue (all galaxies as neighbours), %d pairs, %.1f s"
+                         % (args.oracle_centres, len(w), opairs, odt)}
+
+    # kernels per step: those of ext4pcf_measure (counted by the library) plus those of
+    # ext4pcf_to_map4: angle table + (norm, gamma, integrate) per chunk of radial triples + finish
+    nph2 = N_PHI * N_PHI
+    chunk = min(nb ** 3, max(1, (256 << 20) // (nph2 * 8 * 16)))
+    map4_launches = 2 + 3 * ((nb ** 3 + chunk - 1) // chunk)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": c["name"], "n_gal": len(w), "n_bins": nb, "n_max": nmax,
+                           "precision": args.precision, "n_phi": N_PHI, "apertures": len(ap),
+                           "pairs_per_step": pairs, "l2": "flushed between steps (256 MB write)",
+                           "parallelism": "one catalogue per GPU" if world > 1 else "1 GPU"},
+                "contraction_tflops": contraction_tflops,
+                "breakdown_ms": {k: bd[k] for k in ("ms_grid", "ms_gather", "ms_contract", "ms_correct", "ms_total")},
+                "wall_s": t_wall,
+                "e2e": {"value": pairs / e2e, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "roofline": {"bound": "alu", "kernel": "gather", "achieved": achieved,
+                             "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                             "traffic": None,
+                             "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock (%s MHz)"
+                                          % pk.get("sm_max_mhz", 2070.0),
+                             "algorithmic_flop_per_pair": flop_pair},
+                "fp64_form": fp64_info,
+                "cpu_baseline": cpu,
+                "clocks": clocks,
+                "gpu_launches": int((bd["launches"] + map4_launches) * args.steps)}
+        print(json.dumps(line), flush=True)
+    est.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3"])
+    ap.add_argument("--oracle-centres", type=int, default=2000)
+    ap.add_argument("--fp64-centres", type=int, default=4096)
+    ap.add_argument("--no-baselines", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

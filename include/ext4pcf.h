@@ -77,6 +77,7 @@ typedef struct {
   int64_t pairs;   /* (centre, neighbour) pairs with separation inside the radial bins */
   int64_t centres; /* galaxies that acted as centres */
   int64_t waves;   /* contraction waves launched */
+  int64_t launches; /* kernels launched by the call */
   double ms_grid, ms_gather, ms_contract, ms_correct, ms_total; /* CUDA-event times */
 } ext4pcf_stats;
 
@@ -134,14 +135,16 @@ EXT4PCF_API int ext4pcf_to_real_space(ext4pcf_ctx* ctx, const double* upsilon, i
  * angular bins.
  *   upsilon     device, one catalogue
  *   radial_bins host [n_bins+1];  ap_radii host [n_ap]
- *   xi_pm       host [n_bins][4] (xi+ re, im, xi- re, im) or NULL
+ *   xi_acc      device or host, [n_bins][3][2] accumulators written by ext4pcf_measure
+ *               (xi_+ = first / third, xi_- = second / third per bin), or NULL
  *   m4          host [n_ap][8][2]: the correlators of Eq. M4Ordering (accumulated)
  *   map4_eb     host [n_ap][16]: E/B moments in the order of Eq. 4PCF_rawcomponents
- *   map4_disc   host [n_ap][16] or NULL: Gaussian part from xi_pm (Wick pairs of
- *               <M M> and <M M^*>) in the same order; connected = map4_eb - map4_disc */
+ *   map4_disc   host [n_ap][16] or NULL: Gaussian part built from xi_+- (Wick pairs of
+ *               <M M> and <M M^*>, each an integral of xi_+- with the two-point filters
+ *               T_+- of the same filter), same order; connected = map4_eb - map4_disc */
 EXT4PCF_API int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radial_bins,
                     int n_bins, int n_max, int n_phi, const double* ap_radii, int n_ap,
-                    const double* xi_pm, double* m4, double* map4_eb, double* map4_disc);
+                    const double* xi_acc, double* m4, double* map4_eb, double* map4_disc);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 EXT4PCF_API const char* ext4pcf_last_error(const ext4pcf_ctx* ctx);

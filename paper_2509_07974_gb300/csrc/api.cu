@@ -22,6 +22,10 @@ cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const 
                                double* d_m4, double* d_eb, double* d_disc, cudaStream_t s);
 }  // namespace ext4pcf
 
+namespace ext4pcf {
+thread_local long long g_launches = 0;
+}
+
 using namespace ext4pcf;
 
 namespace {
@@ -271,6 +275,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   bins.rmax = radial_bins[n_bins];
 
   const bool timing = stats != nullptr;
+  const long long launches0 = g_launches;
   float ms_grid = 0, ms_gather = 0, ms_contract = 0, ms_correct = 0, ms_total = 0;
   int64_t tot_centres = 0, tot_waves = 0;
   if (timing) CK(cudaEventRecord(ctx->ev[0], s));
@@ -327,6 +332,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       ENSURE(ctx->flags, ((size_t)nk + (size_t)nk / 1000 + 4096) * 4);
       unsigned* flag = (unsigned*)ctx->flags.p;
       mask_flags<<<(nk + 255) / 256, 256, 0, s>>>(mask_k, cat.perm, nk, flag);
+      g_launches += 2;  // flags + compaction
       unsigned* tmp = (unsigned*)ctx->hist.p;  // reuse as scan scratch
       CK(scan_exclusive(flag, (size_t)nk, tmp, s));
       mask_compact<<<(nk + 255) / 256, 256, 0, s>>>(flag, mask_k, cat.perm, nk, (int*)ctx->centres.p,
@@ -336,6 +342,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       CK(cudaStreamSynchronize(s));
     } else {
       iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
+      ++g_launches;
       CK(cudaGetLastError());
     }
     tot_centres += n_cen;
@@ -409,6 +416,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     stats->pairs = (int64_t)pairs;
     stats->centres = tot_centres;
     stats->waves = tot_waves;
+    stats->launches = (int64_t)(g_launches - launches0);
     stats->ms_grid = ms_grid;
     stats->ms_gather = ms_gather;
     stats->ms_contract = ms_contract;
@@ -439,7 +447,7 @@ int ext4pcf_to_real_space(ext4pcf_ctx* ctx, const double* upsilon, int n_bins, i
 }
 
 int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radial_bins, int n_bins,
-                    int n_max, int n_phi, const double* ap_radii, int n_ap, const double* xi_pm, double* m4,
+                    int n_max, int n_phi, const double* ap_radii, int n_ap, const double* xi_acc, double* m4,
                     double* map4_eb, double* map4_disc) {
   if (!ctx) return EXT4PCF_E_INVALID_ARG;
   ctx->err.clear();
@@ -462,37 +470,38 @@ int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radia
   ENSURE(ctx->t_gam, (size_t)chunk * nph2 * 8 * 16);
   ENSURE(ctx->t_E, (size_t)(2 * n_max + 1) * n_phi * 16);
   ENSURE(ctx->t_part, (size_t)ntri * n_ap * 8 * 16);
-  // small buffer: xi_pm [nb*4], tb [nb], area [nb], ap [n_ap], m4 [n_ap*16], eb [n_ap*16], disc [n_ap*16]
-  const size_t small = (size_t)n_bins * 6 + n_ap * 49;
+  // small buffer: xi_acc [nb*6], tb [nb], area [nb], ap [n_ap], m4 [n_ap*16], eb [n_ap*16], disc [n_ap*16]
+  const size_t small = (size_t)n_bins * 8 + n_ap * 49;
   ENSURE(ctx->t_small, small * 8);
   std::vector<double> hs(small, 0.0);
-  double* h_xi = hs.data();
-  double* h_tb = h_xi + 4 * n_bins;
+  double* h_tb = hs.data() + 6 * n_bins;
   double* h_area = h_tb + n_bins;
   double* h_ap = h_area + n_bins;
   for (int b = 0; b < n_bins; ++b) {
     const double lo = radial_bins[b], hi = radial_bins[b + 1];
     h_tb[b] = (2.0 / 3.0) * (hi * hi * hi - lo * lo * lo) / (hi * hi - lo * lo);
     h_area[b] = 0.5 * (hi * hi - lo * lo);
-    if (xi_pm) for (int k = 0; k < 4; ++k) h_xi[4 * b + k] = xi_pm[4 * b + k];
   }
   for (int k = 0; k < n_ap; ++k) h_ap[k] = ap_radii[k];
   double* d_small = (double*)ctx->t_small.p;
   CK(cudaMemcpyAsync(d_small, hs.data(), small * 8, cudaMemcpyHostToDevice, s));
+  if (xi_acc)
+    CK(cudaMemcpyAsync(d_small, xi_acc, (size_t)n_bins * 6 * 8,
+                       is_device_ptr(xi_acc) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   CK(map4_partials(upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n_ap, (double*)ctx->t_E.p,
                    (double*)ctx->t_norm.p, (double*)ctx->t_gam.p, chunk, (double*)ctx->t_part.p, s));
-  double* d_m4 = d_small + 6 * n_bins + n_ap;
+  double* d_m4 = d_small + 8 * n_bins + n_ap;
   double* d_eb = d_m4 + 16 * n_ap;
   double* d_disc = d_eb + 16 * n_ap;
-  CK(map4_finish_launch((const double*)ctx->t_part.p, ntri, n_ap, xi_pm ? d_small : nullptr, d_small + 4 * n_bins,
-                        d_small + 5 * n_bins, n_bins, d_small + 6 * n_bins, d_m4, d_eb, d_disc, s));
+  CK(map4_finish_launch((const double*)ctx->t_part.p, ntri, n_ap, xi_acc ? d_small : nullptr, d_small + 6 * n_bins,
+                        d_small + 7 * n_bins, n_bins, d_small + 8 * n_bins, d_m4, d_eb, d_disc, s));
   std::vector<double> res((size_t)48 * n_ap);
   CK(cudaMemcpyAsync(res.data(), d_m4, res.size() * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   for (int k = 0; k < 16 * n_ap; ++k) {
     m4[k] += res[k];
     map4_eb[k] += res[16 * n_ap + k];
-    if (map4_disc && xi_pm) map4_disc[k] += res[32 * n_ap + k];
+    if (map4_disc && xi_acc) map4_disc[k] += res[32 * n_ap + k];
   }
   return EXT4PCF_OK;
 }

@@ -85,6 +85,9 @@ struct SortedCat {
   const float4* s4;       // (x_re, x_im, w, 0) as float
 };
 
+// kernels launched by this host thread (each launcher adds what it enqueues)
+extern thread_local long long g_launches;
+
 struct Bins {
   int nb;
   double e2[65];   // squared edges (double)

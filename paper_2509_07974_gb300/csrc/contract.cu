@@ -285,6 +285,7 @@ cudaError_t launch_contract(const Layout& L, const cplx_t<R>* rec, const cplx_t<
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   contract_cuda_core<R, NBT><<<9 * nn * nn, threads, smem, s>>>(L, rec, xw, T, ups);
+  ++g_launches;
   return cudaGetLastError();
 }
 
@@ -317,7 +318,11 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
   const int threads = max(64, (L.nb * L.nb + 31) / 32 * 32);
   const size_t smem = (size_t)kChunk * (1 + 2 * L.nb) * sizeof(cplx_t<R>);
   corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, T, corr);
-  if (xi_acc) xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, T, xi_acc);
+  ++g_launches;
+  if (xi_acc) {
+    xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, T, xi_acc);
+    ++g_launches;
+  }
   return cudaGetLastError();
 }
 
@@ -327,6 +332,7 @@ cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, 
   int blocks = (int)((total + 255) / 256);
   if (blocks > 65536) blocks = 65536;
   apply_corrections<<<blocks, 256, 0, s>>>(L, corr, ups);
+  ++g_launches;
   return cudaGetLastError();
 }
 

@@ -441,6 +441,7 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   if (e != cudaSuccess) return e;
   int grid = T;
   gather_kernel<R, MB><<<grid, kThreads, smem, s>>>(a, rec, xw);
+  ++g_launches;
   (void)sm_count;
   return cudaGetLastError();
 }

@@ -161,10 +161,12 @@ cudaError_t scan_exclusive(unsigned* data, size_t n, unsigned* tmp, cudaStream_t
   if (n == 0) return cudaSuccess;
   size_t nb = (n + kScanBlock - 1) / kScanBlock;
   scan_block<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, tmp);
+  ++g_launches;
   if (nb > 1) {
     cudaError_t e = scan_exclusive(tmp, nb, tmp + nb, s);
     if (e != cudaSuccess) return e;
     scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(data, n, tmp);
+    ++g_launches;
   }
   return cudaGetLastError();
 }
@@ -220,6 +222,7 @@ cudaError_t grid_bbox(const double* pos, int n, double* d_bbox, cudaStream_t s) 
   // partials go after the 4 result slots
   bbox_partial<<<nblk, 256, 0, s>>>(pos, n, d_bbox + 4);
   bbox_final<<<1, 32, 0, s>>>(d_bbox + 4, nblk, d_bbox);
+  g_launches += 2;
   return cudaGetLastError();
 }
 
@@ -235,9 +238,11 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
   out.p4 = gb.p4; out.s4 = gb.s4;
   if (n == 0) {
     fill_start_empty<<<(ncells + 256) / 256, 256, 0, s>>>(gb.cell_start, ncells);
+    ++g_launches;
     return cudaGetLastError();
   }
   make_keys<<<(n + 255) / 256, 256, 0, s>>>(pos, n, x0, y0, 1.0 / cell, ncx, ncy, gb.keys, gb.perm);
+  ++g_launches;
   int bits = 1;
   while ((1 << bits) < ncells) ++bits;
   const int ntiles = (n + kTile - 1) / kTile;
@@ -250,6 +255,7 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
     cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
     if (e != cudaSuccess) return e;
     radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
+    g_launches += 2;  // histogram + scatter
     int* t = kin; kin = kout; kout = t;
     t = vin; vin = vout; vout = t;
   }
@@ -258,6 +264,7 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
   build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, ncx, x0, y0, cell,
                                                (float)cell, want_f32, gb.px, gb.py, gb.xr, gb.xi,
                                                gb.w, gb.p4, gb.s4);
+  g_launches += 2;
   return cudaGetLastError();
 }
 

@@ -235,6 +235,7 @@ cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, i
   const int nn = 2 * N + 1;
   const int ntri = nb * nb * nb;
   angle_table<<<64, 256, 0, s>>>(N, nphi, reinterpret_cast<double2*>(E_scratch));
+  ++g_launches;
   const size_t smem = (size_t)(nn * nn + nn * nphi) * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(real_space_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -261,6 +262,7 @@ cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, i
     a.tri0 = t0; a.ntri = nt;
     map4_kernel<<<nt * n_ap, 128, 0, s>>>(a, reinterpret_cast<const double2*>(gam_chunk), stride,
                                           reinterpret_cast<double2*>(partial));
+    g_launches += 3;
   }
   return cudaGetLastError();
 }
@@ -324,12 +326,15 @@ __global__ void map4_finish(const double2* __restrict__ partial, int ntri, int n
       const double th = ap[ia];
       double Ar = 0, Ai = 0, Bp = 0;
       for (int b = 0; b < nb; ++b) {
+        // xi_+ = sum x^* G_0 / sum w W_0, xi_- = sum x G_-4 / sum w W_0
+        const double den = xipm[6 * b + 4];
+        if (den == 0.0) continue;
         const double x = tb[b] / th, g = exp(-0.25 * x * x);
         const double Tp = (x * x * x * x - 16.0 * x * x + 32.0) / 128.0 * g;
         const double Tm = x * x * x * x / 128.0 * g;
-        Bp += xipm[4 * b] * Tp * area[b] / (th * th);
-        Ar += xipm[4 * b + 2] * Tm * area[b] / (th * th);
-        Ai += xipm[4 * b + 3] * Tm * area[b] / (th * th);
+        Bp += xipm[6 * b] / den * Tp * area[b] / (th * th);
+        Ar += xipm[6 * b + 2] / den * Tm * area[b] / (th * th);
+        Ai += xipm[6 * b + 3] / den * Tm * area[b] / (th * th);
       }
       for (int code = 0; code < 16; ++code) {
         int be[4];
@@ -371,6 +376,7 @@ cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const 
                                double* d_m4, double* d_eb, double* d_disc, cudaStream_t s) {
   map4_finish<<<n_ap, 32, 0, s>>>(reinterpret_cast<const double2*>(partial), ntri, n_ap, d_xipm, d_tb,
                                   d_area, nb, d_ap, d_m4, d_eb, d_disc);
+  ++g_launches;
   return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int64), ("centres", ctypes.c_int64), ("waves", ctypes.c_int64),
-                ("ms_grid", ctypes.c_double), ("ms_gather", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("ms_grid", ctypes.c_double), ("ms_gather", ctypes.c_double),
                 ("ms_contract", ctypes.c_double), ("ms_correct", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
 
@@ -129,10 +129,10 @@ def ext4pcf_to_real_space(ctx, upsilon, n_bins, n_max, n_phi, gamma, norm) -> in
     return _check(ctx, rc)
 
 
-def ext4pcf_to_map4(ctx, upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n_ap, xi_pm,
+def ext4pcf_to_map4(ctx, upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n_ap, xi_acc,
                     m4, map4_eb, map4_disc) -> int:
     rc = load().ext4pcf_to_map4(ctx, _addr(upsilon), _addr(radial_bins), int(n_bins), int(n_max),
-                                int(n_phi), _addr(ap_radii), int(n_ap), _addr(xi_pm), _addr(m4),
+                                int(n_phi), _addr(ap_radii), int(n_ap), _addr(xi_acc), _addr(m4),
                                 _addr(map4_eb), _addr(map4_disc))
     return _check(ctx, rc)
 
@@ -201,7 +201,7 @@ class Estimator:
         ext4pcf_to_real_space(self.ctx, upsilon, nb, n_max, n_phi, gamma, norm)
         return gamma, norm
 
-    def to_map4(self, upsilon, radial_bins, n_phi, ap_radii, xi_pm=None):
+    def to_map4(self, upsilon, radial_bins, n_phi, ap_radii, xi_acc=None):
         import numpy as np
         edges = np.ascontiguousarray(np.asarray(radial_bins, dtype=np.float64))
         nb = edges.size - 1
@@ -211,7 +211,9 @@ class Estimator:
         m4 = np.zeros((n_ap, 8, 2))
         eb = np.zeros((n_ap, 16))
         disc = np.zeros((n_ap, 16))
-        xi = None if xi_pm is None else np.ascontiguousarray(np.asarray(xi_pm, dtype=np.float64))
+        xi = xi_acc
+        if xi is not None and not hasattr(xi, "data_ptr"):
+            xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64))
         ext4pcf_to_map4(self.ctx, upsilon, edges, nb, n_max, n_phi, ap, n_ap, xi, m4, eb, disc)
         return m4[..., 0] + 1j * m4[..., 1], eb, disc
 

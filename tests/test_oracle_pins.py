@@ -18,7 +18,10 @@ def rel_err(a, b):
     """|a-b| per element over max(|b|, rms floor) -- the floor is the rms over (n2, n3)
     of the reference for each (mu, Theta1, Theta2, Theta3)."""
     floor = np.sqrt(np.mean(np.abs(b) ** 2, axis=(1, 2), keepdims=True))
-    den = np.maximum(np.abs(b), floor)
+    # slabs that vanish in exact arithmetic hold only rounding residue: floor them at
+    # 1e-12 of the component's largest value
+    scale = np.abs(b).reshape(b.shape[0], -1).max(axis=1).reshape((-1,) + (1,) * (b.ndim - 1))
+    den = np.maximum(np.maximum(np.abs(b), floor), 1e-12 * scale)
     den = np.where(den > 0, den, 1.0)
     return np.abs(a - b) / den
 
