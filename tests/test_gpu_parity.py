@@ -12,8 +12,13 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "fp32": 1e-4}
 
 
-def rel_err(a, b):
+def rel_err(a, b, unc=None):
+    """Floor-relative error.  `unc` (the reference without multiple-counting corrections),
+    when given, also sets the floor: a corrected value is a difference of uncorrected
+    terms, so its rounding error scales with them."""
     floor = np.sqrt(np.mean(np.abs(b) ** 2, axis=(1, 2), keepdims=True))
+    if unc is not None:
+        floor = np.maximum(floor, np.sqrt(np.mean(np.abs(unc) ** 2, axis=(1, 2), keepdims=True)))
     # slabs that vanish in exact arithmetic hold only rounding residue: floor them at
     # 1e-12 of the component's largest value
     scale = np.abs(b).reshape(b.shape[0], -1).max(axis=1).reshape((-1,) + (1,) * (b.ndim - 1))
@@ -195,8 +200,9 @@ def test_extreme_shapes(torch_cuda, oracle, prec, nb, nmax):
     w = rng.uniform(0.5, 1.5, 60)
     edges = np.geomspace(0.4, 6.0, nb + 1)
     ref = oracle.measure(pos, sh, w, edges, nmax)
+    unc = oracle.measure(pos, sh, w, edges, nmax, corrections=False)
     got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, prec)
-    assert rel_err(got, ref).max() < TOL[prec]
+    assert rel_err(got, ref, unc).max() < TOL[prec]
 
 
 def test_invalid_arguments_are_rejected(torch_cuda):
