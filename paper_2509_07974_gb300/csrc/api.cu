@@ -67,6 +67,10 @@ struct ext4pcf_ctx {
   DBuf centres, flags, rec, xw, corr, counter, ncen;
   // transforms
   DBuf t_norm, t_gam, t_E, t_part, t_small;
+  // tensor-core contraction: work items (built once per shape) and the device status word
+  DBuf tc_items, status;
+  int tc_N = -1, tc_nb = -1;
+  size_t tc_items_bytes = 0;
   cudaEvent_t ev[8] = {};
 };
 
@@ -177,7 +181,8 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
                  &ctx->keys, &ctx->keys_alt, &ctx->perm, &ctx->perm_alt, &ctx->cell_start, &ctx->hist,
                  &ctx->px, &ctx->py, &ctx->xr, &ctx->xi, &ctx->w, &ctx->p4, &ctx->s4, &ctx->bbox,
                  &ctx->centres, &ctx->flags, &ctx->rec, &ctx->xw, &ctx->corr, &ctx->counter, &ctx->ncen,
-                 &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small};
+                 &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small, &ctx->tc_items,
+                 &ctx->status};
   for (DBuf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
@@ -281,6 +286,21 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   if (timing) CK(cudaEventRecord(ctx->ev[0], s));
   ENSURE(ctx->counter, 16);
   CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
+  const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16;
+  if (tc) {
+    if (ctx->tc_N != n_max || ctx->tc_nb != n_bins) {
+      std::vector<int4> items;
+      tc_build_items(L, items);
+      ENSURE(ctx->tc_items, items.size() * sizeof(int4));
+      CK(cudaMemcpy(ctx->tc_items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+      ctx->tc_items_bytes = items.size() * sizeof(int4);
+      ctx->tc_N = n_max;
+      ctx->tc_nb = n_bins;
+    }
+    ENSURE(ctx->status, 16);
+    CK(cudaMemsetAsync(ctx->status.p, 0, 4, s));
+  }
+  const long long timeout = ctx->cfg.timeout_cycles > 0 ? ctx->cfg.timeout_cycles : 20000000000LL;
   ENSURE(ctx->ncen, 16);
   ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
 
@@ -374,7 +394,8 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       } else if (prec == EXT4PCF_FP32) {
         CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, s));
       } else {
-        return fail(ctx, EXT4PCF_E_UNSUPPORTED, "tensor-core contraction not available");
+        CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, prec,
+                            ctx->tc_items.p, ctx->tc_items_bytes, (int*)ctx->status.p, timeout, s));
       }
       if (timing) CK(cudaEventRecord(ctx->ev[5], s));
       if (f64) {
@@ -403,6 +424,12 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       cudaEventElapsedTime(&g, ctx->ev[1], ctx->ev[2]);
       ms_grid += g;
     }
+  }
+  if (tc) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st != 0) return fail(ctx, EXT4PCF_E_TIMEOUT, "a bounded device-side wait expired in the contraction");
   }
   if (host_ups) CK(cudaMemcpyAsync(upsilon, d_ups, ups_bytes * n_cat, cudaMemcpyDeviceToHost, s));
   if (host_xi) CK(cudaMemcpyAsync(xi_acc, d_xi, xi_bytes * n_cat, cudaMemcpyDeviceToHost, s));

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "ext4pcf.h"
 
@@ -136,5 +137,6 @@ cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* x
                              double* ups, int precision, void* scratch, size_t scratch_bytes,
                              int* status, long long timeout, cudaStream_t s);
 size_t contract_tc_scratch(const Layout& L, int T);
+void tc_build_items(const Layout& L, std::vector<int4>& items);
 
 }  // namespace ext4pcf

@@ -1,15 +1,582 @@
-// Tensor-core (tcgen05) contraction of a wave: not available in this build yet.
+// Tensor-core contraction of a wave (tcgen05, sm_103a).
+//
+// For fixed s = n2 + n3 every natural component factorises as
+//   Upsilon_mu[n2,n3](Th1,Th2,Th3) = sum_i A_i^mu[s](Th1) * KR_i[n2,n3](Th2,Th3),
+//   KR_i = xt_i * B_i[n2](Th2) * C_i[n3](Th3)   (a Khatri-Rao product over the centre i),
+// i.e. a complex GEMM over the centre index.  Components that share KR (mu = 0 and 2;
+// mu = 1 and 5) share the GEMM.  Mapping onto tcgen05.mma (M = 128, K along centres):
+//   * A operand (TMEM): 128 KR rows (n2, Th2, Th3) of one s.  Row r of the tile is TMEM
+//     lane r; centre i occupies K elements (2i, 2i+1) = (re, im).  Eight producer warps
+//     form KR on the CUDA cores and write it with tcgen05.st (warp w owns lanes
+//     32 (w % 4) ..; warps w and w + 4 split the centres of a stage).
+//   * B operand (shared memory, K-major, 128-byte swizzle): column (mu, Th1, re|im) holds
+//     the real embedding of A_i^mu(Th1): K rows (2i, 2i+1) = (Ar, -Ai) for the real output
+//     and (Ai, Ar) for the imaginary output, so that D = A_op B_op is the complex product.
+//   * D (TMEM, FP32): 128 rows x (2 * #mu * nb, padded to 16) columns, accumulated over the
+//     wave's centres; the epilogue adds it into the FP64 output.
+// Precision: BF16x3 splits every operand into bf16 hi + lo and accumulates
+// hi*hi + hi*lo + lo*hi (kind::f16); TF32 uses one kind::tf32 pass.
+// Pipeline: 4 stages of 32 centres; full/empty mbarriers between the producers and the one
+// thread that issues the MMAs; tcgen05.commit releases a stage.  Every wait is bounded by
+// a clock budget; on expiry the kernel records an error code and runs to its end.
+#include <vector>
+
 #include "common.cuh"
 
 namespace ext4pcf {
 
-bool tc_supported(const Layout&, int) { return false; }
+namespace {
 
-size_t contract_tc_scratch(const Layout&, int) { return 0; }
+constexpr int kStages = 4;
+constexpr int kStageCentres = 32;
+constexpr int kProducerWarps = 8;
+constexpr int kProducers = kProducerWarps * 32;
+constexpr int kThreads = kProducers + 32;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kDCols = 128;          // D region: two 64-column buffers
+constexpr int kStageCols = 64;       // per stage: A hi [0, 32) + lo [32, 64) (bf16), or 64 fp32
+constexpr int kMaxNpad = 64;         // B columns: 2 * #mu * nb padded to 16 (nb <= 16)
 
-cudaError_t contract_wave_tc(const Layout&, const float2*, const float2*, int, double*, int, void*, size_t,
-                             int*, long long, cudaStream_t) {
-  return cudaErrorNotSupported;
+struct KF {
+  signed char arr, sgn, off, conj;  // arr 0: G, 1: W; index n = sgn * var + off
+};
+struct KRType {
+  signed char xconj;  // 0: x, 1: x^*, 2: w
+  KF B, C;            // row factors B(Th2; n2), C(Th3; n3)
+  signed char nmu;
+  signed char mu[2];
+  KF A[2];            // column factors A(Th1; s)
+};
+
+// Khatri-Rao row types and the components that use them
+__constant__ KRType kKR[7] = {
+    {0, {0, -1, -2, 0}, {0, -1, -3, 0}, 2, {0, 2}, {{0, 1, -3, 0}, {0, -1, -1, 1}}},
+    {0, {0, 1, -2, 1}, {0, -1, -3, 0}, 1, {3, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},
+    {0, {0, -1, -2, 0}, {0, 1, -1, 1}, 1, {4, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},
+    {1, {0, -1, -2, 0}, {0, -1, -1, 0}, 2, {1, 5}, {{0, 1, -1, 0}, {0, -1, -3, 1}}},
+    {1, {0, 1, -2, 1}, {0, -1, -1, 0}, 1, {6, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},
+    {1, {0, -1, -2, 0}, {0, 1, -3, 1}, 1, {7, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},
+    {2, {1, -1, 0, 0}, {1, -1, 0, 0}, 1, {8, 0}, {{1, 1, 0, 0}, {0, 0, 0, 0}}},
+};
+constexpr int kKRTypes = 7;
+__host__ __device__ constexpr int kr_nmu(int t) { return (t == 0 || t == 3) ? 2 : 1; }
+
+struct TcArgs {
+  Layout L;
+  const float2* rec;
+  const float2* xw;
+  int T;
+  double* ups;
+  const int4* items;  // (type, s, row0, nrows)
+  int n_items;
+  long long timeout;
+  int* status;
+};
+
+// ------------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return r != 0;
+}
+// bounded wait: false when the clock budget ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long budget) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(ta)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// K-major operand in shared memory, 128-byte swizzle: rows of 128 bytes, 8-row groups of
+// 1024 bytes (stride-dimension offset), 16-byte chunks XOR-ed with the row index mod 8.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// instruction descriptor: D f32, A/B format code fmt, K-major A and B, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+// bf16 hi/lo split of a pair (re, im) packed as bf16x2 (re in the low half)
+__device__ __forceinline__ void split_bf16(float re, float im, uint32_t& hi, uint32_t& lo) {
+  uint32_t h;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(im), "f"(re));
+  const float hr = __uint_as_float(h << 16), hi_ = __uint_as_float(h & 0xFFFF0000u);
+  uint32_t l;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(im - hi_), "f"(re - hr));
+  hi = h;
+  lo = l;
+}
+
+__device__ __forceinline__ float2 fetch_factor(const float2* __restrict__ rc, const Layout& L, KF f, int var, int b) {
+  const int n = f.sgn * var + f.off;
+  float2 v;
+  bool cj = f.conj != 0;
+  if (f.arr == 0) {
+    v = rc[L.G(n, b)];
+  } else {
+    v = rc[L.W(n >= 0 ? n : -n, b)];
+    cj ^= (n < 0);
+  }
+  if (cj) v.y = -v.y;
+  return v;
+}
+__device__ __forceinline__ float2 centre_x(const float2* __restrict__ xw, int c, int xconj) {
+  float2 x = xw[2 * (size_t)c];
+  if (xconj == 1) x.y = -x.y;
+  if (xconj == 2) x = xw[2 * (size_t)c + 1];
+  return x;
+}
+
+// byte offset of 32-bit word (row n, word j) in a K-major SW128 tile whose rows hold
+// 32 words (128 bytes) per K-atom; tiles of several K-atoms are atom-major.
+__device__ __forceinline__ uint32_t sw128_word_off(int n, int j, int npad) {
+  const int atom = j >> 5, jj = j & 31;
+  const int chunk = jj >> 2, within = (jj & 3) << 2;
+  return (uint32_t)(atom * (npad >> 3) * 1024 + (n >> 3) * 1024 + (n & 7) * 128 + ((chunk ^ (n & 7)) << 4) + within);
+}
+
+// One staged block of a per-centre record: `len` consecutive complex values starting at
+// record element `rec_off`; `lo` is the first multipole index (n for G, m = |n| for W).
+struct Blk {
+  int rec_off, len, lo, is_w;
+};
+
+__device__ __forceinline__ Blk make_blk(const Layout& L, KF f, int va, int vb) {
+  int nlo = f.sgn > 0 ? va + f.off : -vb + f.off;
+  int nhi = f.sgn > 0 ? vb + f.off : -va + f.off;
+  Blk b;
+  b.is_w = f.arr;
+  if (f.arr == 0) {
+    b.lo = nlo;
+    b.rec_off = L.G(nlo, 0);
+    b.len = (nhi - nlo + 1) * L.nb;
+  } else {
+    int mlo, mhi;
+    if (nlo >= 0) { mlo = nlo; mhi = nhi; }
+    else if (nhi <= 0) { mlo = -nhi; mhi = -nlo; }
+    else { mlo = 0; mhi = max(-nlo, nhi); }
+    b.lo = mlo;
+    b.rec_off = L.W(mlo, 0);
+    b.len = (mhi - mlo + 1) * L.nb;
+  }
+  return b;
+}
+// staged index (within the block) and conjugation of factor f at variable v, bin b
+__device__ __forceinline__ int blk_index(const Blk& k, KF f, int v, int b, int nb, bool& cj) {
+  const int n = f.sgn * v + f.off;
+  cj = f.conj != 0;
+  if (!k.is_w) return (n - k.lo) * nb + b;
+  cj ^= (n < 0);
+  return ((n < 0 ? -n : n) - k.lo) * nb + b;
+}
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory"); }
+
+constexpr int kStageBufs = 3;     // staging ring: stage k + 2 is fetched while k is formed
+// staged complex values per centre: x, w, the B and C blocks of at most the tile's n2 values
+// (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two A rows
+__host__ __device__ inline int stage_values(int nb, int N) {
+  int rows = 128 / (nb * nb) + 2;
+  if (rows > 2 * N + 1) rows = 2 * N + 1;
+  return 2 + 2 * rows * nb + 2 * nb;
+}
+constexpr int kPromote = 8;       // stages per TMEM partial sum (256 centres)
+constexpr int kDBuf = 64;         // two D buffers of 64 columns (npad <= 64)
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs args) {
+  constexpr bool kBF16 = PREC == EXT4PCF_SPLIT_BF16;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
+  const Layout L = args.L;
+  const int nb = L.nb, N = L.N, nn = 2 * N + 1, nb2 = nb * nb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int tile_bytes = kMaxNpad * 128;   // one 128-byte-wide K-atom of B (npad <= 64)
+  constexpr int stage_bytes = 2 * tile_bytes;  // hi + lo, or two fp32 K-atoms
+  const int sc_max = stage_values(nb, N);      // staged complex values per centre (upper bound)
+  float2* stg = reinterpret_cast<float2*>(sm + kStages * stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(stg + kStageBufs * kStageCentres * sc_max);
+  uint64_t* empty = full + kStages;
+  uint64_t* dfull = empty + kStages;   // [2]: a D buffer holds a finished partial sum
+  uint64_t* dempty = dfull + 2;        // [2]: the producers have read it
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dempty + 2);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&full[k], kProducers);
+      mbar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&dfull[k], 1);
+      mbar_init(&dempty[k], kProducers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long budget = args.timeout;
+  const int nstage = (args.T + kStageCentres - 1) / kStageCentres;
+  const int nsub = (nstage + kPromote - 1) / kPromote;
+  int err = 0;
+
+  long long gk = 0;  // stages handled by this CTA (phases of full / empty)
+  long long gs = 0;  // partial sums handled by this CTA (phases of dfull / dempty)
+  for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+    const int4 item = args.items[it];
+    const int type = item.x, s = item.y, row0 = item.z, nrows = item.w;
+    const KRType kr = kKR[type];
+    const int nmu = kr.nmu;
+    const int ncols = 2 * nmu * nb;
+    const int npad = (ncols + 15) / 16 * 16;
+    const int n2a = max(-N, s - N);
+    // the tile's rows span n2 in [t2a, t2b]; staged blocks of every centre record:
+    // B(n2), C(n3 = s - n2), A_0(s), A_1(s)
+    const int t2a = n2a + row0 / nb2, t2b = n2a + (row0 + nrows - 1) / nb2;
+    Blk blk[4];
+    blk[0] = make_blk(L, kr.B, t2a, t2b);
+    blk[1] = make_blk(L, kr.C, s - t2b, s - t2a);
+    blk[2] = make_blk(L, kr.A[0], s, s);
+    blk[3] = nmu > 1 ? make_blk(L, kr.A[1], s, s) : Blk{0, 0, 0, 0};
+    int bstart[4];
+    int sc = 2;
+    for (int k = 0; k < 4; ++k) { bstart[k] = sc; sc += blk[k].len; }
+    if (warp < kProducerWarps) {
+      // ------------------------------------------------------------------ producers
+      const int grp = warp & 3, half = warp >> 2;
+      const int rl = grp * 32 + lane;  // tile row = TMEM lane
+      const bool row_ok = rl < nrows;
+      const int rr = row0 + (row_ok ? rl : 0);
+      const int n2 = n2a + rr / nb2, b2 = (rr / nb) % nb, b3 = rr % nb, n3 = s - n2;
+      bool cjB, cjC;
+      const int iB = bstart[0] + blk_index(blk[0], kr.B, n2, b2, nb, cjB);
+      const int iC = bstart[1] + blk_index(blk[1], kr.C, n3, b3, nb, cjC);
+      // B-operand row of this thread: column n, 8 centres [8 q, 8 q + 8)
+      const int bn = tid >> 2, bq = tid & 3;
+      const bool bcol_ok = bn < ncols;
+      int iA = 0, bo = 0;
+      bool cjA = false;
+      if (bcol_ok) {
+        const int g = bn / (2 * nb), b1 = (bn >> 1) % nb;
+        bo = bn & 1;
+        iA = bstart[2 + g] + blk_index(blk[2 + g], kr.A[g], s, b1, nb, cjA);
+      }
+      // copy of one stage's record slices (8 threads per centre)
+      auto issue = [&](int k) {
+        if (k < nstage) {
+          float2* dst = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
+          const int i = tid >> 3, sub = tid & 7, c = k * kStageCentres + i;
+          if (c < args.T) {
+            float2* d = dst + i * sc;
+            if (sub < 2) cp_async8(d + sub, args.xw + 2 * (size_t)c + sub);
+            const float2* rc = args.rec + (size_t)c * L.rec;
+            for (int b = 0; b < 4; ++b)
+              for (int e = sub; e < blk[b].len; e += 8) cp_async8(d + bstart[b] + e, rc + blk[b].rec_off + e);
+          }
+        }
+        cp_async_commit();
+      };
+      issue(0);
+      issue(1);
+      float accD[32];  // FP32 sums of the promoted partials: this thread's row, 32 columns
+#pragma unroll
+      for (int j = 0; j < 32; ++j) accD[j] = 0.f;
+      auto promote = [&](long long g) {  // read partial sum g from its D buffer
+        const int buf = (int)(g & 1);
+        if (!mbar_wait(&dfull[buf], (uint32_t)((g >> 1) & 1), budget)) err = 1;
+        tc_fence_after();
+        const uint32_t dcol = tmem + ((uint32_t)(grp * 32) << 16) + buf * kDBuf + half * 32;
+        uint32_t v[32];
+        tmem_ld16(dcol, v);
+        tmem_ld16(dcol + 16, v + 16);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) accD[j] += __uint_as_float(v[j]);
+        tc_fence_before();
+        mbar_arrive(&dempty[buf]);
+      };
+      const long long gs0 = gs;
+      for (int k = 0; k < nstage; ++k, ++gk) {
+        const int slot = (int)(gk % kStages);
+        const uint32_t ph = (uint32_t)((gk / kStages) & 1);
+        cp_async_wait<1>();
+        producers_sync();
+        issue(k + 2);
+        const float2* st = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
+        const int c0 = k * kStageCentres;
+        if (!mbar_wait(&empty[slot], ph ^ 1u, budget)) err = 1;
+        tc_fence_after();
+        // B operand (shared memory, swizzled): real embedding of A(Th1) for 8 centres
+        unsigned char* bt = sm + slot * stage_bytes;
+        if (bn < npad) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int i = bq * 8 + j;
+            float v0 = 0.f, v1 = 0.f;
+            if (bcol_ok && c0 + i < args.T) {
+              float2 a = st[i * sc + iA];
+              if (cjA) a.y = -a.y;
+              v0 = bo ? a.y : a.x;
+              v1 = bo ? a.x : -a.y;
+            }
+            if (kBF16) {
+              uint32_t h, l;
+              split_bf16(v0, v1, h, l);
+              const uint32_t off = sw128_word_off(bn, i, kMaxNpad);
+              *reinterpret_cast<uint32_t*>(bt + off) = h;
+              *reinterpret_cast<uint32_t*>(bt + tile_bytes + off) = l;
+            } else {
+              *reinterpret_cast<float*>(bt + sw128_word_off(bn, 2 * i, kMaxNpad)) = v0;
+              *reinterpret_cast<float*>(bt + sw128_word_off(bn, 2 * i + 1, kMaxNpad)) = v1;
+            }
+          }
+        }
+        // A operand (TMEM): this row's Khatri-Rao values for 16 centres
+        uint32_t w[32];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int i = half * 16 + j;
+          float kr_re = 0.f, kr_im = 0.f;
+          if (row_ok && c0 + i < args.T) {
+            const float2* sp = st + i * sc;
+            float2 x = sp[kr.xconj == 2 ? 1 : 0];
+            if (kr.xconj == 1) x.y = -x.y;
+            float2 bv = sp[iB], cv = sp[iC];
+            if (cjB) bv.y = -bv.y;
+            if (cjC) cv.y = -cv.y;
+            const float xbr = x.x * bv.x - x.y * bv.y, xbi = x.x * bv.y + x.y * bv.x;
+            kr_re = xbr * cv.x - xbi * cv.y;
+            kr_im = xbr * cv.y + xbi * cv.x;
+          }
+          if (kBF16) {
+            split_bf16(kr_re, kr_im, w[j], w[16 + j]);
+          } else {
+            w[2 * j] = __float_as_uint(kr_re);
+            w[2 * j + 1] = __float_as_uint(kr_im);
+          }
+        }
+        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * kStageCols;
+        if (kBF16) {
+          tmem_st16(acol + half * 16, w);
+          tmem_st16(acol + 32 + half * 16, w + 16);
+        } else {
+          tmem_st16(acol + half * 32, w);
+          tmem_st16(acol + half * 32 + 16, w + 16);
+        }
+        fence_async_smem();
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&full[slot]);
+        // a partial sum finished one promotion block ago is read while the MMAs run on
+        if ((k % kPromote) == kPromote - 1 && k / kPromote >= 1) promote(gs0 + k / kPromote - 1);
+      }
+      cp_async_wait<0>();
+      // the remaining partial sums of this item
+      // in the loop, partials 0 .. F-2 were read (F = complete promotion blocks)
+      const int read_in_loop = max(0, nstage / kPromote - 1);
+      const long long first_left = gs0 + read_in_loop;
+      const long long nleft = nsub - read_in_loop;
+      for (long long g = first_left; g < first_left + nleft; ++g) promote(g);
+      gs = gs0 + nsub;
+      // ------------------------------------------------------------------ epilogue
+      if (row_ok) {
+        const size_t nb3 = (size_t)nb2 * nb;
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+          const int n = half * 32 + j;
+          if (n < ncols) {
+            const int g = n / (2 * nb), b1 = (n >> 1) % nb;
+            const int mu = kr.mu[g];
+            const size_t o = ((((size_t)mu * nn + (n2 + N)) * nn + (n3 + N)) * nb3) + (size_t)b1 * nb2 +
+                             (size_t)b2 * nb + b3;
+            double* p = args.ups + 2 * o;
+            p[0] += (double)accD[j];
+            p[1] += (double)accD[j + 1];
+          }
+        }
+      }
+      producers_sync();
+    } else {
+      // ------------------------------------------------------------------ MMA issuer
+      if (lane == 0) {
+        const uint32_t id = kBF16 ? idesc(1u, npad) : idesc(2u, npad);
+        for (int k = 0; k < nstage; ++k, ++gk) {
+          const int slot = (int)(gk % kStages);
+          const uint32_t ph = (uint32_t)((gk / kStages) & 1);
+          const long long g = gs + k / kPromote;
+          const int buf = (int)(g & 1);
+          const bool first = (k % kPromote) == 0;
+          if (first && g >= 2) {
+            if (!mbar_wait(&dempty[buf], (uint32_t)(((g >> 1) - 1) & 1), budget)) err = 1;
+          }
+          if (!mbar_wait(&full[slot], ph, budget)) err = 1;
+          tc_fence_after();
+          const uint32_t d = tmem + buf * kDBuf;
+          const uint32_t a0 = tmem + kDCols + slot * kStageCols;
+          const uint32_t b0 = saddr(sm + slot * stage_bytes);
+          if (kBF16) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // K = 16 bf16 = 8 centres per MMA
+              const uint64_t bh = desc_sw128(b0 + q * 32), bl = desc_sw128(b0 + tile_bytes + q * 32);
+              mma_f16(d, a0 + q * 8, bh, id, (!first || q > 0) ? 1u : 0u);
+              mma_f16(d, a0 + q * 8, bl, id, 1u);
+              mma_f16(d, a0 + 32 + q * 8, bh, id, 1u);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {  // K = 8 fp32 = 4 centres per MMA
+              const uint64_t b = desc_sw128(b0 + (q >> 2) * tile_bytes + (q & 3) * 32);
+              mma_tf32(d, a0 + q * 8, b, id, (!first || q > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[slot]);
+          if ((k % kPromote) == kPromote - 1 || k == nstage - 1) mma_commit(&dfull[buf]);
+        }
+      } else {
+        gk += nstage;
+      }
+      gs += nsub;
+      __syncwarp();
+    }
+  }
+  // drain: the last partial sum was read by the producers, so no MMA is in flight
+  if (err) atomicExch(args.status, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+size_t tc_smem_bytes(int nb, int N) {
+  return (size_t)kStages * 2 * kMaxNpad * 128 + (size_t)kStageBufs * kStageCentres * stage_values(nb, N) * 8 + 1024 +
+         256;
+}
+
+}  // namespace
+
+bool tc_supported(const Layout& L, int precision) {
+  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32) return false;
+  return 4 * L.nb <= kMaxNpad && L.nb >= 1 && tc_smem_bytes(L.nb, L.N) <= 227 * 1024;
+}
+
+void tc_build_items(const Layout& L, std::vector<int4>& items) {
+  items.clear();
+  const int N = L.N, nb2 = L.nb * L.nb;
+  for (int t = 0; t < kKRTypes; ++t)
+    for (int s = -2 * N; s <= 2 * N; ++s) {
+      const int lo = s - N > -N ? s - N : -N, hi = s + N < N ? s + N : N;
+      const int rows = (hi - lo + 1) * nb2;
+      for (int r0 = 0; r0 < rows; r0 += 128) items.push_back(make_int4(t, s, r0, rows - r0 < 128 ? rows - r0 : 128));
+    }
+}
+
+size_t contract_tc_scratch(const Layout& L, int) {
+  std::vector<int4> it;
+  tc_build_items(L, it);
+  return it.size() * sizeof(int4);
+}
+
+cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, double* ups,
+                             int precision, void* scratch, size_t scratch_bytes, int* status, long long timeout,
+                             cudaStream_t s) {
+  if (T <= 0) return cudaSuccess;
+  // items are written once into scratch by the caller (tc_upload_items); count them here
+  const int n_items = (int)(scratch_bytes / sizeof(int4));
+  TcArgs a;
+  a.L = L; a.rec = rec; a.xw = xw; a.T = T; a.ups = ups;
+  a.items = static_cast<const int4*>(scratch); a.n_items = n_items;
+  a.timeout = timeout; a.status = status;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = tc_smem_bytes(L.nb, L.N);
+  cudaError_t e;
+  if (precision == EXT4PCF_SPLIT_BF16) {
+    e = cudaFuncSetAttribute(contract_tc_kernel<EXT4PCF_SPLIT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    contract_tc_kernel<EXT4PCF_SPLIT_BF16><<<sms, kThreads, smem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(contract_tc_kernel<EXT4PCF_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    contract_tc_kernel<EXT4PCF_TF32><<<sms, kThreads, smem, s>>>(a);
+  }
+  ++g_launches;
+  return cudaGetLastError();
 }
 
 }  // namespace ext4pcf
