@@ -128,9 +128,16 @@ class ClockSampler:
 
 
 def make_workload(seed_offset=0, n=None):
+    """The 2e6-galaxy GRF mock, or (n given) a smaller patch at the same density."""
     import synth
     c = dict(synth.GRF2E6)
-    pos, sh, w = synth.grf_catalog(n or c["n"], c["side"], c["seed"] + seed_offset, grid=c["grid"])
+    if n and n != c["n"]:
+        f = (n / c["n"]) ** 0.5
+        c["side"] = c["side"] * f
+        c["grid"] = max(256, int(2 ** round(np.log2(c["grid"] * f))))
+        c["n"] = n
+        c["name"] = "GRF %.3g gal, %.0f'x%.0f' (same density), 10 log bins 0.5'-40', n_max=20" % (n, c["side"], c["side"])
+    pos, sh, w = synth.grf_catalog(c["n"], c["side"], c["seed"] + seed_offset, grid=c["grid"])
     edges = synth.log_edges(c["lo"], c["hi"], c["nb"])
     return pos, sh, w, edges, c["nmax"], c
 
@@ -200,7 +207,7 @@ def run_reference(args):
     world, rank, _ = dist_setup(False)
     if rank != 0:
         return
-    pos, sh, w, edges, nmax, c = make_workload()
+    pos, sh, w, edges, nmax, c = make_workload(n=args.n_gal)
     n_c = args.oracle_centres
     mask, _, _ = oracle_sample(pos, sh, w, edges, nmax, n_c)  # warm-up build and page-in
     pairs = pairs_of_mask(pos, edges, mask)
@@ -236,7 +243,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     build.build()
     pk = peaks()
-    pos, sh, w, edges, nmax, c = make_workload(seed_offset=rank)
+    pos, sh, w, edges, nmax, c = make_workload(seed_offset=rank, n=args.n_gal)
     nb = len(edges) - 1
     tp = torch.tensor(pos, device=dev)
     ts = torch.tensor(sh, device=dev)
@@ -397,6 +404,8 @@ def main():
     ap.add_argument("--oracle-centres", type=int, default=2000)
     ap.add_argument("--fp64-centres", type=int, default=4096)
     ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--n-gal", type=int, default=None,
+                    help="smaller catalogue at the same density (profiling); default 2e6")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
