@@ -6,14 +6,18 @@
 // i.e. a complex GEMM over the centre index.  Components that share KR (mu = 0 and 2;
 // mu = 1 and 5) share the GEMM.  Mapping onto tcgen05.mma (M = 128, K along centres):
 //   * A operand (TMEM): 128 KR rows (n2, Th2, Th3) of one s.  Row r of the tile is TMEM
-//     lane r; centre i occupies K elements (2i, 2i+1) = (re, im).  Eight producer warps
+//     lane r; centre i occupies K elements (2i, 2i+1) = (re, im).  Sixteen producer warps
 //     form KR on the CUDA cores and write it with tcgen05.st (warp w owns lanes
-//     32 (w % 4) ..; warps w and w + 4 split the centres of a stage).
+//     32 (w % 4) ..; the four warps of a lane group split the 32 centres of a stage).
+//     Each stage's record slices are staged in shared memory with cp.async two stages
+//     ahead, and x~ B is formed once per (centre, n2, Th2) before the rows are built.
 //   * B operand (shared memory, K-major, 128-byte swizzle): column (mu, Th1, re|im) holds
 //     the real embedding of A_i^mu(Th1): K rows (2i, 2i+1) = (Ar, -Ai) for the real output
 //     and (Ai, Ar) for the imaginary output, so that D = A_op B_op is the complex product.
-//   * D (TMEM, FP32): 128 rows x (2 * #mu * nb, padded to 16) columns, accumulated over the
-//     wave's centres; the epilogue adds it into the FP64 output.
+//   * D (TMEM, FP32): 128 rows x (2 * #mu * nb, padded to 16) columns.  Every 256 centres the
+//     partial sum is promoted out of TMEM into FP32 registers (two D buffers alternate, so
+//     the MMAs run on meanwhile); the long FP32 accumulation inside the tensor core would
+//     otherwise lose bits.  The epilogue adds the sums into the FP64 output.
 // Precision: BF16x3 splits every operand into bf16 hi + lo and accumulates
 // hi*hi + hi*lo + lo*hi (kind::f16); TF32 uses one kind::tf32 pass.
 // Pipeline: 4 stages of 32 centres; full/empty mbarriers between the producers and the one
@@ -29,7 +33,7 @@ namespace {
 
 constexpr int kStages = 4;
 constexpr int kStageCentres = 32;
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
 constexpr int kThreads = kProducers + 32;
 constexpr uint32_t kTmemCols = 512;
@@ -112,6 +116,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t* v) {
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
       "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
       : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t* v) {
   asm volatile(
@@ -241,15 +250,17 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory"); }
 
 constexpr int kStageBufs = 3;     // staging ring: stage k + 2 is fetched while k is formed
-// staged complex values per centre: x, w, the B and C blocks of at most the tile's n2 values
-// (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two A rows
+// staged complex values per centre: x, w, a zero, the B and C blocks of at most the tile's
+// n2 values (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two
+// A rows; rounded up to an odd count so that consecutive centres fall in different banks
 __host__ __device__ inline int stage_values(int nb, int N) {
   int rows = 128 / (nb * nb) + 2;
   if (rows > 2 * N + 1) rows = 2 * N + 1;
-  return 2 + 2 * rows * nb + 2 * nb;
+  return (3 + 2 * rows * nb + 2 * nb) | 1;
 }
 constexpr int kPromote = 8;       // stages per TMEM partial sum (256 centres)
 constexpr int kDBuf = 64;         // two D buffers of 64 columns (npad <= 64)
+constexpr int kQuarter = kStageCentres / (kProducerWarps / 4);  // centres per producer warp
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs args) {
@@ -314,59 +325,72 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
     blk[2] = make_blk(L, kr.A[0], s, s);
     blk[3] = nmu > 1 ? make_blk(L, kr.A[1], s, s) : Blk{0, 0, 0, 0};
     int bstart[4];
-    int sc = 2;
+    int sc = 3;
     for (int k = 0; k < 4; ++k) { bstart[k] = sc; sc += blk[k].len; }
+    sc |= 1;
     if (warp < kProducerWarps) {
       // ------------------------------------------------------------------ producers
-      const int grp = warp & 3, half = warp >> 2;
+      const int grp = warp & 3, quarter = warp >> 2;
       const int rl = grp * 32 + lane;  // tile row = TMEM lane
       const bool row_ok = rl < nrows;
       const int rr = row0 + (row_ok ? rl : 0);
       const int n2 = n2a + rr / nb2, b2 = (rr / nb) % nb, b3 = rr % nb, n3 = s - n2;
+      // staged indices of this row's factors (index 2 is a zero: rows past the tile);
+      // the B block holds x~ B after the per-stage product below, conjugated per row if
+      // the factor is W at a negative index (x~ = w is real there)
       bool cjB, cjC;
-      const int iB = bstart[0] + blk_index(blk[0], kr.B, n2, b2, nb, cjB);
-      const int iC = bstart[1] + blk_index(blk[1], kr.C, n3, b3, nb, cjC);
-      // B-operand row of this thread: column n, 8 centres [8 q, 8 q + 8)
-      const int bn = tid >> 2, bq = tid & 3;
-      const bool bcol_ok = bn < ncols;
-      int iA = 0, bo = 0;
-      bool cjA = false;
-      if (bcol_ok) {
+      int iB = bstart[0] + blk_index(blk[0], kr.B, n2, b2, nb, cjB);
+      int iC = bstart[1] + blk_index(blk[1], kr.C, n3, b3, nb, cjC);
+      const float sgnB = (kr.B.arr == 1 && cjB) ? -1.f : 1.f;
+      const float sgnC = cjC ? -1.f : 1.f;
+      if (!row_ok) { iB = 2; iC = 2; }
+      // B-operand words of this thread: column bn, centres [8 bq, 8 bq + 8)
+      const int bn = tid >> 3, bq = tid & 7;  // 64 columns x 8 groups of 4 centres
+      int iA = 2;
+      int bo = 0;
+      float sgnA = 1.f;
+      if (bn < ncols) {
         const int g = bn / (2 * nb), b1 = (bn >> 1) % nb;
+        bool cjA;
         bo = bn & 1;
         iA = bstart[2 + g] + blk_index(blk[2 + g], kr.A[g], s, b1, nb, cjA);
+        sgnA = cjA ? -1.f : 1.f;
       }
-      // copy of one stage's record slices (8 threads per centre)
+      const int xsel = kr.xconj == 2 ? 1 : 0;
+      const float xsgn = kr.xconj == 1 ? -1.f : 1.f;
+      const float bsgn = (kr.B.arr == 0 && kr.B.conj) ? -1.f : 1.f;
+      // copy one stage's record slices (16 threads per centre); tails are zero-filled
       auto issue = [&](int k) {
         if (k < nstage) {
           float2* dst = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
-          const int i = tid >> 3, sub = tid & 7, c = k * kStageCentres + i;
+          const int i = tid >> 4, sub = tid & 15, c = k * kStageCentres + i;
+          float2* d = dst + i * sc;
           if (c < args.T) {
-            float2* d = dst + i * sc;
             if (sub < 2) cp_async8(d + sub, args.xw + 2 * (size_t)c + sub);
+            if (sub == 2) d[2] = make_float2(0.f, 0.f);
             const float2* rc = args.rec + (size_t)c * L.rec;
             for (int b = 0; b < 4; ++b)
-              for (int e = sub; e < blk[b].len; e += 8) cp_async8(d + bstart[b] + e, rc + blk[b].rec_off + e);
+              for (int e = sub; e < blk[b].len; e += 16) cp_async8(d + bstart[b] + e, rc + blk[b].rec_off + e);
+          } else {
+            for (int e = sub; e < sc; e += 16) d[e] = make_float2(0.f, 0.f);
           }
         }
         cp_async_commit();
       };
       issue(0);
       issue(1);
-      float accD[32];  // FP32 sums of the promoted partials: this thread's row, 32 columns
+      float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
 #pragma unroll
-      for (int j = 0; j < 32; ++j) accD[j] = 0.f;
+      for (int j = 0; j < 16; ++j) accD[j] = 0.f;
       auto promote = [&](long long g) {  // read partial sum g from its D buffer
         const int buf = (int)(g & 1);
         if (!mbar_wait(&dfull[buf], (uint32_t)((g >> 1) & 1), budget)) err = 1;
         tc_fence_after();
-        const uint32_t dcol = tmem + ((uint32_t)(grp * 32) << 16) + buf * kDBuf + half * 32;
-        uint32_t v[32];
-        tmem_ld16(dcol, v);
-        tmem_ld16(dcol + 16, v + 16);
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(grp * 32) << 16) + buf * kDBuf + quarter * 16, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) accD[j] += __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j) accD[j] += __uint_as_float(v[j]);
         tc_fence_before();
         mbar_arrive(&dempty[buf]);
       };
@@ -377,23 +401,30 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
         cp_async_wait<1>();
         producers_sync();
         issue(k + 2);
-        const float2* st = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
-        const int c0 = k * kStageCentres;
+        float2* st = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
+        // x~ B for the stage's centres, in place over the B block
+        for (int e = tid; e < kStageCentres * blk[0].len; e += kProducers) {
+          const int i = e / blk[0].len, j = e - i * blk[0].len;
+          float2* sp = st + i * sc;
+          float2 x = sp[xsel];
+          x.y *= xsgn;
+          float2 b = sp[bstart[0] + j];
+          b.y *= bsgn;
+          sp[bstart[0] + j] = make_float2(x.x * b.x - x.y * b.y, x.x * b.y + x.y * b.x);
+        }
+        producers_sync();
         if (!mbar_wait(&empty[slot], ph ^ 1u, budget)) err = 1;
         tc_fence_after();
-        // B operand (shared memory, swizzled): real embedding of A(Th1) for 8 centres
+        // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
         unsigned char* bt = sm + slot * stage_bytes;
         if (bn < npad) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int i = bq * 8 + j;
-            float v0 = 0.f, v1 = 0.f;
-            if (bcol_ok && c0 + i < args.T) {
-              float2 a = st[i * sc + iA];
-              if (cjA) a.y = -a.y;
-              v0 = bo ? a.y : a.x;
-              v1 = bo ? a.x : -a.y;
-            }
+          for (int j = 0; j < 4; ++j) {
+            const int i = bq * 4 + j;
+            float2 a = st[i * sc + iA];
+            a.y *= sgnA;
+            const float v0 = bo ? a.y : a.x;
+            const float v1 = bo ? a.x : -a.y;
             if (kBF16) {
               uint32_t h, l;
               split_bf16(v0, v1, h, l);
@@ -401,30 +432,22 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
               *reinterpret_cast<uint32_t*>(bt + off) = h;
               *reinterpret_cast<uint32_t*>(bt + tile_bytes + off) = l;
             } else {
-              *reinterpret_cast<float*>(bt + sw128_word_off(bn, 2 * i, kMaxNpad)) = v0;
-              *reinterpret_cast<float*>(bt + sw128_word_off(bn, 2 * i + 1, kMaxNpad)) = v1;
+              *reinterpret_cast<float2*>(bt + sw128_word_off(bn, 2 * i, kMaxNpad)) = make_float2(v0, v1);
             }
           }
         }
-        // A operand (TMEM): this row's Khatri-Rao values for 16 centres
-        uint32_t w[32];
+        // A operand (TMEM): this row's Khatri-Rao values for 8 centres
+        uint32_t w[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int i = half * 16 + j;
-          float kr_re = 0.f, kr_im = 0.f;
-          if (row_ok && c0 + i < args.T) {
-            const float2* sp = st + i * sc;
-            float2 x = sp[kr.xconj == 2 ? 1 : 0];
-            if (kr.xconj == 1) x.y = -x.y;
-            float2 bv = sp[iB], cv = sp[iC];
-            if (cjB) bv.y = -bv.y;
-            if (cjC) cv.y = -cv.y;
-            const float xbr = x.x * bv.x - x.y * bv.y, xbi = x.x * bv.y + x.y * bv.x;
-            kr_re = xbr * cv.x - xbi * cv.y;
-            kr_im = xbr * cv.y + xbi * cv.x;
-          }
+        for (int j = 0; j < kQuarter; ++j) {
+          const float2* sp = st + (quarter * kQuarter + j) * sc;
+          float2 xb = sp[iB], cv = sp[iC];
+          xb.y *= sgnB;
+          cv.y *= sgnC;
+          const float kr_re = xb.x * cv.x - xb.y * cv.y;
+          const float kr_im = xb.x * cv.y + xb.y * cv.x;
           if (kBF16) {
-            split_bf16(kr_re, kr_im, w[j], w[16 + j]);
+            split_bf16(kr_re, kr_im, w[j], w[8 + j]);
           } else {
             w[2 * j] = __float_as_uint(kr_re);
             w[2 * j + 1] = __float_as_uint(kr_im);
@@ -432,11 +455,10 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
         }
         const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * kStageCols;
         if (kBF16) {
-          tmem_st16(acol + half * 16, w);
-          tmem_st16(acol + 32 + half * 16, w + 16);
+          tmem_st8(acol + quarter * 8, w);
+          tmem_st8(acol + 32 + quarter * 8, w + 8);
         } else {
-          tmem_st16(acol + half * 32, w);
-          tmem_st16(acol + half * 32 + 16, w + 16);
+          tmem_st16(acol + quarter * 16, w);
         }
         fence_async_smem();
         tmem_wait_st();
@@ -446,19 +468,17 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
         if ((k % kPromote) == kPromote - 1 && k / kPromote >= 1) promote(gs0 + k / kPromote - 1);
       }
       cp_async_wait<0>();
-      // the remaining partial sums of this item
-      // in the loop, partials 0 .. F-2 were read (F = complete promotion blocks)
+      // the remaining partial sums of this item: the loop read partials 0 .. F-2
+      // (F = complete promotion blocks)
       const int read_in_loop = max(0, nstage / kPromote - 1);
-      const long long first_left = gs0 + read_in_loop;
-      const long long nleft = nsub - read_in_loop;
-      for (long long g = first_left; g < first_left + nleft; ++g) promote(g);
+      for (long long g = gs0 + read_in_loop; g < gs0 + nsub; ++g) promote(g);
       gs = gs0 + nsub;
       // ------------------------------------------------------------------ epilogue
       if (row_ok) {
         const size_t nb3 = (size_t)nb2 * nb;
 #pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-          const int n = half * 32 + j;
+        for (int j = 0; j < 16; j += 2) {
+          const int n = quarter * 16 + j;
           if (n < ncols) {
             const int g = n / (2 * nb), b1 = (n >> 1) % nb;
             const int mu = kr.mu[g];

@@ -47,6 +47,17 @@ __device__ __forceinline__ void cpow(R br, R bi, int e, R& pr, R& pi) {
   }
 }
 
+// u^e for 0 <= e < 32 by binary powering, unrolled (e is uniform across the warp)
+template <typename R>
+__device__ __forceinline__ void cpow5(R br, R bi, int e, R& pr, R& pi) {
+  pr = R(1); pi = R(0);
+#pragma unroll
+  for (int bit = 0; bit < 5; ++bit) {
+    if (e & (1 << bit)) { R t = pr * br - pi * bi; pi = pr * bi + pi * br; pr = t; }
+    if (e >> (bit + 1)) { R t = br * br - bi * bi; bi = R(2) * br * bi; br = t; }
+  }
+}
+
 // transposed butterfly: after the call lane l holds in a[0..V/32) the warp totals of the
 // original slots j + base(l), base(l) = sum_k bit_k(l) * V / 2^(5-k)
 template <typename R, int V, int OFF>
@@ -310,53 +321,69 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
           R a[V];
 #pragma unroll
           for (int j = 0; j < V; ++j) a[j] = R(0);
-          for (int e = s0 + lane; e < s1; e += 32) {
-            const R ur = eur[e], ui = eui[e], xr = exr[e], xi = exi[e], ww = ew[e];
-            R pr, pim;
-            cpow<R>(evr[e], evi[e], k, pr, pim);
-            const R x2r = xr * xr - xi * xi, x2i = R(2) * xr * xi;
-            const R xa = xr * xr + xi * xi, w2 = ww * ww;
+          // two pairs per lane and iteration: two independent power recurrences
+          auto accumulate = [&](int e0, int e1) {
+            const bool two = e1 < s1;
+            const R ur0 = eur[e0], ui0 = eui[e0], xr0 = exr[e0], xi0 = exi[e0], w0 = ew[e0];
+            const R ur1 = two ? eur[e1] : R(0), ui1 = two ? eui[e1] : R(0);
+            const R xr1 = two ? exr[e1] : R(0), xi1 = two ? exi[e1] : R(0), w1 = two ? ew[e1] : R(0);
+            R pr0, pi0, pr1, pi1;
+            cpow5<R>(evr[e0], evi[e0], k, pr0, pi0);
+            cpow5<R>(two ? evr[e1] : R(1), two ? evi[e1] : R(0), k, pr1, pi1);
+            const R x2r0 = xr0 * xr0 - xi0 * xi0, x2i0 = R(2) * xr0 * xi0, xa0 = xr0 * xr0 + xi0 * xi0;
+            const R x2r1 = xr1 * xr1 - xi1 * xi1, x2i1 = R(2) * xr1 * xi1, xa1 = xr1 * xr1 + xi1 * xi1;
+            const R ww0 = w0 * w0, ww1 = w1 * w1;
 #pragma unroll
             for (int t = 0; t < MB; ++t) {
               if (t < mb) {
-                a[14 * t + 0] += xr * pr - xi * pim;
-                a[14 * t + 1] += xr * pim + xi * pr;
-                a[14 * t + 2] += xr * pr + xi * pim;
-                a[14 * t + 3] += xi * pr - xr * pim;
-                a[14 * t + 4] += x2r * pr - x2i * pim;
-                a[14 * t + 5] += x2r * pim + x2i * pr;
-                a[14 * t + 6] += x2r * pr + x2i * pim;
-                a[14 * t + 7] += x2i * pr - x2r * pim;
-                a[14 * t + 8] += ww * pr;
-                a[14 * t + 9] += ww * pim;
-                a[14 * t + 10] += xa * pr;
-                a[14 * t + 11] += xa * pim;
-                a[14 * t + 12] += w2 * pr;
-                a[14 * t + 13] += w2 * pim;
-                const R nr2 = pr * ur - pim * ui;
-                pim = pr * ui + pim * ur;
-                pr = nr2;
+                a[14 * t + 0] += xr0 * pr0 - xi0 * pi0 + xr1 * pr1 - xi1 * pi1;
+                a[14 * t + 1] += xr0 * pi0 + xi0 * pr0 + xr1 * pi1 + xi1 * pr1;
+                a[14 * t + 2] += xr0 * pr0 + xi0 * pi0 + xr1 * pr1 + xi1 * pi1;
+                a[14 * t + 3] += xi0 * pr0 - xr0 * pi0 + xi1 * pr1 - xr1 * pi1;
+                a[14 * t + 4] += x2r0 * pr0 - x2i0 * pi0 + x2r1 * pr1 - x2i1 * pi1;
+                a[14 * t + 5] += x2r0 * pi0 + x2i0 * pr0 + x2r1 * pi1 + x2i1 * pr1;
+                a[14 * t + 6] += x2r0 * pr0 + x2i0 * pi0 + x2r1 * pr1 + x2i1 * pi1;
+                a[14 * t + 7] += x2i0 * pr0 - x2r0 * pi0 + x2i1 * pr1 - x2r1 * pi1;
+                a[14 * t + 8] += w0 * pr0 + w1 * pr1;
+                a[14 * t + 9] += w0 * pi0 + w1 * pi1;
+                a[14 * t + 10] += xa0 * pr0 + xa1 * pr1;
+                a[14 * t + 11] += xa0 * pi0 + xa1 * pi1;
+                a[14 * t + 12] += ww0 * pr0 + ww1 * pr1;
+                a[14 * t + 13] += ww0 * pi0 + ww1 * pi1;
+                const R n0 = pr0 * ur0 - pi0 * ui0;
+                pi0 = pr0 * ui0 + pi0 * ur0;
+                pr0 = n0;
+                const R n1 = pr1 * ur1 - pi1 * ui1;
+                pi1 = pr1 * ui1 + pi1 * ur1;
+                pr1 = n1;
               }
             }
             if (m0 == 0) {
-              // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3
-              R u2r = ur * ur - ui * ui, u2i = R(2) * ur * ui;
-              R u4r = u2r * u2r - u2i * u2i, u4i = R(2) * u2r * u2i;
-              R u8r = u4r * u4r - u4i * u4i, u8i = R(2) * u4r * u4i;
-              R x3r = x2r * xr - x2i * xi, x3i = x2r * xi + x2i * xr;
-              R xcr = xa * xr, xci = xa * xi;  // x^2 x^* = |x|^2 x
-              constexpr int o = 14 * MB;
-              a[o + 0] += x3r * u8r + x3i * u8i;  // x3 * conj(u8)
-              a[o + 1] += x3i * u8r - x3r * u8i;
-              a[o + 2] += x3r * u4r + x3i * u4i;
-              a[o + 3] += x3i * u4r - x3r * u4i;
-              a[o + 4] += xcr * u4r + xci * u4i;
-              a[o + 5] += xci * u4r - xcr * u4i;
-              a[o + 6] += xcr;
-              a[o + 7] += xci;
-              a[o + 8] += w2 * ww;
+              // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3 (the second pair is zero if absent)
+#pragma unroll
+              for (int q = 0; q < 2; ++q) {
+                const R ur = q ? ur1 : ur0, ui = q ? ui1 : ui0, xr = q ? xr1 : xr0, xi = q ? xi1 : xi0;
+                const R x2r = q ? x2r1 : x2r0, x2i = q ? x2i1 : x2i0, xa = q ? xa1 : xa0;
+                const R ww = q ? w1 : w0, w2 = q ? ww1 : ww0;
+                R u2r = ur * ur - ui * ui, u2i = R(2) * ur * ui;
+                R u4r = u2r * u2r - u2i * u2i, u4i = R(2) * u2r * u2i;
+                R u8r = u4r * u4r - u4i * u4i, u8i = R(2) * u4r * u4i;
+                R x3r = x2r * xr - x2i * xi, x3i = x2r * xi + x2i * xr;
+                R xcr = xa * xr, xci = xa * xi;  // x^2 x^* = |x|^2 x
+                constexpr int o = 14 * MB;
+                a[o + 0] += x3r * u8r + x3i * u8i;  // x3 * conj(u8)
+                a[o + 1] += x3i * u8r - x3r * u8i;
+                a[o + 2] += x3r * u4r + x3i * u4i;
+                a[o + 3] += x3i * u4r - x3r * u4i;
+                a[o + 4] += xcr * u4r + xci * u4i;
+                a[o + 5] += xci * u4r - xcr * u4i;
+                a[o + 6] += xcr;
+                a[o + 7] += xci;
+                a[o + 8] += w2 * ww;
+              }
             }
-          }
+          };
+          for (int e = s0 + lane; e < s1; e += 64) accumulate(e, e + 32);
           reduce_transpose<R, V>(a, lane);
           const int base = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
                            (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
