@@ -146,6 +146,26 @@ EXT4PCF_API int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const d
                     int n_bins, int n_max, int n_phi, const double* ap_radii, int n_ap,
                     const double* xi_acc, double* m4, double* map4_eb, double* map4_disc);
 
+/* The real-space transform of ext4pcf_to_real_space for callers that cannot allocate device
+ * memory (no cudaMalloc, cudaFree or allocating library routine is called, and no context
+ * is needed).  The paper has no counterpart: this is a deployment variant.  Scratch lives
+ * in one 16 MiB device array inside the library, held by every GPU that loads it until the
+ * process exits, so the sizes must satisfy
+ *     n_bins^3 * n_phi^2 * 8 (rounded up to 256) + (2 n_max + 1) * n_phi * 16 <= 16 MiB
+ * (for example n_bins = 10 with n_phi <= 45, or n_bins = 8 with n_phi <= 63); larger sizes
+ * return EXT4PCF_E_UNSUPPORTED before any work is enqueued.
+ *   upsilon, gamma, norm  device pointers with the layouts of ext4pcf_to_real_space;
+ *                         gamma and norm are accumulated into
+ *   stream                cudaStream_t to enqueue on (NULL = legacy default stream)
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  The call is stream-ordered and returns
+ * after enqueueing.  All calls share the array: calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Returns EXT4PCF_OK, EXT4PCF_E_INVALID_ARG (null or host pointers, sizes out of range),
+ * EXT4PCF_E_UNSUPPORTED (beyond the scratch size) or EXT4PCF_E_CUDA. */
+EXT4PCF_API int ext4pcf_to_real_space_noalloc(const double* upsilon, int n_bins, int n_max, int n_phi,
+                                              double* gamma, double* norm, void* stream);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 EXT4PCF_API const char* ext4pcf_last_error(const ext4pcf_ctx* ctx);
 

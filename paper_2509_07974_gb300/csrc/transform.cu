@@ -10,6 +10,8 @@
 //      J_mu = sum_p P_p R_p pi p! (theta^2/2)^{p+1},
 //    P(z^*) = prod over unconjugated apertures (z^* + d_a^*)^2, R(z) = prod over conjugated
 //    apertures (z + d_a)^2, ph_mu = 2 sum_a s_a zeta_a of the x-projection (s = +-1).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ext4pcf {
@@ -380,4 +382,80 @@ cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const 
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Real-space transform that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code running while a CUDA graph is being captured
+// with a relaxed allocator policy, plug-ins whose host application owns all device memory,
+// and real-time loops that must not block in the allocator.  For them this entry point
+// keeps its scratch (the angular-bin table and the per-bin normalisation counts) in one
+// file-scope device array of kStaticScratchBytes, held by every GPU that loads the library
+// until the process exits.  Its address is looked up once per device with
+// cudaGetSymbolAddress (the host symbol is only a stand-in and must not be passed to a
+// kernel).  Every call shares the array: calls that overlap on the GPU race.  Both scratch
+// regions are fully overwritten by each call before they are read, so nothing needs to be
+// cleared.
+// ---------------------------------------------------------------------------------------
+namespace {
+constexpr size_t kStaticScratchBytes = 16u << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mutex;
+void* g_static_ptr[64] = {};
+
+// address of the static scratch on the current device (set-up on first use per device)
+cudaError_t static_scratch_ptr(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+
+bool device_resident(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+size_t real_space_smem(int N, int nphi);
+cudaError_t real_space(const double* ups, int nb, int N, int nphi, double* gamma, double* norm,
+                       double* scratch_norm, double* E_scratch, cudaStream_t s);
+
 }  // namespace ext4pcf
+
+extern "C" EXT4PCF_API int ext4pcf_to_real_space_noalloc(const double* upsilon, int n_bins, int n_max,
+                                                         int n_phi, double* gamma, double* norm,
+                                                         void* stream) {
+  using namespace ext4pcf;
+  if (!upsilon || !gamma || !norm) return EXT4PCF_E_INVALID_ARG;
+  if (n_bins < 1 || n_bins > 32 || n_max < 0 || n_max > 40 || n_phi < 1 || n_phi > 1024)
+    return EXT4PCF_E_INVALID_ARG;
+  const size_t table_bytes = (size_t)(2 * n_max + 1) * n_phi * 16;
+  const size_t norm_bytes = (size_t)n_bins * n_bins * n_bins * n_phi * n_phi * 8;
+  const size_t table_off = (norm_bytes + 255) / 256 * 256;
+  if (table_off + table_bytes > kStaticScratchBytes) return EXT4PCF_E_UNSUPPORTED;
+  if (real_space_smem(n_max, n_phi) > 227 * 1024) return EXT4PCF_E_UNSUPPORTED;
+  if (!device_resident(upsilon) || !device_resident(gamma) || !device_resident(norm))
+    return EXT4PCF_E_INVALID_ARG;
+  void* base = nullptr;
+  if (static_scratch_ptr(&base) != cudaSuccess) return EXT4PCF_E_CUDA;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  cudaError_t e = real_space(upsilon, n_bins, n_max, n_phi, gamma, norm, reinterpret_cast<double*>(b),
+                             reinterpret_cast<double*>(b + table_off), static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? EXT4PCF_OK : EXT4PCF_E_CUDA;
+}

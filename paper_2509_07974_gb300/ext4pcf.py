@@ -65,6 +65,8 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_measure.argtypes = [P, P, P, P, I64, P, I, I, P, I, P, P, P, ctypes.POINTER(Stats)]
     lib.ext4pcf_to_real_space.argtypes = [P, P, I, I, I, P, P]
     lib.ext4pcf_to_map4.argtypes = [P, P, P, I, I, I, P, I, P, P, P, P]
+    lib.ext4pcf_to_real_space_noalloc.argtypes = [P, I, I, I, P, P, P]
+    lib.ext4pcf_to_real_space_noalloc.restype = I
     lib.ext4pcf_last_error.argtypes = [P]
     lib.ext4pcf_last_error.restype = ctypes.c_char_p
     for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_to_real_space",
@@ -135,6 +137,14 @@ def ext4pcf_to_map4(ctx, upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n
                                 int(n_phi), _addr(ap_radii), int(n_ap), _addr(xi_acc), _addr(m4),
                                 _addr(map4_eb), _addr(map4_disc))
     return _check(ctx, rc)
+
+
+def ext4pcf_to_real_space_noalloc(upsilon, n_bins, n_max, n_phi, gamma, norm, stream=None) -> int:
+    """Allocation-free real-space transform (static 16 MiB device scratch, no context).
+    Returns the ABI status code (0 on success); does not raise."""
+    st = getattr(stream, "cuda_stream", stream)
+    return load().ext4pcf_to_real_space_noalloc(_addr(upsilon), int(n_bins), int(n_max), int(n_phi),
+                                                _addr(gamma), _addr(norm), st)
 
 
 # ---- torch convenience wrapper ---------------------------------------------------------
