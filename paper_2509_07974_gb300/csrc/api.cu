@@ -68,7 +68,7 @@ struct ext4pcf_ctx {
   // transforms
   DBuf t_norm, t_gam, t_E, t_part, t_small;
   // tensor-core contraction: work items (built once per shape) and the device status word
-  DBuf tc_items, status;
+  DBuf tc_items, tc_xb, status;
   int tc_N = -1, tc_nb = -1;
   size_t tc_items_bytes = 0;
   cudaEvent_t ev[8] = {};
@@ -182,7 +182,7 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
                  &ctx->px, &ctx->py, &ctx->xr, &ctx->xi, &ctx->w, &ctx->p4, &ctx->s4, &ctx->bbox,
                  &ctx->centres, &ctx->flags, &ctx->rec, &ctx->xw, &ctx->corr, &ctx->counter, &ctx->ncen,
                  &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small, &ctx->tc_items,
-                 &ctx->status};
+                 &ctx->tc_xb, &ctx->status};
   for (DBuf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
@@ -286,7 +286,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   if (timing) CK(cudaEventRecord(ctx->ev[0], s));
   ENSURE(ctx->counter, 16);
   CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
-  const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16;
+  const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16 || prec == EXT4PCF_3XTF32;
   if (tc) {
     if (ctx->tc_N != n_max || ctx->tc_nb != n_bins) {
       std::vector<int4> items;
@@ -373,6 +373,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     if (T > n_cen) T = n_cen;
     if (T < 1) T = 1;
     ENSURE(ctx->rec, (size_t)T * L.rec * cbytes);
+    if (tc) ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, T));
     ENSURE(ctx->xw, (size_t)T * 2 * cbytes);
     const size_t corr_doubles = corrections_size(L);
     ENSURE(ctx->corr, corr_doubles * 8);
@@ -395,7 +396,8 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
         CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, s));
       } else {
         CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, prec,
-                            ctx->tc_items.p, ctx->tc_items_bytes, (int*)ctx->status.p, timeout, s));
+                            (const int4*)ctx->tc_items.p, (int)(ctx->tc_items_bytes / sizeof(int4)),
+                            (float2*)ctx->tc_xb.p, (int*)ctx->status.p, timeout, s));
       }
       if (timing) CK(cudaEventRecord(ctx->ev[5], s));
       if (f64) {

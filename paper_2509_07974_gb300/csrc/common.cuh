@@ -134,9 +134,9 @@ size_t corrections_size(const Layout& L);  // doubles
 // contract_tc.cu (tensor cores)
 bool tc_supported(const Layout& L, int precision);
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T,
-                             double* ups, int precision, void* scratch, size_t scratch_bytes,
+                             double* ups, int precision, const int4* items, int n_items, float2* xb,
                              int* status, long long timeout, cudaStream_t s);
-size_t contract_tc_scratch(const Layout& L, int T);
+size_t contract_tc_xb_bytes(const Layout& L, int T);
 void tc_build_items(const Layout& L, std::vector<int4>& items);
 
 }  // namespace ext4pcf

@@ -9,8 +9,8 @@
 //     lane r; centre i occupies K elements (2i, 2i+1) = (re, im).  Sixteen producer warps
 //     form KR on the CUDA cores and write it with tcgen05.st (warp w owns lanes
 //     32 (w % 4) ..; the four warps of a lane group split the 32 centres of a stage).
-//     Each stage's record slices are staged in shared memory with cp.async two stages
-//     ahead, and x~ B is formed once per (centre, n2, Th2) before the rows are built.
+//     Each stage's record slices (x~ B rows, C rows, A rows) are staged in shared memory
+//     with cp.async two stages ahead.
 //   * B operand (shared memory, K-major, 128-byte swizzle): column (mu, Th1, re|im) holds
 //     the real embedding of A_i^mu(Th1): K rows (2i, 2i+1) = (Ar, -Ai) for the real output
 //     and (Ai, Ar) for the imaginary output, so that D = A_op B_op is the complex product.
@@ -19,10 +19,13 @@
 //     the MMAs run on meanwhile); the long FP32 accumulation inside the tensor core would
 //     otherwise lose bits.  The epilogue adds the sums into the FP64 output.
 // Precision: BF16x3 splits every operand into bf16 hi + lo and accumulates
-// hi*hi + hi*lo + lo*hi (kind::f16); TF32 uses one kind::tf32 pass.
-// Pipeline: 4 stages of 32 centres; full/empty mbarriers between the producers and the one
+// hi*hi + hi*lo + lo*hi (kind::f16); 3xTF32 does the same with tf32 hi + lo (kind::tf32,
+// ~22 mantissa bits per operand); TF32 uses one kind::tf32 pass.
+// x~ B is formed for the whole wave by xb_kernel before the contraction.
+// Pipeline: 4 (3 for 3xTF32) stages of 32 centres; full/empty mbarriers between the producers and the one
 // thread that issues the MMAs; tcgen05.commit releases a stage.  Every wait is bounded by
 // a clock budget; on expiry the kernel records an error code and runs to its end.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -31,7 +34,6 @@ namespace ext4pcf {
 
 namespace {
 
-constexpr int kStages = 4;
 constexpr int kStageCentres = 32;
 constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
@@ -206,6 +208,7 @@ __device__ __forceinline__ uint32_t sw128_word_off(int n, int j, int npad) {
   return (uint32_t)(atom * (npad >> 3) * 1024 + (n >> 3) * 1024 + (n & 7) * 128 + ((chunk ^ (n & 7)) << 4) + within);
 }
 
+
 // One staged block of a per-centre record: `len` consecutive complex values starting at
 // record element `rec_off`; `lo` is the first multipole index (n for G, m = |n| for W).
 struct Blk {
@@ -249,35 +252,85 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory"); }
 
-constexpr int kStageBufs = 3;     // staging ring: stage k + 2 is fetched while k is formed
-// staged complex values per centre: x, w, a zero, the B and C blocks of at most the tile's
-// n2 values (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two
-// A rows; rounded up to an odd count so that consecutive centres fall in different banks
+// x~ times the row factor B, per centre: [5][2N+1][nb] complex, indexed by n2:
+//   0: x G[-n2-2]   1: x G[n2-2]^*   2: x^* G[-n2-2]   3: x^* G[n2-2]^*   4: w W[-n2]
+constexpr int kXBTypes = 5;
+__constant__ signed char kXBOfType[7] = {0, 1, 0, 2, 3, 2, 4};
+
+__global__ void xb_kernel(const Layout L, const float2* __restrict__ rec, const float2* __restrict__ xw, int T,
+                          float2* __restrict__ xb) {
+  const int nb = L.nb, N = L.N, nn = 2 * N + 1;
+  const int per = kXBTypes * nn * nb;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < (size_t)T * per;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k / per), r = (int)(k % per);
+    const int t = r / (nn * nb), n2 = (r / nb) % nn - N, b = r % nb;
+    const float2* rc = rec + (size_t)c * L.rec;
+    float2 x = xw[2 * (size_t)c], f;
+    if (t == 4) {
+      const int m = -n2;
+      f = rc[L.W(m >= 0 ? m : -m, b)];
+      if (m < 0) f.y = -f.y;
+      x = xw[2 * (size_t)c + 1];
+    } else {
+      f = (t & 1) ? rc[L.G(n2 - 2, b)] : rc[L.G(-n2 - 2, b)];
+      if (t & 1) f.y = -f.y;
+      if (t >= 2) x.y = -x.y;
+    }
+    xb[k] = make_float2(x.x * f.x - x.y * f.y, x.x * f.y + x.y * f.x);
+  }
+}
+
+constexpr int kStageBufs = 3;  // staging ring: stage k + 2 is fetched while k is formed
+// staged complex values per centre: a zero, the x~B and C blocks of at most the tile's n2
+// values (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two A
+// rows; rounded up to an odd count so that consecutive centres fall in different banks
 __host__ __device__ inline int stage_values(int nb, int N) {
   int rows = 128 / (nb * nb) + 2;
   if (rows > 2 * N + 1) rows = 2 * N + 1;
-  return (3 + 2 * rows * nb + 2 * nb) | 1;
+  return (1 + 2 * rows * nb + 2 * nb) | 1;
 }
-constexpr int kPromote = 8;       // stages per TMEM partial sum (256 centres)
-constexpr int kDBuf = 64;         // two D buffers of 64 columns (npad <= 64)
+constexpr int kPromote = 8;  // stages per TMEM partial sum (256 centres)
+constexpr int kDBuf = 64;    // two D buffers of 64 columns (npad <= 64)
 constexpr int kQuarter = kStageCentres / (kProducerWarps / 4);  // centres per producer warp
 
+// Per precision: stages, TMEM columns and 128-byte-wide shared-memory K-atoms per stage.
+template <int PREC> struct TcPrec;
+template <> struct TcPrec<EXT4PCF_SPLIT_BF16> {  // A: hi | lo (bf16x2); B: hi atom | lo atom
+  static constexpr int kStages = 4, kStageCols = 64, kAtoms = 2;
+};
+template <> struct TcPrec<EXT4PCF_TF32> {  // A: fp32 (re, im) pairs; B: two atoms
+  static constexpr int kStages = 4, kStageCols = 64, kAtoms = 2;
+};
+template <> struct TcPrec<EXT4PCF_3XTF32> {  // A: hi | lo fp32 pairs; B: hi 2 atoms | lo 2 atoms
+  static constexpr int kStages = 3, kStageCols = 128, kAtoms = 4;
+};
+
+// tf32 hi/lo split: hi keeps sign, exponent and 10 mantissa bits; lo = x - hi is exact
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(x) & 0xFFFFE000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs args) {
-  constexpr bool kBF16 = PREC == EXT4PCF_SPLIT_BF16;
+__global__ void __launch_bounds__(kThreads, 1)
+contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
+  using P = TcPrec<PREC>;
+  constexpr int kSt = P::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const Layout L = args.L;
   const int nb = L.nb, N = L.N, nn = 2 * N + 1, nb2 = nb * nb;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int tile_bytes = kMaxNpad * 128;   // one 128-byte-wide K-atom of B (npad <= 64)
-  constexpr int stage_bytes = 2 * tile_bytes;  // hi + lo, or two fp32 K-atoms
-  const int sc_max = stage_values(nb, N);      // staged complex values per centre (upper bound)
-  float2* stg = reinterpret_cast<float2*>(sm + kStages * stage_bytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(stg + kStageBufs * kStageCentres * sc_max);
-  uint64_t* empty = full + kStages;
-  uint64_t* dfull = empty + kStages;   // [2]: a D buffer holds a finished partial sum
-  uint64_t* dempty = dfull + 2;        // [2]: the producers have read it
+  constexpr int tile_bytes = kMaxNpad * 128;  // one 128-byte-wide K-atom (npad <= 64)
+  constexpr int stage_bytes = P::kAtoms * tile_bytes;
+  const int sc_max = stage_values(nb, N);
+  float2* stg = reinterpret_cast<float2*>(sm + kSt * stage_bytes);
+  int* gmap = reinterpret_cast<int*>(stg + kStageBufs * kStageCentres * sc_max);  // [sc_max]
+  uint64_t* full = reinterpret_cast<uint64_t*>(gmap + ((sc_max + 1) & ~1));
+  uint64_t* empty = full + kSt;
+  uint64_t* dfull = empty + kSt;  // [2]: a D buffer holds a finished partial sum
+  uint64_t* dempty = dfull + 2;   // [2]: the producers have read it
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dempty + 2);
 
   if (warp == 0) {
@@ -287,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int k = 0; k < kStages; ++k) {
+    for (int k = 0; k < kSt; ++k) {
       mbar_init(&full[k], kProducers);
       mbar_init(&empty[k], 1);
     }
@@ -304,6 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
   const long long budget = args.timeout;
   const int nstage = (args.T + kStageCentres - 1) / kStageCentres;
   const int nsub = (nstage + kPromote - 1) / kPromote;
+  const size_t xb_stride = (size_t)kXBTypes * nn * nb;
   int err = 0;
 
   long long gk = 0;  // stages handled by this CTA (phases of full / empty)
@@ -316,61 +370,65 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
     const int ncols = 2 * nmu * nb;
     const int npad = (ncols + 15) / 16 * 16;
     const int n2a = max(-N, s - N);
-    // the tile's rows span n2 in [t2a, t2b]; staged blocks of every centre record:
-    // B(n2), C(n3 = s - n2), A_0(s), A_1(s)
+    // the tile's rows span n2 in [t2a, t2b]; staged per centre: [0] zero, x~B rows
+    // [t2a, t2b], C rows for n3 = s - n2, A_0(s), A_1(s)
     const int t2a = n2a + row0 / nb2, t2b = n2a + (row0 + nrows - 1) / nb2;
-    Blk blk[4];
-    blk[0] = make_blk(L, kr.B, t2a, t2b);
-    blk[1] = make_blk(L, kr.C, s - t2b, s - t2a);
-    blk[2] = make_blk(L, kr.A[0], s, s);
-    blk[3] = nmu > 1 ? make_blk(L, kr.A[1], s, s) : Blk{0, 0, 0, 0};
-    int bstart[4];
-    int sc = 3;
-    for (int k = 0; k < 4; ++k) { bstart[k] = sc; sc += blk[k].len; }
-    sc |= 1;
+    const int xb_len = (t2b - t2a + 1) * nb;
+    const int xb_off = (kXBOfType[type] * nn + (t2a + N)) * nb;
+    const Blk bkC = make_blk(L, kr.C, s - t2b, s - t2a);
+    const Blk bkA0 = make_blk(L, kr.A[0], s, s);
+    const Blk bkA1 = nmu > 1 ? make_blk(L, kr.A[1], s, s) : Blk{0, 0, 0, 0};
+    const int bC = 1 + xb_len, bA0 = bC + bkC.len, bA1 = bA0 + bkA0.len;
+    const int sc = (bA1 + bkA1.len) | 1;
     if (warp < kProducerWarps) {
       // ------------------------------------------------------------------ producers
+      // record offsets of the staged values after the x~B block (-1: nothing to copy)
+      for (int e = bC + tid; e < sc; e += kProducers) {
+        int m = -1;
+        if (e < bA0) m = bkC.rec_off + (e - bC);
+        else if (e < bA1) m = bkA0.rec_off + (e - bA0);
+        else if (e < bA1 + bkA1.len) m = bkA1.rec_off + (e - bA1);
+        gmap[e] = m;
+      }
+      producers_sync();
       const int grp = warp & 3, quarter = warp >> 2;
       const int rl = grp * 32 + lane;  // tile row = TMEM lane
       const bool row_ok = rl < nrows;
       const int rr = row0 + (row_ok ? rl : 0);
       const int n2 = n2a + rr / nb2, b2 = (rr / nb) % nb, b3 = rr % nb, n3 = s - n2;
-      // staged indices of this row's factors (index 2 is a zero: rows past the tile);
-      // the B block holds x~ B after the per-stage product below, conjugated per row if
-      // the factor is W at a negative index (x~ = w is real there)
-      bool cjB, cjC;
-      int iB = bstart[0] + blk_index(blk[0], kr.B, n2, b2, nb, cjB);
-      int iC = bstart[1] + blk_index(blk[1], kr.C, n3, b3, nb, cjC);
-      const float sgnB = (kr.B.arr == 1 && cjB) ? -1.f : 1.f;
+      bool cjC;
+      int iB = 1 + (n2 - t2a) * nb + b2;
+      int iC = bC + blk_index(bkC, kr.C, n3, b3, nb, cjC);
       const float sgnC = cjC ? -1.f : 1.f;
-      if (!row_ok) { iB = 2; iC = 2; }
-      // B-operand words of this thread: column bn, centres [8 bq, 8 bq + 8)
-      const int bn = tid >> 3, bq = tid & 7;  // 64 columns x 8 groups of 4 centres
-      int iA = 2;
-      int bo = 0;
+      if (!row_ok) { iB = 0; iC = 0; }
+      // B-operand words of this thread: column bn, centres [4 bq, 4 bq + 4)
+      const int bn = tid >> 3, bq = tid & 7;
+      int iA = 0, bo = 0;
       float sgnA = 1.f;
       if (bn < ncols) {
         const int g = bn / (2 * nb), b1 = (bn >> 1) % nb;
         bool cjA;
         bo = bn & 1;
-        iA = bstart[2 + g] + blk_index(blk[2 + g], kr.A[g], s, b1, nb, cjA);
+        iA = (g ? bA1 : bA0) + blk_index(g ? bkA1 : bkA0, kr.A[g], s, b1, nb, cjA);
         sgnA = cjA ? -1.f : 1.f;
       }
-      const int xsel = kr.xconj == 2 ? 1 : 0;
-      const float xsgn = kr.xconj == 1 ? -1.f : 1.f;
-      const float bsgn = (kr.B.arr == 0 && kr.B.conj) ? -1.f : 1.f;
-      // copy one stage's record slices (16 threads per centre); tails are zero-filled
+      // copy one stage's slices (16 threads per centre); tails are zero-filled
       auto issue = [&](int k) {
         if (k < nstage) {
-          float2* dst = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
-          const int i = tid >> 4, sub = tid & 15, c = k * kStageCentres + i;
-          float2* d = dst + i * sc;
+          float2* d = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max + (tid >> 4) * sc;
+          const int sub = tid & 15, c = k * kStageCentres + (tid >> 4);
           if (c < args.T) {
-            if (sub < 2) cp_async8(d + sub, args.xw + 2 * (size_t)c + sub);
-            if (sub == 2) d[2] = make_float2(0.f, 0.f);
+            if (sub == 0) d[0] = make_float2(0.f, 0.f);
+            const float2* xs = xbarr + (size_t)c * xb_stride + xb_off - 1;
             const float2* rc = args.rec + (size_t)c * L.rec;
-            for (int b = 0; b < 4; ++b)
-              for (int e = sub; e < blk[b].len; e += 16) cp_async8(d + bstart[b] + e, rc + blk[b].rec_off + e);
+            for (int e = 1 + sub; e < sc; e += 16) {
+              if (e < bC) {
+                cp_async8(d + e, xs + e);
+              } else {
+                const int m = gmap[e];
+                if (m >= 0) cp_async8(d + e, rc + m);
+              }
+            }
           } else {
             for (int e = sub; e < sc; e += 16) d[e] = make_float2(0.f, 0.f);
           }
@@ -396,23 +454,12 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
       };
       const long long gs0 = gs;
       for (int k = 0; k < nstage; ++k, ++gk) {
-        const int slot = (int)(gk % kStages);
-        const uint32_t ph = (uint32_t)((gk / kStages) & 1);
+        const int slot = (int)(gk % kSt);
+        const uint32_t ph = (uint32_t)((gk / kSt) & 1);
         cp_async_wait<1>();
         producers_sync();
         issue(k + 2);
-        float2* st = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
-        // x~ B for the stage's centres, in place over the B block
-        for (int e = tid; e < kStageCentres * blk[0].len; e += kProducers) {
-          const int i = e / blk[0].len, j = e - i * blk[0].len;
-          float2* sp = st + i * sc;
-          float2 x = sp[xsel];
-          x.y *= xsgn;
-          float2 b = sp[bstart[0] + j];
-          b.y *= bsgn;
-          sp[bstart[0] + j] = make_float2(x.x * b.x - x.y * b.y, x.x * b.y + x.y * b.x);
-        }
-        producers_sync();
+        const float2* st = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
         if (!mbar_wait(&empty[slot], ph ^ 1u, budget)) err = 1;
         tc_fence_after();
         // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
@@ -425,40 +472,63 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
             a.y *= sgnA;
             const float v0 = bo ? a.y : a.x;
             const float v1 = bo ? a.x : -a.y;
-            if (kBF16) {
+            if (PREC == EXT4PCF_SPLIT_BF16) {
               uint32_t h, l;
               split_bf16(v0, v1, h, l);
               const uint32_t off = sw128_word_off(bn, i, kMaxNpad);
               *reinterpret_cast<uint32_t*>(bt + off) = h;
               *reinterpret_cast<uint32_t*>(bt + tile_bytes + off) = l;
-            } else {
+            } else if (PREC == EXT4PCF_TF32) {
               *reinterpret_cast<float2*>(bt + sw128_word_off(bn, 2 * i, kMaxNpad)) = make_float2(v0, v1);
+            } else {
+              uint32_t h0, l0, h1, l1;
+              split_tf32(v0, h0, l0);
+              split_tf32(v1, h1, l1);
+              const uint32_t off = sw128_word_off(bn, 2 * i, kMaxNpad);
+              *reinterpret_cast<uint2*>(bt + off) = make_uint2(h0, h1);
+              *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + off) = make_uint2(l0, l1);
             }
           }
         }
-        // A operand (TMEM): this row's Khatri-Rao values for 8 centres
-        uint32_t w[16];
+        // A operand (TMEM): this row's Khatri-Rao values x~B * C for 8 centres
+        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * P::kStageCols;
+        if (PREC == EXT4PCF_SPLIT_BF16) {
+          uint32_t w[16];
 #pragma unroll
-        for (int j = 0; j < kQuarter; ++j) {
-          const float2* sp = st + (quarter * kQuarter + j) * sc;
-          float2 xb = sp[iB], cv = sp[iC];
-          xb.y *= sgnB;
-          cv.y *= sgnC;
-          const float kr_re = xb.x * cv.x - xb.y * cv.y;
-          const float kr_im = xb.x * cv.y + xb.y * cv.x;
-          if (kBF16) {
-            split_bf16(kr_re, kr_im, w[j], w[8 + j]);
-          } else {
-            w[2 * j] = __float_as_uint(kr_re);
-            w[2 * j + 1] = __float_as_uint(kr_im);
+          for (int j = 0; j < kQuarter; ++j) {
+            const float2* sp = st + (quarter * kQuarter + j) * sc;
+            const float2 xb = sp[iB];
+            float2 cv = sp[iC];
+            cv.y *= sgnC;
+            split_bf16(xb.x * cv.x - xb.y * cv.y, xb.x * cv.y + xb.y * cv.x, w[j], w[8 + j]);
           }
-        }
-        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * kStageCols;
-        if (kBF16) {
           tmem_st8(acol + quarter * 8, w);
           tmem_st8(acol + 32 + quarter * 8, w + 8);
-        } else {
+        } else if (PREC == EXT4PCF_TF32) {
+          uint32_t w[16];
+#pragma unroll
+          for (int j = 0; j < kQuarter; ++j) {
+            const float2* sp = st + (quarter * kQuarter + j) * sc;
+            const float2 xb = sp[iB];
+            float2 cv = sp[iC];
+            cv.y *= sgnC;
+            w[2 * j] = __float_as_uint(xb.x * cv.x - xb.y * cv.y);
+            w[2 * j + 1] = __float_as_uint(xb.x * cv.y + xb.y * cv.x);
+          }
           tmem_st16(acol + quarter * 16, w);
+        } else {
+          uint32_t wh[16], wl[16];
+#pragma unroll
+          for (int j = 0; j < kQuarter; ++j) {
+            const float2* sp = st + (quarter * kQuarter + j) * sc;
+            const float2 xb = sp[iB];
+            float2 cv = sp[iC];
+            cv.y *= sgnC;
+            split_tf32(xb.x * cv.x - xb.y * cv.y, wh[2 * j], wl[2 * j]);
+            split_tf32(xb.x * cv.y + xb.y * cv.x, wh[2 * j + 1], wl[2 * j + 1]);
+          }
+          tmem_st16(acol + quarter * 16, wh);
+          tmem_st16(acol + 64 + quarter * 16, wl);
         }
         fence_async_smem();
         tmem_wait_st();
@@ -494,10 +564,10 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
     } else {
       // ------------------------------------------------------------------ MMA issuer
       if (lane == 0) {
-        const uint32_t id = kBF16 ? idesc(1u, npad) : idesc(2u, npad);
+        const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad) : idesc(2u, npad);
         for (int k = 0; k < nstage; ++k, ++gk) {
-          const int slot = (int)(gk % kStages);
-          const uint32_t ph = (uint32_t)((gk / kStages) & 1);
+          const int slot = (int)(gk % kSt);
+          const uint32_t ph = (uint32_t)((gk / kSt) & 1);
           const long long g = gs + k / kPromote;
           const int buf = (int)(g & 1);
           const bool first = (k % kPromote) == 0;
@@ -507,9 +577,9 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
           if (!mbar_wait(&full[slot], ph, budget)) err = 1;
           tc_fence_after();
           const uint32_t d = tmem + buf * kDBuf;
-          const uint32_t a0 = tmem + kDCols + slot * kStageCols;
+          const uint32_t a0 = tmem + kDCols + slot * P::kStageCols;
           const uint32_t b0 = saddr(sm + slot * stage_bytes);
-          if (kBF16) {
+          if (PREC == EXT4PCF_SPLIT_BF16) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {  // K = 16 bf16 = 8 centres per MMA
               const uint64_t bh = desc_sw128(b0 + q * 32), bl = desc_sw128(b0 + tile_bytes + q * 32);
@@ -517,11 +587,20 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
               mma_f16(d, a0 + q * 8, bl, id, 1u);
               mma_f16(d, a0 + 32 + q * 8, bh, id, 1u);
             }
-          } else {
+          } else if (PREC == EXT4PCF_TF32) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {  // K = 8 fp32 = 4 centres per MMA
               const uint64_t b = desc_sw128(b0 + (q >> 2) * tile_bytes + (q & 3) * 32);
               mma_tf32(d, a0 + q * 8, b, id, (!first || q > 0) ? 1u : 0u);
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {  // hi*hi + hi*lo + lo*hi, K = 8 fp32 per MMA
+              const uint32_t bo_ = (q >> 2) * tile_bytes + (q & 3) * 32;
+              const uint64_t bh = desc_sw128(b0 + bo_), bl = desc_sw128(b0 + 2 * tile_bytes + bo_);
+              mma_tf32(d, a0 + q * 8, bh, id, (!first || q > 0) ? 1u : 0u);
+              mma_tf32(d, a0 + q * 8, bl, id, 1u);
+              mma_tf32(d, a0 + 64 + q * 8, bh, id, 1u);
             }
           }
           mma_commit(&empty[slot]);
@@ -539,19 +618,32 @@ __global__ void __launch_bounds__(kThreads, 1) contract_tc_kernel(const TcArgs a
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-size_t tc_smem_bytes(int nb, int N) {
-  return (size_t)kStages * 2 * kMaxNpad * 128 + (size_t)kStageBufs * kStageCentres * stage_values(nb, N) * 8 + 1024 +
-         256;
+size_t tc_smem_bytes(int nb, int N, int prec) {
+  const bool x3 = prec == EXT4PCF_3XTF32;
+  const int st = x3 ? TcPrec<EXT4PCF_3XTF32>::kStages : 4;
+  const int atoms = x3 ? TcPrec<EXT4PCF_3XTF32>::kAtoms : 2;
+  const int sc = stage_values(nb, N);
+  return (size_t)st * atoms * kMaxNpad * 128 + (size_t)kStageBufs * kStageCentres * sc * 8 +
+         (size_t)((sc + 1) & ~1) * 4 + 1024 + 256;
+}
+
+template <int PREC>
+cudaError_t launch_tc(const TcArgs& a, const float2* xb, size_t smem, int sms, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  contract_tc_kernel<PREC><<<sms, kThreads, smem, s>>>(a, xb);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_supported(const Layout& L, int precision) {
-  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32) return false;
-  return 4 * L.nb <= kMaxNpad && L.nb >= 1 && tc_smem_bytes(L.nb, L.N) <= 227 * 1024;
+  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32 && precision != EXT4PCF_3XTF32) return false;
+  return L.nb >= 1 && 4 * L.nb <= kMaxNpad && tc_smem_bytes(L.nb, L.N, precision) <= 227 * 1024;
 }
 
 void tc_build_items(const Layout& L, std::vector<int4>& items) {
@@ -565,38 +657,34 @@ void tc_build_items(const Layout& L, std::vector<int4>& items) {
     }
 }
 
-size_t contract_tc_scratch(const Layout& L, int) {
-  std::vector<int4> it;
-  tc_build_items(L, it);
-  return it.size() * sizeof(int4);
+size_t contract_tc_xb_bytes(const Layout& L, int T) {
+  return (size_t)T * kXBTypes * (2 * L.N + 1) * L.nb * sizeof(float2);
 }
 
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, double* ups,
-                             int precision, void* scratch, size_t scratch_bytes, int* status, long long timeout,
-                             cudaStream_t s) {
+                             int precision, const int4* items, int n_items, float2* xb, int* status,
+                             long long timeout, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
-  // items are written once into scratch by the caller (tc_upload_items); count them here
-  const int n_items = (int)(scratch_bytes / sizeof(int4));
+  {
+    const size_t total = (size_t)T * kXBTypes * (2 * L.N + 1) * L.nb;
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 65536);
+    xb_kernel<<<blocks, 256, 0, s>>>(L, rec, xw, T, xb);
+    ++g_launches;
+  }
   TcArgs a;
   a.L = L; a.rec = rec; a.xw = xw; a.T = T; a.ups = ups;
-  a.items = static_cast<const int4*>(scratch); a.n_items = n_items;
+  a.items = items; a.n_items = n_items;
   a.timeout = timeout; a.status = status;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = tc_smem_bytes(L.nb, L.N);
+  const size_t smem = tc_smem_bytes(L.nb, L.N, precision);
   cudaError_t e;
-  if (precision == EXT4PCF_SPLIT_BF16) {
-    e = cudaFuncSetAttribute(contract_tc_kernel<EXT4PCF_SPLIT_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    contract_tc_kernel<EXT4PCF_SPLIT_BF16><<<sms, kThreads, smem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(contract_tc_kernel<EXT4PCF_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    contract_tc_kernel<EXT4PCF_TF32><<<sms, kThreads, smem, s>>>(a);
-  }
+  if (precision == EXT4PCF_SPLIT_BF16) e = launch_tc<EXT4PCF_SPLIT_BF16>(a, xb, smem, sms, s);
+  else if (precision == EXT4PCF_TF32) e = launch_tc<EXT4PCF_TF32>(a, xb, smem, sms, s);
+  else e = launch_tc<EXT4PCF_3XTF32>(a, xb, smem, sms, s);
   ++g_launches;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace ext4pcf

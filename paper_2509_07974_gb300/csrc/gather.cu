@@ -10,11 +10,12 @@
 //       summation order is deterministic).  Chunks hold up to `cap` pairs; long neighbour
 //       lists take several chunks.
 //   (b) warp k owns the powers m in [k*MB, k*MB+MB) of u = e^{i phi_ij}: each lane takes
-//       pairs of a bin, raises u to the block's first power (u^MB is stored per pair) and
-//       walks the block by recurrence in registers, accumulating the seven quantities
-//       x u^m, x u^-m, x^2 u^m, x^2 u^-m, w u^m, |x|^2 u^m, w^2 u^m.  At the end of a bin
-//       the 32 lanes' partial sums are combined by a transposed butterfly (each lane ends
-//       with V/32 totals) and added to the centre's record in shared memory.
+//       two pairs of a bin at a time, raises u to the block's first power (u^MB is stored
+//       per pair) and walks the block by recurrence in registers, accumulating seven real
+//       weights times u^m: Re x, Im x, Re x^2, Im x^2, w, |x|^2, w^2 (two FMAs each).  The
+//       complex sums x u^{+-m} and x^2 u^{+-m} follow from the first four at the end of the
+//       bin.  The 32 lanes' partial sums are then combined by a transposed butterfly (each
+//       lane ends with V/32 totals) and added to the centre's record in shared memory.
 //   (c) the record is written to the wave buffer.
 // FP64 variant: positions and arithmetic in double; the bin decision r^2 = dx*dx + dy*dy is
 // evaluated with two rounded products and one rounded sum, as the FP64 definition reads.
@@ -336,14 +337,16 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
 #pragma unroll
             for (int t = 0; t < MB; ++t) {
               if (t < mb) {
-                a[14 * t + 0] += xr0 * pr0 - xi0 * pi0 + xr1 * pr1 - xi1 * pi1;
-                a[14 * t + 1] += xr0 * pi0 + xi0 * pr0 + xr1 * pi1 + xi1 * pr1;
-                a[14 * t + 2] += xr0 * pr0 + xi0 * pi0 + xr1 * pr1 + xi1 * pi1;
-                a[14 * t + 3] += xi0 * pr0 - xr0 * pi0 + xi1 * pr1 - xr1 * pi1;
-                a[14 * t + 4] += x2r0 * pr0 - x2i0 * pi0 + x2r1 * pr1 - x2i1 * pi1;
-                a[14 * t + 5] += x2r0 * pi0 + x2i0 * pr0 + x2r1 * pi1 + x2i1 * pr1;
-                a[14 * t + 6] += x2r0 * pr0 + x2i0 * pi0 + x2r1 * pr1 + x2i1 * pi1;
-                a[14 * t + 7] += x2i0 * pr0 - x2r0 * pi0 + x2i1 * pr1 - x2r1 * pi1;
+                // real weights Re x, Im x, Re x^2, Im x^2 times u^m; G_{+-m} and XX_{+-m}
+                // follow from them at the end of the bin (see below)
+                a[14 * t + 0] += xr0 * pr0 + xr1 * pr1;
+                a[14 * t + 1] += xr0 * pi0 + xr1 * pi1;
+                a[14 * t + 2] += xi0 * pr0 + xi1 * pr1;
+                a[14 * t + 3] += xi0 * pi0 + xi1 * pi1;
+                a[14 * t + 4] += x2r0 * pr0 + x2r1 * pr1;
+                a[14 * t + 5] += x2r0 * pi0 + x2r1 * pi1;
+                a[14 * t + 6] += x2i0 * pr0 + x2i1 * pr1;
+                a[14 * t + 7] += x2i0 * pi0 + x2i1 * pi1;
                 a[14 * t + 8] += w0 * pr0 + w1 * pr1;
                 a[14 * t + 9] += w0 * pi0 + w1 * pi1;
                 a[14 * t + 10] += xa0 * pr0 + xa1 * pr1;
@@ -384,6 +387,19 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
             }
           };
           for (int e = s0 + lane; e < s1; e += 64) accumulate(e, e + 32);
+          // with R = sum Re(x) u^m = (a0, a1) and I = sum Im(x) u^m = (a2, a3):
+          //   sum x u^m = (a0 - a3, a1 + a2),  sum x conj(u^m) = (a0 + a3, a2 - a1)
+#pragma unroll
+          for (int t = 0; t < MB; ++t) {
+#pragma unroll
+            for (int q = 0; q < 8; q += 4) {
+              const R r0 = a[14 * t + q], r1 = a[14 * t + q + 1], i0 = a[14 * t + q + 2], i1 = a[14 * t + q + 3];
+              a[14 * t + q] = r0 - i1;
+              a[14 * t + q + 1] = r1 + i0;
+              a[14 * t + q + 2] = r0 + i1;
+              a[14 * t + q + 3] = i0 - r1;
+            }
+          }
           reduce_transpose<R, V>(a, lane);
           const int base = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
                            (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
