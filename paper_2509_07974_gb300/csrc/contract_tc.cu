@@ -14,7 +14,7 @@
 //   * B operand (shared memory, K-major, 128-byte swizzle): column (mu, Th1, re|im) holds
 //     the real embedding of A_i^mu(Th1): K rows (2i, 2i+1) = (Ar, -Ai) for the real output
 //     and (Ai, Ar) for the imaginary output, so that D = A_op B_op is the complex product.
-//   * D (TMEM, FP32): 128 rows x (2 * #mu * nb, padded to 16) columns.  Every 256 centres the
+//   * D (TMEM, FP32): 128 rows x (2 * #mu * nb, padded to 16) columns.  Every 64 centres the
 //     partial sum is promoted out of TMEM into FP32 registers (two D buffers alternate, so
 //     the MMAs run on meanwhile); the long FP32 accumulation inside the tensor core would
 //     otherwise lose bits.  The epilogue adds the sums into the FP64 output.
@@ -290,7 +290,10 @@ __host__ __device__ inline int stage_values(int nb, int N) {
   if (rows > 2 * N + 1) rows = 2 * N + 1;
   return (1 + 2 * rows * nb + 2 * nb) | 1;
 }
-constexpr int kPromote = 8;  // stages per TMEM partial sum (256 centres)
+// stages per TMEM partial sum (64 centres): the tensor core's FP32 accumulation loses bits
+// in proportion to the MMAs it accumulates (measured: ~3e-4 over 750 MMAs, ~5e-5 over
+// 96, ~1.5e-4 over 192 for 3xTF32), so partial sums are short and summed in registers
+constexpr int kPromote = 2;
 constexpr int kDBuf = 64;    // two D buffers of 64 columns (npad <= 64)
 constexpr int kQuarter = kStageCentres / (kProducerWarps / 4);  // centres per producer warp
 
