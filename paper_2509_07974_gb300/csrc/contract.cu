@@ -143,8 +143,10 @@ contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx
         for (int k = 0; k < NBT; ++k) {
           if (k < nb) {
             const Cx a = sA[cc * NBT + k];
-            acc[k].x += a.x * kr.x - a.y * kr.y;
-            acc[k].y += a.x * kr.y + a.y * kr.x;
+            acc[k].x += a.x * kr.x;  // separate multiply-adds: a sum of products would
+            acc[k].x -= a.y * kr.y;  // cost an extra multiply and add
+            acc[k].y += a.x * kr.y;
+            acc[k].y += a.y * kr.x;
           }
         }
       }

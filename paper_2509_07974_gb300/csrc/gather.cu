@@ -334,32 +334,37 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
             const R x2r0 = xr0 * xr0 - xi0 * xi0, x2i0 = R(2) * xr0 * xi0, xa0 = xr0 * xr0 + xi0 * xi0;
             const R x2r1 = xr1 * xr1 - xi1 * xi1, x2i1 = R(2) * xr1 * xi1, xa1 = xr1 * xr1 + xi1 * xi1;
             const R ww0 = w0 * w0, ww1 = w1 * w1;
+            // one power at a time; every slot is updated by two separate multiply-adds
+            // (a sum of products would cost a multiply, a fused multiply-add and an add)
+            auto step = [&](int t) {
+              a[14 * t + 0] += xr0 * pr0;   a[14 * t + 0] += xr1 * pr1;
+              a[14 * t + 1] += xr0 * pi0;   a[14 * t + 1] += xr1 * pi1;
+              a[14 * t + 2] += xi0 * pr0;   a[14 * t + 2] += xi1 * pr1;
+              a[14 * t + 3] += xi0 * pi0;   a[14 * t + 3] += xi1 * pi1;
+              a[14 * t + 4] += x2r0 * pr0;  a[14 * t + 4] += x2r1 * pr1;
+              a[14 * t + 5] += x2r0 * pi0;  a[14 * t + 5] += x2r1 * pi1;
+              a[14 * t + 6] += x2i0 * pr0;  a[14 * t + 6] += x2i1 * pr1;
+              a[14 * t + 7] += x2i0 * pi0;  a[14 * t + 7] += x2i1 * pi1;
+              a[14 * t + 8] += w0 * pr0;    a[14 * t + 8] += w1 * pr1;
+              a[14 * t + 9] += w0 * pi0;    a[14 * t + 9] += w1 * pi1;
+              a[14 * t + 10] += xa0 * pr0;  a[14 * t + 10] += xa1 * pr1;
+              a[14 * t + 11] += xa0 * pi0;  a[14 * t + 11] += xa1 * pi1;
+              a[14 * t + 12] += ww0 * pr0;  a[14 * t + 12] += ww1 * pr1;
+              a[14 * t + 13] += ww0 * pi0;  a[14 * t + 13] += ww1 * pi1;
+              const R n0 = pr0 * ur0 - pi0 * ui0;
+              pi0 = pr0 * ui0 + pi0 * ur0;
+              pr0 = n0;
+              const R n1 = pr1 * ur1 - pi1 * ui1;
+              pi1 = pr1 * ui1 + pi1 * ur1;
+              pr1 = n1;
+            };
+            if (mb == MB) {  // the common case: a full block, no predicates
 #pragma unroll
-            for (int t = 0; t < MB; ++t) {
-              if (t < mb) {
-                // real weights Re x, Im x, Re x^2, Im x^2 times u^m; G_{+-m} and XX_{+-m}
-                // follow from them at the end of the bin (see below)
-                a[14 * t + 0] += xr0 * pr0 + xr1 * pr1;
-                a[14 * t + 1] += xr0 * pi0 + xr1 * pi1;
-                a[14 * t + 2] += xi0 * pr0 + xi1 * pr1;
-                a[14 * t + 3] += xi0 * pi0 + xi1 * pi1;
-                a[14 * t + 4] += x2r0 * pr0 + x2r1 * pr1;
-                a[14 * t + 5] += x2r0 * pi0 + x2r1 * pi1;
-                a[14 * t + 6] += x2i0 * pr0 + x2i1 * pr1;
-                a[14 * t + 7] += x2i0 * pi0 + x2i1 * pi1;
-                a[14 * t + 8] += w0 * pr0 + w1 * pr1;
-                a[14 * t + 9] += w0 * pi0 + w1 * pi1;
-                a[14 * t + 10] += xa0 * pr0 + xa1 * pr1;
-                a[14 * t + 11] += xa0 * pi0 + xa1 * pi1;
-                a[14 * t + 12] += ww0 * pr0 + ww1 * pr1;
-                a[14 * t + 13] += ww0 * pi0 + ww1 * pi1;
-                const R n0 = pr0 * ur0 - pi0 * ui0;
-                pi0 = pr0 * ui0 + pi0 * ur0;
-                pr0 = n0;
-                const R n1 = pr1 * ur1 - pi1 * ui1;
-                pi1 = pr1 * ui1 + pi1 * ur1;
-                pr1 = n1;
-              }
+              for (int t = 0; t < MB; ++t) step(t);
+            } else {
+#pragma unroll
+              for (int t = 0; t < MB; ++t)
+                if (t < mb) step(t);
             }
             if (m0 == 0) {
               // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3 (the second pair is zero if absent)
