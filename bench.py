@@ -400,7 +400,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3"])
+    ap.add_argument("--precision", default="3xtf32", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3"])
     ap.add_argument("--oracle-centres", type=int, default=2000)
     ap.add_argument("--fp64-centres", type=int, default=4096)
     ap.add_argument("--no-baselines", action="store_true")
