@@ -406,6 +406,13 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       if (!row_ok) { iB = 0; iC = 0; }
       // B-operand words of this thread: column bn, centres [4 bq, 4 bq + 4)
       const int bn = tid >> 3, bq = tid & 7;
+      uint32_t boff[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        boff[j] = PREC == EXT4PCF_SPLIT_BF16 ? sw128_word_off(bn, bq * 4 + j, kMaxNpad)
+                                             : sw128_word_off(bn, 2 * (bq * 4 + j), kMaxNpad);
+      const float2* const a_base = nullptr;  // (the A values are read at st + i * sc + iA)
+      (void)a_base;
       int iA = 0, bo = 0;
       float sgnA = 1.f;
       if (bn < ncols) {
@@ -415,21 +422,41 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         iA = (g ? bA1 : bA0) + blk_index(g ? bkA1 : bkA0, kr.A[g], s, b1, nb, cjA);
         sgnA = cjA ? -1.f : 1.f;
       }
-      // copy one stage's slices (16 threads per centre); tails are zero-filled
+      // copy plan of this thread for every stage (16 threads per centre): staged slots
+      // e = 1 + sub + 16 j, each read from the x~B array (source offset >= 0 relative to the
+      // item's x~B row block) or from the record (offset encoded as -1 - offset)
+      constexpr int kMaxCopies = 12;  // 16 * 12 >= stage_values(nb, N) for every supported shape
+      int csrc[kMaxCopies];
+      int ncopy = 0;
+      {
+        const int sub = tid & 15;
+#pragma unroll
+        for (int j = 0; j < kMaxCopies; ++j) {
+          const int e = 1 + sub + 16 * j;
+          csrc[j] = 0x7FFFFFFF;  // nothing to copy
+          if (e < sc) {
+            if (e < bC) csrc[j] = e - 1;
+            else if (gmap[e] >= 0) csrc[j] = -1 - gmap[e];
+            ncopy = j + 1;
+          }
+        }
+      }
+      // copy one stage's slices; tails are zero-filled
       auto issue = [&](int k) {
         if (k < nstage) {
           float2* d = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max + (tid >> 4) * sc;
           const int sub = tid & 15, c = k * kStageCentres + (tid >> 4);
           if (c < args.T) {
             if (sub == 0) d[0] = make_float2(0.f, 0.f);
-            const float2* xs = xbarr + (size_t)c * xb_stride + xb_off - 1;
+            const float2* xs = xbarr + (size_t)c * xb_stride + xb_off;
             const float2* rc = args.rec + (size_t)c * L.rec;
-            for (int e = 1 + sub; e < sc; e += 16) {
-              if (e < bC) {
-                cp_async8(d + e, xs + e);
-              } else {
-                const int m = gmap[e];
-                if (m >= 0) cp_async8(d + e, rc + m);
+            float2* dd = d + 1 + sub;
+#pragma unroll
+            for (int j = 0; j < kMaxCopies; ++j) {
+              if (j < ncopy) {
+                const int o = csrc[j];
+                if (o >= 0 && o != 0x7FFFFFFF) cp_async8(dd + 16 * j, xs + o);
+                else if (o < 0) cp_async8(dd + 16 * j, rc + (-1 - o));
               }
             }
           } else {
@@ -468,40 +495,39 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
         unsigned char* bt = sm + slot * stage_bytes;
         if (bn < npad) {
+          const float2* ap = st + bq * 4 * sc + iA;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const int i = bq * 4 + j;
-            float2 a = st[i * sc + iA];
+            float2 a = ap[j * sc];
             a.y *= sgnA;
             const float v0 = bo ? a.y : a.x;
             const float v1 = bo ? a.x : -a.y;
             if (PREC == EXT4PCF_SPLIT_BF16) {
               uint32_t h, l;
               split_bf16(v0, v1, h, l);
-              const uint32_t off = sw128_word_off(bn, i, kMaxNpad);
-              *reinterpret_cast<uint32_t*>(bt + off) = h;
-              *reinterpret_cast<uint32_t*>(bt + tile_bytes + off) = l;
+              *reinterpret_cast<uint32_t*>(bt + boff[j]) = h;
+              *reinterpret_cast<uint32_t*>(bt + tile_bytes + boff[j]) = l;
             } else if (PREC == EXT4PCF_TF32) {
-              *reinterpret_cast<float2*>(bt + sw128_word_off(bn, 2 * i, kMaxNpad)) = make_float2(v0, v1);
+              *reinterpret_cast<float2*>(bt + boff[j]) = make_float2(v0, v1);
             } else {
               uint32_t h0, l0, h1, l1;
               split_tf32(v0, h0, l0);
               split_tf32(v1, h1, l1);
-              const uint32_t off = sw128_word_off(bn, 2 * i, kMaxNpad);
-              *reinterpret_cast<uint2*>(bt + off) = make_uint2(h0, h1);
-              *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + off) = make_uint2(l0, l1);
+              *reinterpret_cast<uint2*>(bt + boff[j]) = make_uint2(h0, h1);
+              *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + boff[j]) = make_uint2(l0, l1);
             }
           }
         }
         // A operand (TMEM): this row's Khatri-Rao values x~B * C for 8 centres
+        const float2* qB = st + quarter * kQuarter * sc + iB;
+        const float2* qC = st + quarter * kQuarter * sc + iC;
         const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * P::kStageCols;
         if (PREC == EXT4PCF_SPLIT_BF16) {
           uint32_t w[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
-            const float2* sp = st + (quarter * kQuarter + j) * sc;
-            const float2 xb = sp[iB];
-            float2 cv = sp[iC];
+            const float2 xb = qB[j * sc];
+            float2 cv = qC[j * sc];
             cv.y *= sgnC;
             split_bf16(xb.x * cv.x - xb.y * cv.y, xb.x * cv.y + xb.y * cv.x, w[j], w[8 + j]);
           }
@@ -511,9 +537,8 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           uint32_t w[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
-            const float2* sp = st + (quarter * kQuarter + j) * sc;
-            const float2 xb = sp[iB];
-            float2 cv = sp[iC];
+            const float2 xb = qB[j * sc];
+            float2 cv = qC[j * sc];
             cv.y *= sgnC;
             w[2 * j] = __float_as_uint(xb.x * cv.x - xb.y * cv.y);
             w[2 * j + 1] = __float_as_uint(xb.x * cv.y + xb.y * cv.x);
@@ -523,9 +548,8 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           uint32_t wh[16], wl[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
-            const float2* sp = st + (quarter * kQuarter + j) * sc;
-            const float2 xb = sp[iB];
-            float2 cv = sp[iC];
+            const float2 xb = qB[j * sc];
+            float2 cv = qC[j * sc];
             cv.y *= sgnC;
             split_tf32(xb.x * cv.x - xb.y * cv.y, wh[2 * j], wl[2 * j]);
             split_tf32(xb.x * cv.y + xb.y * cv.x, wh[2 * j + 1], wl[2 * j + 1]);

@@ -33,6 +33,37 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRows = 64;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// One bucketed pair in shared memory: u = e^{i phi}, v = u^mb, x = w gamma_c, w.
+template <typename R> struct Ent;
+template <> struct Ent<float> {
+  float4 uv;  // (u_re, u_im, v_re, v_im)
+  float4 xw;  // (x_re, x_im, w, 0)
+};
+template <> struct Ent<double> {
+  double2 u, v, x, w;
+};
+__device__ __forceinline__ void ent_store(Ent<float>* e, float ur, float ui, float vr, float vi, float xr, float xi, float w) {
+  e->uv = make_float4(ur, ui, vr, vi);
+  e->xw = make_float4(xr, xi, w, 0.f);
+}
+__device__ __forceinline__ void ent_store(Ent<double>* e, double ur, double ui, double vr, double vi, double xr, double xi,
+                                          double w) {
+  e->u = make_double2(ur, ui);
+  e->v = make_double2(vr, vi);
+  e->x = make_double2(xr, xi);
+  e->w = make_double2(w, 0.0);
+}
+__device__ __forceinline__ void ent_load(const Ent<float>* e, float& ur, float& ui, float& vr, float& vi, float& xr, float& xi,
+                                         float& w) {
+  const float4 a = e->uv, b = e->xw;
+  ur = a.x; ui = a.y; vr = a.z; vi = a.w; xr = b.x; xi = b.y; w = b.z;
+}
+__device__ __forceinline__ void ent_load(const Ent<double>* e, double& ur, double& ui, double& vr, double& vi, double& xr,
+                                         double& xi, double& w) {
+  const double2 u = e->u, v = e->v, x = e->x;
+  ur = u.x; ui = u.y; vr = v.x; vi = v.y; xr = x.x; xi = x.y; w = e->w.x;
+}
+
 template <typename R, int MB> struct GCfg {
   static constexpr int kRaw = 14 * MB + 10;
   static constexpr int V = (kRaw + 31) / 32 * 32;
@@ -181,15 +212,9 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
 
-  Cx* acc = reinterpret_cast<Cx*>(smem);
-  R* eur = reinterpret_cast<R*>(acc + L.rec);
-  R* eui = eur + cap;
-  R* evr = eui + cap;
-  R* evi = evr + cap;
-  R* exr = evi + cap;
-  R* exi = exr + cap;
-  R* ew = exi + cap;
-  double* e2 = reinterpret_cast<double*>(ew + cap);
+  Ent<R>* ent = reinterpret_cast<Ent<R>*>(smem);
+  Cx* acc = reinterpret_cast<Cx*>(ent + cap);
+  double* e2 = reinterpret_cast<double*>(acc + L.rec);
   float* e2f = reinterpret_cast<float*>(e2 + 65);
   float* win = e2f + 65;
   int* cnt = reinterpret_cast<int*>(win + 65);
@@ -302,8 +327,7 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
           const int dst = off[b] + run[b] + pre + (int)rank;
           R vr, vi;
           cpow<R>(ur, ui, mb, vr, vi);
-          eur[dst] = ur; eui[dst] = ui; evr[dst] = vr; evi[dst] = vi;
-          exr[dst] = xr; exi[dst] = xi; ew[dst] = ww;
+          ent_store(&ent[dst], ur, ui, vr, vi, xr, xi, ww);
         }
         __syncthreads();
         if (tid < nb) {
@@ -325,12 +349,13 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
           // two pairs per lane and iteration: two independent power recurrences
           auto accumulate = [&](int e0, int e1) {
             const bool two = e1 < s1;
-            const R ur0 = eur[e0], ui0 = eui[e0], xr0 = exr[e0], xi0 = exi[e0], w0 = ew[e0];
-            const R ur1 = two ? eur[e1] : R(0), ui1 = two ? eui[e1] : R(0);
-            const R xr1 = two ? exr[e1] : R(0), xi1 = two ? exi[e1] : R(0), w1 = two ? ew[e1] : R(0);
+            R ur0, ui0, vr0, vi0, xr0, xi0, w0, ur1, ui1, vr1, vi1, xr1, xi1, w1;
+            ent_load(&ent[e0], ur0, ui0, vr0, vi0, xr0, xi0, w0);
+            ent_load(&ent[two ? e1 : e0], ur1, ui1, vr1, vi1, xr1, xi1, w1);
+            if (!two) { xr1 = R(0); xi1 = R(0); w1 = R(0); }  // the second pair adds nothing
             R pr0, pi0, pr1, pi1;
-            cpow5<R>(evr[e0], evi[e0], k, pr0, pi0);
-            cpow5<R>(two ? evr[e1] : R(1), two ? evi[e1] : R(0), k, pr1, pi1);
+            cpow5<R>(vr0, vi0, k, pr0, pi0);
+            cpow5<R>(vr1, vi1, k, pr1, pi1);
             const R x2r0 = xr0 * xr0 - xi0 * xi0, x2i0 = R(2) * xr0 * xi0, xa0 = xr0 * xr0 + xi0 * xi0;
             const R x2r1 = xr1 * xr1 - xi1 * xi1, x2i1 = R(2) * xr1 * xi1, xa1 = xr1 * xr1 + xi1 * xi1;
             const R ww0 = w0 * w0, ww1 = w1 * w1;
@@ -478,12 +503,12 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
                        (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64;
   const size_t budget = 227 * 1024;
-  if (fixed + 7 * sizeof(R) * kThreads > budget) return cudaErrorInvalidConfiguration;
-  int cap = (int)((budget - fixed) / (7 * sizeof(R)));
+  if (fixed + sizeof(Ent<R>) * kThreads > budget) return cudaErrorInvalidConfiguration;
+  int cap = (int)((budget - fixed) / sizeof(Ent<R>));
   cap = cap / kThreads * kThreads;
   if (cap > 8192) cap = 8192;
   a.cap = cap;
-  const size_t smem = fixed + (size_t)cap * 7 * sizeof(R);
+  const size_t smem = fixed + (size_t)cap * sizeof(Ent<R>);
   cudaError_t e = cudaFuncSetAttribute(gather_kernel<R, MB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
