@@ -426,42 +426,44 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       // e = 1 + sub + 16 j, each read from the x~B array (source offset >= 0 relative to the
       // item's x~B row block) or from the record (offset encoded as -1 - offset)
       constexpr int kMaxCopies = 12;  // 16 * 12 >= stage_values(nb, N) for every supported shape
-      int csrc[kMaxCopies];
-      int ncopy = 0;
+      int coff[kMaxCopies];            // source offset (complex elements) of staged slot j
+      unsigned from_xb = 0, active = 0;
       {
         const int sub = tid & 15;
 #pragma unroll
         for (int j = 0; j < kMaxCopies; ++j) {
           const int e = 1 + sub + 16 * j;
-          csrc[j] = 0x7FFFFFFF;  // nothing to copy
+          coff[j] = 0;
           if (e < sc) {
-            if (e < bC) csrc[j] = e - 1;
-            else if (gmap[e] >= 0) csrc[j] = -1 - gmap[e];
-            ncopy = j + 1;
+            if (e < bC) { coff[j] = e - 1; from_xb |= 1u << j; active |= 1u << j; }
+            else if (gmap[e] >= 0) { coff[j] = gmap[e]; active |= 1u << j; }
           }
         }
       }
-      // copy one stage's slices; tails are zero-filled
+      // source pointers of the next stage to fetch (advanced by 32 centres per stage)
+      const int ci0 = tid >> 4;
+      const float2* xs_next = xbarr + (size_t)ci0 * xb_stride + xb_off;
+      const float2* rc_next = args.rec + (size_t)ci0 * L.rec;
+      const size_t xs_step = (size_t)kStageCentres * xb_stride, rc_step = (size_t)kStageCentres * L.rec;
+      int fetch_buf = 0;  // staging buffer of the next stage to fetch
+      // copy one stage's slices (stages are fetched in order); tails are zero-filled
       auto issue = [&](int k) {
         if (k < nstage) {
-          float2* d = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max + (tid >> 4) * sc;
-          const int sub = tid & 15, c = k * kStageCentres + (tid >> 4);
+          float2* d = stg + (size_t)fetch_buf * kStageCentres * sc_max + ci0 * sc;
+          const int sub = tid & 15, c = k * kStageCentres + ci0;
           if (c < args.T) {
             if (sub == 0) d[0] = make_float2(0.f, 0.f);
-            const float2* xs = xbarr + (size_t)c * xb_stride + xb_off;
-            const float2* rc = args.rec + (size_t)c * L.rec;
             float2* dd = d + 1 + sub;
 #pragma unroll
             for (int j = 0; j < kMaxCopies; ++j) {
-              if (j < ncopy) {
-                const int o = csrc[j];
-                if (o >= 0 && o != 0x7FFFFFFF) cp_async8(dd + 16 * j, xs + o);
-                else if (o < 0) cp_async8(dd + 16 * j, rc + (-1 - o));
-              }
+              if (active & (1u << j)) cp_async8(dd + 16 * j, ((from_xb >> j) & 1u ? xs_next : rc_next) + coff[j]);
             }
           } else {
             for (int e = sub; e < sc; e += 16) d[e] = make_float2(0.f, 0.f);
           }
+          xs_next += xs_step;
+          rc_next += rc_step;
+          fetch_buf = fetch_buf == kStageBufs - 1 ? 0 : fetch_buf + 1;
         }
         cp_async_commit();
       };
@@ -483,13 +485,15 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         mbar_arrive(&dempty[buf]);
       };
       const long long gs0 = gs;
+      int slot = (int)(gk % kSt);
+      uint32_t ph = (uint32_t)((gk / kSt) & 1);
+      int read_buf = 0;
       for (int k = 0; k < nstage; ++k, ++gk) {
-        const int slot = (int)(gk % kSt);
-        const uint32_t ph = (uint32_t)((gk / kSt) & 1);
         cp_async_wait<1>();
         producers_sync();
         issue(k + 2);
-        const float2* st = stg + (size_t)(k % kStageBufs) * kStageCentres * sc_max;
+        const float2* st = stg + (size_t)read_buf * kStageCentres * sc_max;
+        read_buf = read_buf == kStageBufs - 1 ? 0 : read_buf + 1;
         if (!mbar_wait(&empty[slot], ph ^ 1u, budget)) err = 1;
         tc_fence_after();
         // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
@@ -561,6 +565,7 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         tmem_wait_st();
         tc_fence_before();
         mbar_arrive(&full[slot]);
+        if (++slot == kSt) { slot = 0; ph ^= 1u; }
         // a partial sum finished one promotion block ago is read while the MMAs run on
         if ((k % kPromote) == kPromote - 1 && k / kPromote >= 1) promote(gs0 + k / kPromote - 1);
       }
@@ -592,9 +597,9 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       // ------------------------------------------------------------------ MMA issuer
       if (lane == 0) {
         const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad) : idesc(2u, npad);
+        int slot = (int)(gk % kSt);
+        uint32_t ph = (uint32_t)((gk / kSt) & 1);
         for (int k = 0; k < nstage; ++k, ++gk) {
-          const int slot = (int)(gk % kSt);
-          const uint32_t ph = (uint32_t)((gk / kSt) & 1);
           const long long g = gs + k / kPromote;
           const int buf = (int)(g & 1);
           const bool first = (k % kPromote) == 0;
@@ -632,6 +637,7 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           }
           mma_commit(&empty[slot]);
           if ((k % kPromote) == kPromote - 1 || k == nstage - 1) mma_commit(&dfull[buf]);
+          if (++slot == kSt) { slot = 0; ph ^= 1u; }
         }
       } else {
         gk += nstage;

@@ -33,36 +33,17 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRows = 64;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// One bucketed pair in shared memory: u = e^{i phi}, v = u^mb, x = w gamma_c, w.
-template <typename R> struct Ent;
-template <> struct Ent<float> {
-  float4 uv;  // (u_re, u_im, v_re, v_im)
-  float4 xw;  // (x_re, x_im, w, 0)
+// Bucketed pairs in shared memory, structure of arrays: uv = (u_re, u_im, v_re, v_im) with
+// u = e^{i phi}, v = u^mb; x = w gamma_c; w.  28 bytes per pair in FP32.
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+struct __align__(16) Dbl4 { double x, y, z, w; };
+template <> struct Vec4<double> { using T = Dbl4; };
+template <typename R> struct EntArrays {
+  typename Vec4<R>::T* uv;
+  cplx_t<R>* x;
+  R* w;
 };
-template <> struct Ent<double> {
-  double2 u, v, x, w;
-};
-__device__ __forceinline__ void ent_store(Ent<float>* e, float ur, float ui, float vr, float vi, float xr, float xi, float w) {
-  e->uv = make_float4(ur, ui, vr, vi);
-  e->xw = make_float4(xr, xi, w, 0.f);
-}
-__device__ __forceinline__ void ent_store(Ent<double>* e, double ur, double ui, double vr, double vi, double xr, double xi,
-                                          double w) {
-  e->u = make_double2(ur, ui);
-  e->v = make_double2(vr, vi);
-  e->x = make_double2(xr, xi);
-  e->w = make_double2(w, 0.0);
-}
-__device__ __forceinline__ void ent_load(const Ent<float>* e, float& ur, float& ui, float& vr, float& vi, float& xr, float& xi,
-                                         float& w) {
-  const float4 a = e->uv, b = e->xw;
-  ur = a.x; ui = a.y; vr = a.z; vi = a.w; xr = b.x; xi = b.y; w = b.z;
-}
-__device__ __forceinline__ void ent_load(const Ent<double>* e, double& ur, double& ui, double& vr, double& vi, double& xr,
-                                         double& xi, double& w) {
-  const double2 u = e->u, v = e->v, x = e->x;
-  ur = u.x; ui = u.y; vr = v.x; vi = v.y; xr = x.x; xi = x.y; w = e->w.x;
-}
 
 template <typename R, int MB> struct GCfg {
   static constexpr int kRaw = 14 * MB + 10;
@@ -212,8 +193,11 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
 
-  Ent<R>* ent = reinterpret_cast<Ent<R>*>(smem);
-  Cx* acc = reinterpret_cast<Cx*>(ent + cap);
+  using V4 = typename Vec4<R>::T;
+  V4* euv = reinterpret_cast<V4*>(smem);
+  Cx* ex = reinterpret_cast<Cx*>(euv + cap);
+  R* ew = reinterpret_cast<R*>(ex + cap);
+  Cx* acc = reinterpret_cast<Cx*>(ew + cap);
   double* e2 = reinterpret_cast<double*>(acc + L.rec);
   float* e2f = reinterpret_cast<float*>(e2 + 65);
   float* win = e2f + 65;
@@ -327,7 +311,11 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
           const int dst = off[b] + run[b] + pre + (int)rank;
           R vr, vi;
           cpow<R>(ur, ui, mb, vr, vi);
-          ent_store(&ent[dst], ur, ui, vr, vi, xr, xi, ww);
+          V4 q;
+          q.x = ur; q.y = ui; q.z = vr; q.w = vi;
+          euv[dst] = q;
+          ex[dst] = cmk<Cx>(xr, xi);
+          ew[dst] = ww;
         }
         __syncthreads();
         if (tid < nb) {
@@ -349,10 +337,14 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
           // two pairs per lane and iteration: two independent power recurrences
           auto accumulate = [&](int e0, int e1) {
             const bool two = e1 < s1;
-            R ur0, ui0, vr0, vi0, xr0, xi0, w0, ur1, ui1, vr1, vi1, xr1, xi1, w1;
-            ent_load(&ent[e0], ur0, ui0, vr0, vi0, xr0, xi0, w0);
-            ent_load(&ent[two ? e1 : e0], ur1, ui1, vr1, vi1, xr1, xi1, w1);
-            if (!two) { xr1 = R(0); xi1 = R(0); w1 = R(0); }  // the second pair adds nothing
+            const int e1c = two ? e1 : e0;
+            const V4 q0 = euv[e0], q1 = euv[e1c];
+            const Cx xx0 = ex[e0], xx1 = ex[e1c];
+            const R ur0 = q0.x, ui0 = q0.y, vr0 = q0.z, vi0 = q0.w;
+            const R ur1 = q1.x, ui1 = q1.y, vr1 = q1.z, vi1 = q1.w;
+            const R xr0 = xx0.x, xi0 = xx0.y, w0 = ew[e0];
+            // the second pair adds nothing when it is absent
+            const R xr1 = two ? xx1.x : R(0), xi1 = two ? xx1.y : R(0), w1 = two ? ew[e1c] : R(0);
             R pr0, pi0, pr1, pi1;
             cpow5<R>(vr0, vi0, k, pr0, pi0);
             cpow5<R>(vr1, vi1, k, pr1, pi1);
@@ -503,12 +495,13 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
                        (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64;
   const size_t budget = 227 * 1024;
-  if (fixed + sizeof(Ent<R>) * kThreads > budget) return cudaErrorInvalidConfiguration;
-  int cap = (int)((budget - fixed) / sizeof(Ent<R>));
+  constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R);
+  if (fixed + per_pair * kThreads > budget) return cudaErrorInvalidConfiguration;
+  int cap = (int)((budget - fixed) / per_pair);
   cap = cap / kThreads * kThreads;
   if (cap > 8192) cap = 8192;
   a.cap = cap;
-  const size_t smem = fixed + (size_t)cap * sizeof(Ent<R>);
+  const size_t smem = fixed + (size_t)cap * per_pair;
   cudaError_t e = cudaFuncSetAttribute(gather_kernel<R, MB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
