@@ -14,9 +14,10 @@ cudaError_t scan_exclusive(unsigned* data, size_t n, unsigned* tmp, cudaStream_t
 cudaError_t real_space(const double* ups, int nb, int N, int nphi, double* gamma, double* norm,
                        double* scratch_norm, double* E_scratch, cudaStream_t s);
 size_t real_space_smem(int N, int nphi);
+int map4_nsplit(int chunk_tri, int ntri, int n_ap);
 cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, int N, int nphi,
                           const double* ap_host, int n_ap, double* E_scratch, double* norm_chunk,
-                          double* gam_chunk, int chunk_tri, double* partial, cudaStream_t s);
+                          double* gam_chunk, int chunk_tri, int nsplit, double* partial, cudaStream_t s);
 cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const double* d_xipm,
                                const double* d_tb, const double* d_area, int nb, const double* d_ap,
                                double* d_m4, double* d_eb, double* d_disc, cudaStream_t s);
@@ -498,7 +499,8 @@ int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radia
   ENSURE(ctx->t_norm, (size_t)chunk * nph2 * 8);
   ENSURE(ctx->t_gam, (size_t)chunk * nph2 * 8 * 16);
   ENSURE(ctx->t_E, (size_t)(2 * n_max + 1) * n_phi * 16);
-  ENSURE(ctx->t_part, (size_t)ntri * n_ap * 8 * 16);
+  const int nsplit = map4_nsplit(chunk, ntri, n_ap);
+  ENSURE(ctx->t_part, (size_t)ntri * nsplit * n_ap * 8 * 16);
   // small buffer: xi_acc [nb*6], tb [nb], area [nb], ap [n_ap], m4 [n_ap*16], eb [n_ap*16], disc [n_ap*16]
   const size_t small = (size_t)n_bins * 8 + n_ap * 49;
   ENSURE(ctx->t_small, small * 8);
@@ -518,11 +520,11 @@ int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radia
     CK(cudaMemcpyAsync(d_small, xi_acc, (size_t)n_bins * 6 * 8,
                        is_device_ptr(xi_acc) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   CK(map4_partials(upsilon, radial_bins, n_bins, n_max, n_phi, ap_radii, n_ap, (double*)ctx->t_E.p,
-                   (double*)ctx->t_norm.p, (double*)ctx->t_gam.p, chunk, (double*)ctx->t_part.p, s));
+                   (double*)ctx->t_norm.p, (double*)ctx->t_gam.p, chunk, nsplit, (double*)ctx->t_part.p, s));
   double* d_m4 = d_small + 8 * n_bins + n_ap;
   double* d_eb = d_m4 + 16 * n_ap;
   double* d_disc = d_eb + 16 * n_ap;
-  CK(map4_finish_launch((const double*)ctx->t_part.p, ntri, n_ap, xi_acc ? d_small : nullptr, d_small + 6 * n_bins,
+  CK(map4_finish_launch((const double*)ctx->t_part.p, ntri * nsplit, n_ap, xi_acc ? d_small : nullptr, d_small + 6 * n_bins,
                         d_small + 7 * n_bins, n_bins, d_small + 8 * n_bins, d_m4, d_eb, d_disc, s));
   std::vector<double> res((size_t)48 * n_ap);
   CK(cudaMemcpyAsync(res.data(), d_m4, res.size() * 8, cudaMemcpyDeviceToHost, s));

@@ -98,6 +98,7 @@ __device__ __forceinline__ Cx centre_factor(const Cx* __restrict__ xw, int c, in
 }
 
 constexpr int kChunk = 32;
+constexpr int kCorrChunk = 128;  // centres staged per pass of the correction kernel
 
 // threads of a contraction block: one per (Theta2, Theta3), rounded up to whole warps
 constexpr int contract_threads(int nbt) {
@@ -178,8 +179,8 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
   const int mu = blockIdx.x / (per_mu + 1);
   const int row = blockIdx.x % (per_mu + 1);
   Cx* sx = reinterpret_cast<Cx*>(smem_raw);
-  Cx* sP = sx + kChunk;
-  Cx* sO = sP + kChunk * nb;
+  Cx* sP = sx + kCorrChunk;
+  Cx* sO = sP + kCorrChunk * nb;
   const int tid = threadIdx.x;
   const Comp cp = kComp[mu];
   const size_t nb2 = (size_t)nb * nb;
@@ -193,8 +194,8 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
     const int ba = tid / nb, bb = tid % nb;
     const bool active = tid < nb * nb;
     Cx acc = cmk<Cx>(R(0), R(0));
-    for (int c0 = 0; c0 < T; c0 += kChunk) {
-      const int nc = min(kChunk, T - c0);
+    for (int c0 = 0; c0 < T; c0 += kCorrChunk) {
+      const int nc = min(kCorrChunk, T - c0);
       for (int k = tid; k < nc * (2 * nb + 1); k += blockDim.x) {
         const int cc = k / (2 * nb + 1), r = k % (2 * nb + 1);
         const Cx* rc = rec + (size_t)(c0 + cc) * L.rec;
@@ -213,18 +214,30 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
       o[1] += (double)acc.y;
     }
   } else {
-    // triple term, thread = bin
-    const int b = tid;
-    Cx acc = cmk<Cx>(R(0), R(0));
-    if (b < nb) {
-      const int k = kTriple[mu];
-      for (int c = 0; c < T; ++c) {
-        const Cx* rc = rec + (size_t)c * L.rec;
-        acc = cadd(acc, cmul(centre_factor(xw, c, cp.xconj), rc[L.TR(k, b)]));
+    // triple term: threads stride over the centres, each summing every bin, then a
+    // fixed-order tree reduction over the threads (one bin at a time)
+    const int k = kTriple[mu];
+    double* red = reinterpret_cast<double*>(smem_raw);  // [2][blockDim]
+    for (int b = 0; b < nb; ++b) {
+      Cx acc = cmk<Cx>(R(0), R(0));
+      for (int c = tid; c < T; c += blockDim.x)
+        acc = cadd(acc, cmul(centre_factor(xw, c, cp.xconj), rec[(size_t)c * L.rec + L.TR(k, b)]));
+      red[tid] = (double)acc.x;
+      red[blockDim.x + tid] = (double)acc.y;
+      __syncthreads();
+      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (tid < st) {
+          red[tid] += red[tid + st];
+          red[blockDim.x + tid] += red[blockDim.x + tid + st];
+        }
+        __syncthreads();
       }
-      double* o = corr + 2 * (mu_base + (size_t)per_mu * nb2 + b);
-      o[0] += (double)acc.x;
-      o[1] += (double)acc.y;
+      if (tid == 0) {
+        double* o = corr + 2 * (mu_base + (size_t)per_mu * nb2 + b);
+        o[0] += red[0];
+        o[1] += red[blockDim.x];
+      }
+      __syncthreads();
     }
   }
 }
@@ -317,8 +330,11 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
   if (T <= 0) return cudaSuccess;
   const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
   const int blocks = 9 * (2 * nn + ns + 1);
-  const int threads = max(64, (L.nb * L.nb + 31) / 32 * 32);
-  const size_t smem = (size_t)kChunk * (1 + 2 * L.nb) * sizeof(cplx_t<R>);
+  const int threads = max(256, (L.nb * L.nb + 31) / 32 * 32);
+  const size_t smem = std::max((size_t)kCorrChunk * (1 + 2 * L.nb) * sizeof(cplx_t<R>),
+                               (size_t)2 * threads * sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(corrections_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, T, corr);
   ++g_launches;
   if (xi_acc) {

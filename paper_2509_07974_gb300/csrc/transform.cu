@@ -112,90 +112,127 @@ __device__ __forceinline__ double2 cm(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// block = (triple in chunk, aperture); threads over angular bins (p, q)
-__global__ void map4_kernel(const Map4Args a, const double2* __restrict__ gam, size_t gam_mu_stride,
-                            double2* __restrict__ partial) {
-  __shared__ double red[16][128];
-  const int lt = blockIdx.x / a.n_ap, ia = blockIdx.x % a.n_ap;
+// block = (triple in chunk, slice of the angular bins).  The aperture-independent part of
+// F_mu (Gamma_mu times the phase and geometric factors times the coefficients P_t R_t of
+// J_mu) is formed once per angular bin, kM4Bins bins at a time, and kept in shared memory;
+// then the threads, one per (mu, aperture) pair, fold the tile into their sums.  Only
+// t <= min(deg P, deg R) contributes: 0 for mu = 0, 2 for one conjugated aperture, 4 for two.
+constexpr int kM4Bins = 16;     // angular bins per tile (kM4Bins * 8 = blockDim items)
+constexpr int kM4Threads = 128;
+constexpr int kM4MaxPairs = 4;  // (mu, aperture) pairs per thread: 8 * 64 / 128
+
+__global__ void __launch_bounds__(kM4Threads) map4_kernel(const Map4Args a, const double2* __restrict__ gam,
+                                                          size_t gam_mu_stride, int nsplit,
+                                                          double2* __restrict__ partial) {
+  __shared__ double2 coef[kM4Bins][8][5];  // Gamma_mu e^{i ph_mu} geo P_t R_t, t <= 4
+  __shared__ double exs[kM4Bins][64];      // e^{-sum|d|^2 / 2 theta^2} per bin and aperture
+  __shared__ double sd2s[kM4Bins];
+  __shared__ double hps[64][5];            // pi t! h^{t+1} / (4 pi theta^4)^4
+  const size_t nph2 = (size_t)a.nphi * a.nphi;
+  const int lt = blockIdx.x / nsplit, split = blockIdx.x % nsplit;
   const int tri = a.tri0 + lt, nb = a.nb;
   const int b1 = tri / (nb * nb), b2 = (tri / nb) % nb, b3 = tri % nb;
   const double t1 = a.tb[b1], t2 = a.tb[b2], t3 = a.tb[b3];
-  const double th = a.ap[ia], th2 = th * th, h = 0.5 * th2;
-  const double q0 = 4.0 * kPi * th2 * th2;
-  const double pref = 2.0 * kPi * t1 * t2 * t3 / (q0 * q0 * q0 * q0) * a.vol[b1] * a.vol[b2] * a.vol[b3];
   const double dphi = 2.0 * kPi / a.nphi;
-  const double w2 = dphi * dphi;
-  double hp[9];  // pi p! h^{p+1}
-  {
+  const double geo = 2.0 * kPi * t1 * t2 * t3 * a.vol[b1] * a.vol[b2] * a.vol[b3] * dphi * dphi;
+  const size_t kbeg = nph2 * split / nsplit, kend = nph2 * (split + 1) / nsplit;
+  for (int ia = threadIdx.x; ia < a.n_ap; ia += blockDim.x) {
+    const double th2 = a.ap[ia] * a.ap[ia], h = 0.5 * th2;
+    const double q0 = 4.0 * kPi * th2 * th2;
+    const double norm = 1.0 / (q0 * q0 * q0 * q0);
     double f = 1.0, hh = h;
-    for (int p = 0; p < 9; ++p) { if (p > 0) f *= p; hp[p] = kPi * f * hh; hh *= h; }
+    for (int t = 0; t < 5; ++t) { if (t > 0) f *= t; hps[ia][t] = kPi * f * hh * norm; hh *= h; }
   }
-  double acc[16];
-  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-  const size_t nph2 = (size_t)a.nphi * a.nphi;
-  for (int k = threadIdx.x; k < a.nphi * a.nphi; k += blockDim.x) {
-    const int p = k / a.nphi, q = k % a.nphi;
-    const double p12 = (p + 0.5) * dphi, p13 = (q + 0.5) * dphi;
-    double s12, c12, s13, c13;
-    sincos(p12, &s12, &c12);
-    sincos(p13, &s13, &c13);
-    const double2 v[4] = {make_double2(0, 0), make_double2(t1, 0), make_double2(t2 * c12, t2 * s12),
-                          make_double2(t3 * c13, t3 * s13)};
-    const double2 cen = make_double2((v[1].x + v[2].x + v[3].x) * 0.25, (v[1].y + v[2].y + v[3].y) * 0.25);
-    double2 d[4];
-    double sd2 = 0;
-    for (int j = 0; j < 4; ++j) {
-      d[j] = make_double2(v[j].x - cen.x, v[j].y - cen.y);
-      sd2 += d[j].x * d[j].x + d[j].y * d[j].y;
-    }
-    const double ex = exp(-sd2 / (2.0 * th2)) * pref * w2;
-    for (int mu = 0; mu < 8; ++mu) {
-      double2 P[9], R[9];
-      int dP = 0, dR = 0;
-      P[0] = make_double2(1, 0); R[0] = make_double2(1, 0);
-      for (int j = 0; j < 4; ++j) {
-        const bool cj = kBeta[mu][j];
-        double2* poly = cj ? R : P;
-        int& dg = cj ? dR : dP;
-        const double2 root = cj ? d[j] : make_double2(d[j].x, -d[j].y);
-        for (int rep = 0; rep < 2; ++rep) {
-          poly[dg + 1] = poly[dg];
-          for (int t = dg; t >= 1; --t) {
-            const double2 m = cm(poly[t], root);
-            poly[t] = make_double2(poly[t - 1].x + m.x, poly[t - 1].y + m.y);
-          }
-          poly[0] = cm(poly[0], root);
-          ++dg;
+  const int npairs = 8 * a.n_ap;
+  double2 acc[kM4MaxPairs];
+  for (int r = 0; r < kM4MaxPairs; ++r) acc[r] = make_double2(0, 0);
+  for (size_t k0 = kbeg; k0 < kend; k0 += kM4Bins) {
+    __syncthreads();  // previous tile fully consumed (and hps written)
+    {
+      // one (bin, mu) item per thread
+      const int j = threadIdx.x >> 3, mu = threadIdx.x & 7;
+      const size_t k = k0 + j;
+      if (k >= kend) {
+        for (int t = 0; t < 5; ++t) coef[j][mu][t] = make_double2(0, 0);
+        if (mu == 0) sd2s[j] = 0;
+      } else {
+        const int p = (int)(k / a.nphi), q = (int)(k % a.nphi);
+        const double p12 = (p + 0.5) * dphi, p13 = (q + 0.5) * dphi;
+        double s12, c12, s13, c13;
+        sincos(p12, &s12, &c12);
+        sincos(p13, &s13, &c13);
+        const double2 v[4] = {make_double2(0, 0), make_double2(t1, 0), make_double2(t2 * c12, t2 * s12),
+                              make_double2(t3 * c13, t3 * s13)};
+        const double2 cen =
+            make_double2((v[1].x + v[2].x + v[3].x) * 0.25, (v[1].y + v[2].y + v[3].y) * 0.25);
+        double2 d[4];
+        double sd2 = 0;
+        for (int jj = 0; jj < 4; ++jj) {
+          d[jj] = make_double2(v[jj].x - cen.x, v[jj].y - cen.y);
+          sd2 += d[jj].x * d[jj].x + d[jj].y * d[jj].y;
         }
+        if (mu == 0) sd2s[j] = sd2;
+        double2 P[9], R[9];
+        int dP = 0, dR = 0;
+        P[0] = make_double2(1, 0);
+        R[0] = make_double2(1, 0);
+        for (int jj = 0; jj < 4; ++jj) {
+          const bool cj = kBeta[mu][jj];
+          double2* poly = cj ? R : P;
+          int& dg = cj ? dR : dP;
+          const double2 root = cj ? d[jj] : make_double2(d[jj].x, -d[jj].y);
+          for (int rep = 0; rep < 2; ++rep) {
+            poly[dg + 1] = poly[dg];
+            for (int t = dg; t >= 1; --t) {
+              const double2 m = cm(poly[t], root);
+              poly[t] = make_double2(poly[t - 1].x + m.x, poly[t - 1].y + m.y);
+            }
+            poly[0] = cm(poly[0], root);
+            ++dg;
+          }
+        }
+        // e^{i ph}, ph = 2 sum s_a zeta_a, zeta = (phi13/2, 0, phi12, phi13)
+        const double ph = (kBeta[mu][0] ? -1.0 : 1.0) * p13 + 2.0 * (kBeta[mu][2] ? -1.0 : 1.0) * p12 +
+                          2.0 * (kBeta[mu][3] ? -1.0 : 1.0) * p13;
+        double sp, cp;
+        sincos(ph, &sp, &cp);
+        const double2 g =
+            cm(gam[(size_t)mu * gam_mu_stride + (size_t)lt * nph2 + k], make_double2(cp * geo, sp * geo));
+        const int tmax = dP < dR ? dP : dR;
+        for (int t = 0; t < 5; ++t) coef[j][mu][t] = t <= tmax ? cm(g, cm(P[t], R[t])) : make_double2(0, 0);
       }
-      double2 J = make_double2(0, 0);
-      for (int t = 0; t <= dP && t <= dR; ++t) {
-        const double2 m = cm(P[t], R[t]);
-        J.x += m.x * hp[t];
-        J.y += m.y * hp[t];
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < kM4Bins * a.n_ap; w += blockDim.x) {
+      const int j = w / a.n_ap, ia = w % a.n_ap;
+      const double th = a.ap[ia];
+      exs[j][ia] = exp(-sd2s[j] / (2.0 * th * th));
+    }
+    __syncthreads();
+    for (int r = 0; r < kM4MaxPairs; ++r) {
+      const int pr = threadIdx.x + r * kM4Threads;
+      if (pr >= npairs) break;
+      const int mu = pr / a.n_ap, ia = pr % a.n_ap;
+      const int tmax = mu == 0 ? 0 : (mu < 5 ? 2 : 4);
+      double2 s = acc[r];
+      for (int j = 0; j < kM4Bins; ++j) {
+        double re = 0, im = 0;
+        for (int t = 0; t <= tmax; ++t) {
+          re += coef[j][mu][t].x * hps[ia][t];
+          im += coef[j][mu][t].y * hps[ia][t];
+        }
+        s.x += re * exs[j][ia];
+        s.y += im * exs[j][ia];
       }
-      // e^{i ph}, ph = 2 sum s_a zeta_a, zeta = (phi13/2, 0, phi12, phi13)
-      const double ph = (kBeta[mu][0] ? -1.0 : 1.0) * p13 + 2.0 * (kBeta[mu][2] ? -1.0 : 1.0) * p12 +
-                        2.0 * (kBeta[mu][3] ? -1.0 : 1.0) * p13;
-      double sp, cp;
-      sincos(ph, &sp, &cp);
-      const double2 F = cm(make_double2(cp * ex, sp * ex), J);
-      const double2 g = gam[(size_t)mu * gam_mu_stride + (size_t)lt * nph2 + k];
-      const double2 c = cm(g, F);
-      acc[2 * mu] += c.x;
-      acc[2 * mu + 1] += c.y;
+      acc[r] = s;
     }
   }
-  for (int k = 0; k < 16; ++k) red[k][threadIdx.x] = acc[k];
-  __syncthreads();
-  for (int st = 64; st > 0; st >>= 1) {
-    if (threadIdx.x < st)
-      for (int k = 0; k < 16; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
-    __syncthreads();
+  for (int r = 0; r < kM4MaxPairs; ++r) {
+    const int pr = threadIdx.x + r * kM4Threads;
+    if (pr >= npairs) break;
+    const int mu = pr / a.n_ap, ia = pr % a.n_ap;
+    partial[(((size_t)tri * nsplit + split) * a.n_ap + ia) * 8 + mu] = acc[r];
   }
-  if (threadIdx.x < 8)
-    partial[((size_t)tri * a.n_ap + ia) * 8 + threadIdx.x] =
-        make_double2(red[2 * threadIdx.x][0], red[2 * threadIdx.x + 1][0]);
 }
 
 }  // namespace
@@ -229,11 +266,19 @@ size_t real_space_smem(int N, int nphi) {
   return (size_t)(nn * nn + nn * nphi) * sizeof(double2);
 }
 
-// Aperture measures: triples processed in chunks; returns per-(triple, aperture) partial
-// sums in `partial` [ntri][n_ap][8] complex.
+// Aperture measures: triples processed in chunks; returns per-(triple, slice, aperture)
+// partial sums in `partial` [ntri][nsplit][n_ap][8] complex, the angular bins of each
+// triple split into nsplit slices.
+int map4_nsplit(int chunk_tri, int ntri, int n_ap) {
+  int ns = (4 * 152 + chunk_tri - 1) / chunk_tri;
+  const size_t cap = (size_t)(256u << 20) / ((size_t)ntri * n_ap * 8 * 16);
+  if ((size_t)ns > cap) ns = (int)cap;
+  return ns < 1 ? 1 : (ns > 16 ? 16 : ns);
+}
+
 cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, int N, int nphi,
                           const double* ap_host, int n_ap, double* E_scratch, double* norm_chunk,
-                          double* gam_chunk, int chunk_tri, double* partial, cudaStream_t s) {
+                          double* gam_chunk, int chunk_tri, int nsplit, double* partial, cudaStream_t s) {
   const int nn = 2 * N + 1;
   const int ntri = nb * nb * nb;
   angle_table<<<64, 256, 0, s>>>(N, nphi, reinterpret_cast<double2*>(E_scratch));
@@ -262,8 +307,8 @@ cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, i
     real_space_kernel<false><<<8 * nt, 256, smem, s>>>(U, nb, N, nphi, E, t0, nt, norm_chunk, nullptr,
                                                        reinterpret_cast<double2*>(gam_chunk), stride);
     a.tri0 = t0; a.ntri = nt;
-    map4_kernel<<<nt * n_ap, 128, 0, s>>>(a, reinterpret_cast<const double2*>(gam_chunk), stride,
-                                          reinterpret_cast<double2*>(partial));
+    map4_kernel<<<nt * nsplit, kM4Threads, 0, s>>>(a, reinterpret_cast<const double2*>(gam_chunk), stride,
+                                                   nsplit, reinterpret_cast<double2*>(partial));
     g_launches += 3;
   }
   return cudaGetLastError();
@@ -271,8 +316,9 @@ cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, i
 
 namespace {
 
-// Sum the partials over triples (fixed order), then the E/B split and the Gaussian part.
-__global__ void map4_finish(const double2* __restrict__ partial, int ntri, int n_ap,
+// Sum the partials over triples and slices (fixed order), then the E/B split and the
+// Gaussian part.
+__global__ void map4_finish(const double2* __restrict__ partial, int nunits, int n_ap,
                             const double* __restrict__ xipm, const double* __restrict__ tb,
                             const double* __restrict__ area, int nb, const double* __restrict__ ap,
                             double* __restrict__ m4, double* __restrict__ eb, double* __restrict__ disc) {
@@ -281,7 +327,7 @@ __global__ void map4_finish(const double2* __restrict__ partial, int ntri, int n
   __shared__ double2 D[16];
   if (threadIdx.x < 8) {
     double re = 0, im = 0;
-    for (int t = 0; t < ntri; ++t) {
+    for (int t = 0; t < nunits; ++t) {
       const double2 v = partial[((size_t)t * n_ap + ia) * 8 + threadIdx.x];
       re += v.x; im += v.y;
     }
