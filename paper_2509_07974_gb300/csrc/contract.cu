@@ -168,7 +168,8 @@ contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx
   }
 }
 
-// Correction sums over the wave: block (mu, kind, index); thread (ba, bb).
+// Correction sums over the wave: block (mu, kind, index); thread (2x2 tile of (ba, bb), slice
+// of the centres), or, for the triple term, threads over the centres.
 template <typename R>
 __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
                                    const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ corr) {
@@ -178,9 +179,6 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
   const int per_mu = 2 * nn + ns;  // index rows of the three double-counting kinds
   const int mu = blockIdx.x / (per_mu + 1);
   const int row = blockIdx.x % (per_mu + 1);
-  Cx* sx = reinterpret_cast<Cx*>(smem_raw);
-  Cx* sP = sx + kCorrChunk;
-  Cx* sO = sP + kCorrChunk * nb;
   const int tid = threadIdx.x;
   const Comp cp = kComp[mu];
   const size_t nb2 = (size_t)nb * nb;
@@ -191,27 +189,62 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
     else if (row < 2 * nn) { kind = 1; var = row - nn - N; }
     else { kind = 2; var = row - 2 * nn - 2 * N; }
     const Corr cr = kCorr[kind][mu];
-    const int ba = tid / nb, bb = tid % nb;
-    const bool active = tid < nb * nb;
-    Cx acc = cmk<Cx>(R(0), R(0));
+    // staged per centre: x~ P (bins padded to an even count with zeros) and O
+    const int nt2 = (nb + 1) / 2, nbp = 2 * nt2;
+    Cx* sP = reinterpret_cast<Cx*>(smem_raw);
+    Cx* sO = sP + kCorrChunk * nbp;
+    // thread = (2x2 tile of (ba, bb), slice of the chunk's centres)
+    const int ntiles = nt2 * nt2;
+    const int nslices = max(1, (int)blockDim.x / ntiles);
+    const int tile = tid % ntiles, slice = tid / ntiles;
+    const bool active = slice < nslices;
+    const int ta = 2 * (tile / nt2), tb = 2 * (tile % nt2);
+    Cx acc[2][2];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) acc[i][j] = cmk<Cx>(R(0), R(0));
     for (int c0 = 0; c0 < T; c0 += kCorrChunk) {
       const int nc = min(kCorrChunk, T - c0);
-      for (int k = tid; k < nc * (2 * nb + 1); k += blockDim.x) {
-        const int cc = k / (2 * nb + 1), r = k % (2 * nb + 1);
+      for (int k = tid; k < nc * 2 * nbp; k += blockDim.x) {
+        const int cc = k / (2 * nbp), r = k % (2 * nbp);
         const Cx* rc = rec + (size_t)(c0 + cc) * L.rec;
-        if (r == 0) sx[cc] = centre_factor(xw, c0 + cc, cp.xconj);
-        else if (r <= nb) sP[cc * nb + r - 1] = fetch(rc, L, cr.P, var, r - 1);
-        else sO[cc * nb + r - 1 - nb] = fetch(rc, L, cr.O, var, r - 1 - nb);
+        Cx v = cmk<Cx>(R(0), R(0));
+        if (r < nbp) {
+          if (r < nb) v = cmul(centre_factor(xw, c0 + cc, cp.xconj), fetch(rc, L, cr.P, var, r));
+          sP[cc * nbp + r] = v;
+        } else {
+          if (r - nbp < nb) v = fetch(rc, L, cr.O, var, r - nbp);
+          sO[cc * nbp + r - nbp] = v;
+        }
       }
       __syncthreads();
       if (active)
-        for (int cc = 0; cc < nc; ++cc) acc = cadd(acc, cmul(cmul(sx[cc], sP[cc * nb + ba]), sO[cc * nb + bb]));
+        for (int cc = slice; cc < nc; cc += nslices) {
+          const Cx p0 = sP[cc * nbp + ta], p1 = sP[cc * nbp + ta + 1];
+          const Cx o0 = sO[cc * nbp + tb], o1 = sO[cc * nbp + tb + 1];
+          acc[0][0] = cadd(acc[0][0], cmul(p0, o0));
+          acc[0][1] = cadd(acc[0][1], cmul(p0, o1));
+          acc[1][0] = cadd(acc[1][0], cmul(p1, o0));
+          acc[1][1] = cadd(acc[1][1], cmul(p1, o1));
+        }
       __syncthreads();
     }
-    if (active) {
-      double* o = corr + 2 * (mu_base + (size_t)row * nb2 + (size_t)ba * nb + bb);
-      o[0] += (double)acc.x;
-      o[1] += (double)acc.y;
+    // fixed-order sum over the slices
+    Cx* red = reinterpret_cast<Cx*>(smem_raw);  // [nslices][ntiles][4]
+    if (active)
+      for (int q = 0; q < 4; ++q) red[((size_t)slice * ntiles + tile) * 4 + q] = acc[q >> 1][q & 1];
+    __syncthreads();
+    for (int o = tid; o < nb * nb; o += blockDim.x) {
+      const int ba = o / nb, bb = o % nb;
+      const int t = (ba >> 1) * nt2 + (bb >> 1), q = (ba & 1) * 2 + (bb & 1);
+      double re = 0, im = 0;
+      for (int sl = 0; sl < nslices; ++sl) {
+        const Cx v = red[((size_t)sl * ntiles + t) * 4 + q];
+        re += (double)v.x;
+        im += (double)v.y;
+      }
+      double* out = corr + 2 * (mu_base + (size_t)row * nb2 + o);
+      out[0] += re;
+      out[1] += im;
     }
   } else {
     // triple term: threads stride over the centres, each summing every bin, then a
@@ -330,8 +363,10 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
   if (T <= 0) return cudaSuccess;
   const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
   const int blocks = 9 * (2 * nn + ns + 1);
-  const int threads = max(256, (L.nb * L.nb + 31) / 32 * 32);
-  const size_t smem = std::max((size_t)kCorrChunk * (1 + 2 * L.nb) * sizeof(cplx_t<R>),
+  const int threads = 256;
+  const int nbp = 2 * ((L.nb + 1) / 2);
+  const size_t smem = std::max(std::max((size_t)kCorrChunk * 2 * nbp * sizeof(cplx_t<R>),
+                                        (size_t)threads * 4 * sizeof(cplx_t<R>)),
                                (size_t)2 * threads * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(corrections_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

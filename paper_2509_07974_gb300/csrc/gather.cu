@@ -168,6 +168,84 @@ template <> struct Pair<float> {
   }
 };
 
+// FP32 pass-3 inner loop with packed pairs: every (Re, Im) accumulator pair takes one
+// two-lane fused multiply-add per pair of the bin (each lane rounds like a scalar FFMA), and
+// the power recurrence u^{m+1} = u^m u runs on the pair (Re, Im) as one packed multiply and
+// one packed multiply-add.  Fills a[0, 14 MB + 10) in the slot order of the scalar path.
+template <int MB>
+__device__ __forceinline__ void accumulate_f32x2(float* a, const float4* __restrict__ euv,
+                                                 const float2* __restrict__ ex, const float* __restrict__ ew,
+                                                 int s0, int s1, int lane, int k, int mb, bool first) {
+  float2 acc[7 * MB];
+#pragma unroll
+  for (int j = 0; j < 7 * MB; ++j) acc[j] = make_float2(0.f, 0.f);
+  float tr[10];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) tr[j] = 0.f;
+  for (int e0 = s0 + lane; e0 < s1; e0 += 64) {
+    const int e1 = e0 + 32;
+    const bool two = e1 < s1;
+    const int e1c = two ? e1 : e0;
+    const float4 q0 = euv[e0], q1 = euv[e1c];
+    const float2 xx0 = ex[e0], xx1 = ex[e1c];
+    const float w0 = ew[e0];
+    // the second pair adds nothing when it is absent
+    const float xr1 = two ? xx1.x : 0.f, xi1 = two ? xx1.y : 0.f, w1 = two ? ew[e1c] : 0.f;
+    float2 P0, P1;
+    cpow5<float>(q0.z, q0.w, k, P0.x, P0.y);
+    cpow5<float>(q1.z, q1.w, k, P1.x, P1.y);
+    const float2 U0 = make_float2(q0.x, q0.y), U0s = make_float2(-q0.y, q0.x);
+    const float2 U1 = make_float2(q1.x, q1.y), U1s = make_float2(-q1.y, q1.x);
+    const float wt0[7] = {xx0.x, xx0.y, xx0.x * xx0.x - xx0.y * xx0.y, 2.f * xx0.x * xx0.y, w0,
+                          xx0.x * xx0.x + xx0.y * xx0.y, w0 * w0};
+    const float wt1[7] = {xr1, xi1, xr1 * xr1 - xi1 * xi1, 2.f * xr1 * xi1, w1, xr1 * xr1 + xi1 * xi1, w1 * w1};
+    auto step = [&](int t) {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        acc[7 * t + q] = __ffma2_rn(make_float2(wt0[q], wt0[q]), P0, acc[7 * t + q]);
+        acc[7 * t + q] = __ffma2_rn(make_float2(wt1[q], wt1[q]), P1, acc[7 * t + q]);
+      }
+      P0 = __ffma2_rn(make_float2(P0.x, P0.x), U0, __fmul2_rn(make_float2(P0.y, P0.y), U0s));
+      P1 = __ffma2_rn(make_float2(P1.x, P1.x), U1, __fmul2_rn(make_float2(P1.y, P1.y), U1s));
+    };
+    if (mb == MB) {
+#pragma unroll
+      for (int t = 0; t < MB; ++t) step(t);
+    } else {
+#pragma unroll
+      for (int t = 0; t < MB; ++t)
+        if (t < mb) step(t);
+    }
+    if (first) {
+      // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3 (the second pair is zero if absent)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float ur = q ? q1.x : q0.x, ui = q ? q1.y : q0.y;
+        const float* wt = q ? wt1 : wt0;
+        const float xr = wt[0], xi = wt[1], x2r = wt[2], x2i = wt[3], ww = wt[4], xa = wt[5], w2 = wt[6];
+        float u2r = ur * ur - ui * ui, u2i = 2.f * ur * ui;
+        float u4r = u2r * u2r - u2i * u2i, u4i = 2.f * u2r * u2i;
+        float u8r = u4r * u4r - u4i * u4i, u8i = 2.f * u4r * u4i;
+        float x3r = x2r * xr - x2i * xi, x3i = x2r * xi + x2i * xr;
+        float xcr = xa * xr, xci = xa * xi;  // x^2 x^* = |x|^2 x
+        tr[0] += x3r * u8r + x3i * u8i;  // x3 * conj(u8)
+        tr[1] += x3i * u8r - x3r * u8i;
+        tr[2] += x3r * u4r + x3i * u4i;
+        tr[3] += x3i * u4r - x3r * u4i;
+        tr[4] += xcr * u4r + xci * u4i;
+        tr[5] += xci * u4r - xcr * u4i;
+        tr[6] += xcr;
+        tr[7] += xci;
+        tr[8] += w2 * ww;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 7 * MB; ++j) { a[2 * j] = acc[j].x; a[2 * j + 1] = acc[j].y; }
+#pragma unroll
+  for (int j = 0; j < 10; ++j) a[14 * MB + j] = tr[j];
+}
+
 struct GatherArgs {
   SortedCat cat;
   Bins bins;
@@ -336,6 +414,7 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
           for (int j = 0; j < V; ++j) a[j] = R(0);
           // two pairs per lane and iteration: two independent power recurrences
           auto accumulate = [&](int e0, int e1) {
+            if constexpr (sizeof(R) == 4) return;  // the FP32 path runs accumulate_f32x2
             const bool two = e1 < s1;
             const int e1c = two ? e1 : e0;
             const V4 q0 = euv[e0], q1 = euv[e1c];
@@ -408,7 +487,12 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
               }
             }
           };
-          for (int e = s0 + lane; e < s1; e += 64) accumulate(e, e + 32);
+          if constexpr (sizeof(R) == 4)
+            accumulate_f32x2<MB>(reinterpret_cast<float*>(a), reinterpret_cast<const float4*>(euv),
+                                 reinterpret_cast<const float2*>(ex), reinterpret_cast<const float*>(ew), s0,
+                                 s1, lane, k, mb, m0 == 0);
+          else
+            for (int e = s0 + lane; e < s1; e += 64) accumulate(e, e + 32);
           // with R = sum Re(x) u^m = (a0, a1) and I = sum Im(x) u^m = (a2, a3):
           //   sum x u^m = (a0 - a3, a1 + a2),  sum x conj(u^m) = (a0 + a3, a2 - a1)
 #pragma unroll
