@@ -259,8 +259,8 @@ struct GatherArgs {
   unsigned long long* pair_count;
 };
 
-template <typename R, int MB>
-__global__ void __launch_bounds__(kThreads, 1)
+template <typename R, int MB, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __restrict__ xw) {
   using Cx = cplx_t<R>;
   constexpr int V = GCfg<R, MB>::V;
@@ -553,7 +553,11 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   }
 }
 
-template <typename R> constexpr int kMB = sizeof(R) == 4 ? 6 : 3;
+// powers per warp block and resident CTAs per SM: FP32 runs two CTAs of 8 warps per SM
+// (3 powers per block keep the accumulators within 128 registers, and each CTA gets half
+// of the shared memory), FP64 one CTA with 3 powers per block
+template <typename R> constexpr int kMB = 3;
+template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 
 }  // namespace
 
@@ -563,6 +567,7 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
                         unsigned long long* pair_count, int sm_count, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
   constexpr int MB = kMB<R>;
+  constexpr int MINB = kMinBlocks<R>;
   GatherArgs a;
   a.cat = cat; a.bins = bins; a.L = L; a.centres = centres; a.T = T; a.pair_count = pair_count;
   // rounding window of the float bin decision: |dx| carries ~2 ulp of max(cell, r)
@@ -578,7 +583,7 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   a.nblk = (npow + a.mb - 1) / a.mb;
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
                        (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64;
-  const size_t budget = 227 * 1024;
+  const size_t budget = MINB == 1 ? 227 * 1024 : 113 * 1024;
   constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R);
   if (fixed + per_pair * kThreads > budget) return cudaErrorInvalidConfiguration;
   int cap = (int)((budget - fixed) / per_pair);
@@ -586,11 +591,11 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   if (cap > 8192) cap = 8192;
   a.cap = cap;
   const size_t smem = fixed + (size_t)cap * per_pair;
-  cudaError_t e = cudaFuncSetAttribute(gather_kernel<R, MB>,
+  cudaError_t e = cudaFuncSetAttribute(gather_kernel<R, MB, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = T;
-  gather_kernel<R, MB><<<grid, kThreads, smem, s>>>(a, rec, xw);
+  gather_kernel<R, MB, MINB><<<grid, kThreads, smem, s>>>(a, rec, xw);
   ++g_launches;
   (void)sm_count;
   return cudaGetLastError();
