@@ -26,6 +26,9 @@
  *  - Errors: every entry point returns EXT4PCF_OK (0) or a negative code; no exception
  *    crosses the ABI.  ext4pcf_last_error() gives a message for the last failure.  A
  *    context may be used by one host thread at a time.
+ *  - Environment: EXT4PCF_GATHER=tc makes the tensor-core precisions (TF32, 3XTF32,
+ *    SPLIT_BF16) use the tensor-core neighbour gather (3xTF32 products) instead of the
+ *    CUDA-core FP32 gather; both give the same records to FP32 rounding.
  */
 #ifndef EXT4PCF_H
 #define EXT4PCF_H

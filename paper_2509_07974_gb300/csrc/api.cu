@@ -379,6 +379,10 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     const size_t corr_doubles = corrections_size(L);
     ENSURE(ctx->corr, corr_doubles * 8);
     CK(cudaMemsetAsync(ctx->corr.p, 0, corr_doubles * 8, s));
+    // the tensor-core gather (gather_tc.cu) is selected with EXT4PCF_GATHER=tc; the CUDA-core
+    // gather is the default because it is faster on the workloads measured so far
+    const char* gsel = std::getenv("EXT4PCF_GATHER");
+    const bool use_tc_gather = gsel && std::strcmp(gsel, "tc") == 0;
     for (int w0 = 0; w0 < n_cen; w0 += T) {
       const int Tw = std::min(T, n_cen - w0);
       const int* cl = (const int*)ctx->centres.p + w0;
@@ -386,6 +390,9 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       if (f64) {
         CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                                (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      } else if (tc && use_tc_gather && gather_tc_supported(L)) {
+        CK(gather_wave_tc(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+                          (unsigned long long*)ctx->counter.p, ctx->sm_count, (int*)ctx->status.p, timeout, s));
       } else {
         CK(gather_wave<float>(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));

@@ -121,6 +121,13 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
                         const int* centres, int T, cplx_t<R>* rec, cplx_t<R>* xw,
                         unsigned long long* pair_count, int sm_count, cudaStream_t s);
 
+// gather_tc.cu: the same records by a tensor-core gather (FP32 inputs, 3xTF32 products);
+// status receives 1 if a bounded wait ran out.
+bool gather_tc_supported(const Layout& L);
+cudaError_t gather_wave_tc(const SortedCat& cat, const Bins& bins, const Layout& L, const int* centres, int T,
+                           float2* rec, float2* xw, unsigned long long* pair_count, int sm_count, int* status,
+                           long long timeout, cudaStream_t s);
+
 // contract.cu
 template <typename R>
 cudaError_t contract_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,

@@ -23,6 +23,7 @@
 // rounded), so dx is accurate to ~1e-7 of the cell size; pairs whose r^2 lies within a few
 // rounding errors of a bin edge are re-decided from the double positions.
 #include "common.cuh"
+#include "gather_common.cuh"
 
 namespace ext4pcf {
 
@@ -30,7 +31,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxRows = 64;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Bucketed pairs in shared memory, structure of arrays: uv = (u_re, u_im, v_re, v_im) with
@@ -93,80 +93,6 @@ __device__ __forceinline__ void reduce_transpose(R* a, int lane) {
   rt_step<R, V / 16, 1>(a, lane);
 }
 
-__device__ __forceinline__ int bin_search(const double* e2, int nb, double r2) {
-  int lo = 0, hi = nb;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (r2 >= e2[mid]) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-__device__ __forceinline__ int bin_search_f(const float* e2, int nb, float r2) {
-  int lo = 0, hi = nb;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (r2 >= e2[mid]) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// Exact FP64 decision, identical to the definition: two rounded products, one rounded sum.
-__device__ __forceinline__ int classify_f64(double dx, double dy, const double* e2, int nb) {
-  double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-  if (!(r2 >= e2[0]) || !(r2 < e2[nb])) return -1;
-  return bin_search(e2, nb, r2);
-}
-
-struct CentreF64 { double x, y; };
-
-// Returns the bin of candidate q (or -1) and u = e^{i phi}.
-template <typename R> struct Pair;
-
-template <> struct Pair<double> {
-  __device__ static int classify(const SortedCat& cat, int q, double cx, double cy, const float4&,
-                                 const double* e2, const float*, const float*, int nb,
-                                 double& ur, double& ui) {
-    double dx = cat.px[q] - cx, dy = cat.py[q] - cy;
-    int b = classify_f64(dx, dy, e2, nb);
-    if (b >= 0) {
-      double rinv = 1.0 / sqrt(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
-      ur = dx * rinv; ui = dy * rinv;
-    }
-    return b;
-  }
-  __device__ static void load_x(const SortedCat& cat, int q, double& xr, double& xi, double& w) {
-    xr = cat.xr[q]; xi = cat.xi[q]; w = cat.w[q];
-  }
-};
-
-template <> struct Pair<float> {
-  __device__ static int classify(const SortedCat& cat, int q, double cx, double cy, const float4& P,
-                                 const double* e2, const float* e2f, const float* win, int nb,
-                                 float& ur, float& ui) {
-    float4 Q = cat.p4[q];
-    float dx = (Q.x - P.x) + (Q.z - P.z);
-    float dy = (Q.y - P.y) + (Q.w - P.w);
-    float r2 = dx * dx + dy * dy;
-    int b;
-    // the float decision stands unless r2 is within the edge's rounding window
-    if (r2 < e2f[0] - win[0] || r2 >= e2f[nb] + win[nb]) return -1;
-    b = (r2 >= e2f[0]) ? ((r2 >= e2f[nb]) ? nb : bin_search_f(e2f, nb, r2)) : -1;
-    bool near = false;
-    if (b < 0) near = true;  // within win[0] of the inner edge
-    else if (b == nb) near = true;
-    else near = (r2 - e2f[b] < win[b]) || (e2f[b + 1] - r2 <= win[b + 1]);
-    if (near) b = classify_f64(cat.px[q] - cx, cat.py[q] - cy, e2, nb);
-    if (b >= 0) {
-      float rinv = rsqrtf(r2);
-      ur = dx * rinv; ui = dy * rinv;
-    }
-    return b;
-  }
-  __device__ static void load_x(const SortedCat& cat, int q, float& xr, float& xi, float& w) {
-    float4 s = cat.s4[q];
-    xr = s.x; xi = s.y; w = s.z;
-  }
-};
 
 // FP32 pass-3 inner loop with packed pairs: every (Re, Im) accumulator pair takes one
 // two-lane fused multiply-add per pair of the bin (each lane rounds like a scalar FFMA), and
@@ -246,19 +172,6 @@ __device__ __forceinline__ void accumulate_f32x2(float* a, const float4* __restr
   for (int j = 0; j < 10; ++j) a[14 * MB + j] = tr[j];
 }
 
-struct GatherArgs {
-  SortedCat cat;
-  Bins bins;
-  float win[65];
-  Layout L;
-  const int* centres;
-  int T;
-  int cap;
-  int mb;    // powers per warp block (<= MB)
-  int nblk;  // power blocks
-  unsigned long long* pair_count;
-};
-
 template <typename R, int MB, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __restrict__ xw) {
@@ -269,7 +182,6 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   const Layout L = args.L;
   const int nb = args.bins.nb, cap = args.cap, mb = args.mb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned lt = (1u << lane) - 1u;
 
   using V4 = typename Vec4<R>::T;
   V4* euv = reinterpret_cast<V4*>(smem);
@@ -286,6 +198,7 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   int* rstart = wcnt + kWarps * 64;
   int* rpre = rstart + kMaxRows;
   int* misc = rpre + kMaxRows + 1;
+  signed char* cbin = reinterpret_cast<signed char*>(misc + 8);  // bin of each candidate of a chunk
 
   for (int b = tid; b <= nb; b += kThreads) {
     e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b]; win[b] = args.win[b];
@@ -326,83 +239,20 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
     const int nr = misc[0], total = misc[1];
     unsigned long long pairs_here = 0;
 
-    auto candidate = [&](int t) -> int {  // flattened candidate index -> sorted position
-      int lo = 0, hi = nr;
-      while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (t >= rpre[mid]) lo = mid; else hi = mid;
-      }
-      return rstart[lo] + (t - rpre[lo]);
-    };
-
     for (int cpos = 0; cpos < total;) {
-      // ---- pass 1: how many candidates fit the chunk, and per-bin counts
-      for (int b = tid; b < nb; b += kThreads) cnt[b] = 0;
-      __syncthreads();
-      int cend = cpos, chunk_pairs = 0;
-      while (cend < total && chunk_pairs + kThreads <= cap) {
-        const int t = cend + tid;
-        int b = -1;
-        if (t < total) {
-          R ur, ui;
-          b = Pair<R>::classify(cat, candidate(t), pxi, pyi, Pi, e2, e2f, win, nb, ur, ui);
-        }
-        const unsigned m = __ballot_sync(kFull, b >= 0);
-        if (b >= 0) {
-          const unsigned peers = __match_any_sync(m, b);
-          if ((peers & lt) == 0) atomicAdd(&cnt[b], __popc(peers));
-        }
-        __syncthreads();
-        int s = 0;
-        for (int k = 0; k < nb; ++k) s += cnt[k];
-        chunk_pairs = s;
-        cend = min(cend + kThreads, total);
-        __syncthreads();
-      }
-      if (tid == 0) {
-        int s = 0;
-        for (int b = 0; b < nb; ++b) { off[b] = s; s += cnt[b]; run[b] = 0; }
-        off[nb] = s;
-      }
-      __syncthreads();
-      // ---- pass 2: stable bucketing of the chunk's pairs by bin
-      for (int bs = cpos; bs < cend; bs += kThreads) {
-        const int t = bs + tid;
-        int b = -1;
-        R ur = 0, ui = 0, xr = 0, xi = 0, ww = 0;
-        if (t < cend) {
-          const int q = candidate(t);
-          b = Pair<R>::classify(cat, q, pxi, pyi, Pi, e2, e2f, win, nb, ur, ui);
-          if (b >= 0) Pair<R>::load_x(cat, q, xr, xi, ww);
-        }
-        const unsigned m = __ballot_sync(kFull, b >= 0);
-        unsigned rank = 0;
-        if (b >= 0) {
-          const unsigned peers = __match_any_sync(m, b);
-          rank = __popc(peers & lt);
-          if ((peers & lt) == 0) wcnt[warp * 64 + b] = __popc(peers);
-        }
-        __syncthreads();
-        if (b >= 0) {
-          int pre = 0;
-          for (int w2 = 0; w2 < warp; ++w2) pre += wcnt[w2 * 64 + b];
-          const int dst = off[b] + run[b] + pre + (int)rank;
-          R vr, vi;
-          cpow<R>(ur, ui, mb, vr, vi);
-          V4 q;
-          q.x = ur; q.y = ui; q.z = vr; q.w = vi;
-          euv[dst] = q;
-          ex[dst] = cmk<Cx>(xr, xi);
-          ew[dst] = ww;
-        }
-        __syncthreads();
-        if (tid < nb) {
-          int s = 0;
-          for (int w2 = 0; w2 < kWarps; ++w2) { s += wcnt[w2 * 64 + tid]; wcnt[w2 * 64 + tid] = 0; }
-          run[tid] += s;
-        }
-        __syncthreads();
-      }
+      // ---- classification and stable bucketing by bin of the next cap candidates
+      const int cend = min(total, cpos + cap);
+      bucket_chunk<R, kWarps>(cat, rstart, rpre, nr, cpos, cend, pxi, pyi, Pi, e2, e2f, win, nb, cbin, wcnt, off,
+                              [&](int dst, R ur, R ui, int q) {
+                                R xr, xi, ww, vr, vi;
+                                Pair<R>::load_x(cat, q, xr, xi, ww);
+                                cpow<R>(ur, ui, mb, vr, vi);
+                                V4 e;
+                                e.x = ur; e.y = ui; e.z = vr; e.w = vi;
+                                euv[dst] = e;
+                                ex[dst] = cmk<Cx>(xr, xi);
+                                ew[dst] = ww;
+                              });
       // ---- pass 3: accumulate the power blocks
       for (int k = warp; k < args.nblk; k += kWarps) {
         const int m0 = k * mb;
@@ -584,7 +434,7 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
                        (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64;
   const size_t budget = MINB == 1 ? 227 * 1024 : 113 * 1024;
-  constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R);
+  constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R) + 1;
   if (fixed + per_pair * kThreads > budget) return cudaErrorInvalidConfiguration;
   int cap = (int)((budget - fixed) / per_pair);
   cap = cap / kThreads * kThreads;

@@ -292,3 +292,69 @@ def test_full_size_sampled_centres(torch_cuda, oracle, grf_full, prec):
     ref = oracle.measure(pos, sh, w, edges, nmax, centre_mask=mask)
     got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, prec, mask=mask)
     assert rel_err(got, ref).max() < TOL[prec]
+
+
+# --------------------------------------------------------------------------------------
+# The tensor-core neighbour gather (EXT4PCF_GATHER=tc): same records as the CUDA-core
+# gather to FP32 rounding, so the same bounds against the oracle apply.
+@pytest.fixture
+def tc_gather(monkeypatch):
+    monkeypatch.setenv("EXT4PCF_GATHER", "tc")
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "bf16x3", "tf32"])
+def test_tc_gather_small_workload(torch_cuda, small, tc_gather, prec):
+    got, xi = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"],
+                      prec, xi=True)
+    assert rel_err(got, small["ref"]).max() < TOL[prec]
+    assert np.allclose(xi, small["xi"], rtol=TOL[prec], atol=TOL[prec] * np.abs(small["xi"]).max())
+
+
+@pytest.mark.parametrize("wave", [1, 70])
+def test_tc_gather_ragged_waves(torch_cuda, small, tc_gather, wave):
+    got = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], small["nmax"], "3xtf32",
+                  wave=wave)
+    assert rel_err(got, small["ref"]).max() < TOL["3xtf32"]
+
+
+def test_tc_gather_deterministic_and_counts(torch_cuda, small, tc_gather, monkeypatch):
+    args = (small["pos"], small["sh"], small["w"], small["edges"], small["nmax"], "3xtf32")
+    a, sa = run_gpu(torch_cuda, *args, stats=True)
+    b = run_gpu(torch_cuda, *args)
+    assert np.array_equal(a, b)
+    monkeypatch.delenv("EXT4PCF_GATHER")
+    c, sc = run_gpu(torch_cuda, *args, stats=True)
+    assert sa["pairs"] == sc["pairs"] and sa["centres"] == sc["centres"]
+    # the two gathers differ by FP32 rounding of the multipoles only
+    assert rel_err(a, c).max() < 2e-5
+
+
+@pytest.mark.parametrize("nb,nmax", [(1, 0), (16, 2), (12, 3), (2, 25), (2, 40)])
+def test_tc_gather_extreme_shapes(torch_cuda, oracle, tc_gather, nb, nmax):
+    """n_max = 25 and 40 take the 64-column variant (more than 16 powers u^{3a})."""
+    rng = np.random.default_rng(13)
+    pos = rng.uniform(0, 10, (60, 2))
+    sh = rng.normal(0, 0.3, pos.shape)
+    w = rng.uniform(0.5, 1.5, 60)
+    edges = np.geomspace(0.4, 6.0, nb + 1)
+    ref = oracle.measure(pos, sh, w, edges, nmax)
+    unc = oracle.measure(pos, sh, w, edges, nmax, corrections=False)
+    got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, "3xtf32")
+    assert rel_err(got, ref, unc).max() < TOL["3xtf32"]
+
+
+def test_tc_gather_centre_mask_and_host_pointers(torch_cuda, oracle, small, tc_gather):
+    mask = (np.random.default_rng(9).uniform(size=len(small["w"])) < 0.3).astype(np.uint8)
+    ref = oracle.measure(small["pos"], small["sh"], small["w"], small["edges"], 6, centre_mask=mask)
+    got = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], 6, "3xtf32", mask=mask)
+    assert rel_err(got, ref).max() < TOL["3xtf32"]
+    got_h = run_gpu(torch_cuda, small["pos"], small["sh"], small["w"], small["edges"], 6, "3xtf32", mask=mask,
+                    host=True)
+    assert np.array_equal(got, got_h)
+
+
+def test_tc_gather_full_size_sampled_centres(torch_cuda, oracle, grf_full, tc_gather):
+    pos, sh, w, edges, nmax, mask = grf_full
+    ref = oracle.measure(pos, sh, w, edges, nmax, centre_mask=mask)
+    got = run_gpu(torch_cuda, pos, sh, w, edges, nmax, "3xtf32", mask=mask)
+    assert rel_err(got, ref).max() < TOL["3xtf32"]
