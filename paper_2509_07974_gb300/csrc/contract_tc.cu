@@ -41,7 +41,6 @@ constexpr int kProducers = kProducerWarps * 32;
 constexpr int kThreads = kProducers + 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kDCols = 128;          // D region: two 64-column buffers
-constexpr int kStageCols = 64;       // per stage: A hi [0, 32) + lo [32, 64) (bf16), or 64 fp32
 constexpr int kMaxNpad = 64;         // B columns: 2 * #mu * nb padded to 16 (nb <= 16)
 
 struct KF {
@@ -66,7 +65,6 @@ __constant__ KRType kKR[7] = {
     {2, {1, -1, 0, 0}, {1, -1, 0, 0}, 1, {8, 0}, {{1, 1, 0, 0}, {0, 0, 0, 0}}},
 };
 constexpr int kKRTypes = 7;
-__host__ __device__ constexpr int kr_nmu(int t) { return (t == 0 || t == 3) ? 2 : 1; }
 
 struct TcArgs {
   Layout L;
@@ -89,26 +87,6 @@ __device__ __forceinline__ void split_bf16(float re, float im, uint32_t& hi, uin
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(im - hi_), "f"(re - hr));
   hi = h;
   lo = l;
-}
-
-__device__ __forceinline__ float2 fetch_factor(const float2* __restrict__ rc, const Layout& L, KF f, int var, int b) {
-  const int n = f.sgn * var + f.off;
-  float2 v;
-  bool cj = f.conj != 0;
-  if (f.arr == 0) {
-    v = rc[L.G(n, b)];
-  } else {
-    v = rc[L.W(n >= 0 ? n : -n, b)];
-    cj ^= (n < 0);
-  }
-  if (cj) v.y = -v.y;
-  return v;
-}
-__device__ __forceinline__ float2 centre_x(const float2* __restrict__ xw, int c, int xconj) {
-  float2 x = xw[2 * (size_t)c];
-  if (xconj == 1) x.y = -x.y;
-  if (xconj == 2) x = xw[2 * (size_t)c + 1];
-  return x;
 }
 
 // One staged block of a per-centre record: `len` consecutive complex values starting at
@@ -319,26 +297,25 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         sgnA = cjA ? -1.f : 1.f;
       }
       // copy plan of this thread for every stage (16 threads per centre): staged slots
-      // e = 1 + sub + 16 j, each read from the x~B array (source offset >= 0 relative to the
-      // item's x~B row block) or from the record (offset encoded as -1 - offset)
+      // e = 1 + sub + 16 j; slots j < jx come from the x~B array (source offset e - 1 from
+      // the item's x~B row block), slots jx <= j < jr from the record (offset coff[j])
       constexpr int kMaxCopies = 12;  // 16 * 12 >= stage_values(nb, N) for every supported shape
-      int coff[kMaxCopies];            // source offset (complex elements) of staged slot j
-      unsigned from_xb = 0, active = 0;
-      {
-        const int sub = tid & 15;
+      // record offsets (< 2^16 for every supported shape: at most (14 * 40 + 13) * 32
+      // elements per record), two per register
+      uint32_t coff2[kMaxCopies / 2];
+      const int sub = tid & 15;
+      const int e_end = bA1 + bkA1.len;  // slots past the A blocks are padding
+      const int jx = max(0, (bC - 1 - sub + 15) / 16), jr = max(0, (e_end - 1 - sub + 15) / 16);
 #pragma unroll
-        for (int j = 0; j < kMaxCopies; ++j) {
-          const int e = 1 + sub + 16 * j;
-          coff[j] = 0;
-          if (e < sc) {
-            if (e < bC) { coff[j] = e - 1; from_xb |= 1u << j; active |= 1u << j; }
-            else if (gmap[e] >= 0) { coff[j] = gmap[e]; active |= 1u << j; }
-          }
-        }
+      for (int j = 0; j < kMaxCopies; j += 2) {
+        const int e0 = 1 + sub + 16 * j, e1 = e0 + 16;
+        const uint32_t o0 = (e0 >= bC && e0 < e_end) ? (uint32_t)gmap[e0] : 0u;
+        const uint32_t o1 = (e1 >= bC && e1 < e_end) ? (uint32_t)gmap[e1] : 0u;
+        coff2[j / 2] = o0 | (o1 << 16);
       }
       // source pointers of the next stage to fetch (advanced by 32 centres per stage)
       const int ci0 = tid >> 4;
-      const float2* xs_next = xbarr + (size_t)ci0 * xb_stride + xb_off;
+      const float2* xs_next = xbarr + (size_t)ci0 * xb_stride + xb_off + sub;
       const float2* rc_next = args.rec + (size_t)ci0 * L.rec;
       const size_t xs_step = (size_t)kStageCentres * xb_stride, rc_step = (size_t)kStageCentres * L.rec;
       int fetch_buf = 0;  // staging buffer of the next stage to fetch
@@ -346,13 +323,15 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       auto issue = [&](int k) {
         if (k < nstage) {
           float2* d = stg + (size_t)fetch_buf * kStageCentres * sc_max + ci0 * sc;
-          const int sub = tid & 15, c = k * kStageCentres + ci0;
+          const int c = k * kStageCentres + ci0;
           if (c < args.T) {
             if (sub == 0) d[0] = make_float2(0.f, 0.f);
             float2* dd = d + 1 + sub;
 #pragma unroll
             for (int j = 0; j < kMaxCopies; ++j) {
-              if (active & (1u << j)) cp_async8(dd + 16 * j, ((from_xb >> j) & 1u ? xs_next : rc_next) + coff[j]);
+              if (j >= jr) break;
+              if (j < jx) cp_async8(dd + 16 * j, xs_next + 16 * j);
+              else cp_async8(dd + 16 * j, rc_next + ((coff2[j / 2] >> (16 * (j & 1))) & 0xFFFFu));
             }
           } else {
             for (int e = sub; e < sc; e += 16) d[e] = make_float2(0.f, 0.f);
