@@ -172,6 +172,73 @@ __device__ __forceinline__ void accumulate_f32x2(float* a, const float4* __restr
   for (int j = 0; j < 10; ++j) a[14 * MB + j] = tr[j];
 }
 
+// FP32 pass-3 inner loop, one pair per lane per iteration (for larger power blocks: the
+// per-pair set-up -- loads, the block's first power, the weights -- is paid once per block
+// of MB powers).  Fills a[0, 14 MB + 10) in the slot order of the scalar path.
+template <int MB>
+__device__ __forceinline__ void accumulate1_f32x2(float* a, const float4* __restrict__ euv,
+                                                  const float2* __restrict__ ex, const float* __restrict__ ew,
+                                                  int s0, int s1, int lane, int k, int mb, bool first) {
+  float2 acc[7 * MB];
+#pragma unroll
+  for (int j = 0; j < 7 * MB; ++j) acc[j] = make_float2(0.f, 0.f);
+  for (int e = s0 + lane; e < s1; e += 32) {
+    const float4 q = euv[e];
+    const float2 xx = ex[e];
+    const float w = ew[e];
+    float2 P;
+    cpow5<float>(q.z, q.w, k, P.x, P.y);
+    const float2 U = make_float2(q.x, q.y), Us = make_float2(-q.y, q.x);
+    const float wt[7] = {xx.x, xx.y, xx.x * xx.x - xx.y * xx.y, 2.f * xx.x * xx.y, w,
+                         xx.x * xx.x + xx.y * xx.y, w * w};
+    auto step = [&](int t) {
+#pragma unroll
+      for (int qq = 0; qq < 7; ++qq) acc[7 * t + qq] = __ffma2_rn(make_float2(wt[qq], wt[qq]), P, acc[7 * t + qq]);
+      P = __ffma2_rn(make_float2(P.x, P.x), U, __fmul2_rn(make_float2(P.y, P.y), Us));
+    };
+    if (mb == MB) {
+#pragma unroll
+      for (int t = 0; t < MB; ++t) step(t);
+    } else {
+#pragma unroll
+      for (int t = 0; t < MB; ++t)
+        if (t < mb) step(t);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 7 * MB; ++j) { a[2 * j] = acc[j].x; a[2 * j + 1] = acc[j].y; }
+  // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3: a pass of its own, taken by the block
+  // that holds u^0, so that these sums hold no registers in the power loop
+  float tr[10];
+#pragma unroll
+  for (int j = 0; j < 10; ++j) tr[j] = 0.f;
+  if (first) {
+    for (int e = s0 + lane; e < s1; e += 32) {
+      const float4 q = euv[e];
+      const float2 xx = ex[e];
+      const float w = ew[e];
+      const float ur = q.x, ui = q.y, xr = xx.x, xi = xx.y;
+      const float x2r = xr * xr - xi * xi, x2i = 2.f * xr * xi, xa = xr * xr + xi * xi;
+      float u2r = ur * ur - ui * ui, u2i = 2.f * ur * ui;
+      float u4r = u2r * u2r - u2i * u2i, u4i = 2.f * u2r * u2i;
+      float u8r = u4r * u4r - u4i * u4i, u8i = 2.f * u4r * u4i;
+      float x3r = x2r * xr - x2i * xi, x3i = x2r * xi + x2i * xr;
+      float xcr = xa * xr, xci = xa * xi;  // x^2 x^* = |x|^2 x
+      tr[0] += x3r * u8r + x3i * u8i;  // x3 * conj(u8)
+      tr[1] += x3i * u8r - x3r * u8i;
+      tr[2] += x3r * u4r + x3i * u4i;
+      tr[3] += x3i * u4r - x3r * u4i;
+      tr[4] += xcr * u4r + xci * u4i;
+      tr[5] += xci * u4r - xcr * u4i;
+      tr[6] += xcr;
+      tr[7] += xci;
+      tr[8] += (w * w) * w;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 10; ++j) a[14 * MB + j] = tr[j];
+}
+
 template <typename R, int MB, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __restrict__ xw) {
@@ -337,7 +404,11 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
               }
             }
           };
-          if constexpr (sizeof(R) == 4)
+          if constexpr (sizeof(R) == 4 && MB >= 6)
+            accumulate1_f32x2<MB>(reinterpret_cast<float*>(a), reinterpret_cast<const float4*>(euv),
+                                  reinterpret_cast<const float2*>(ex), reinterpret_cast<const float*>(ew), s0,
+                                  s1, lane, k, mb, m0 == 0);
+          else if constexpr (sizeof(R) == 4)
             accumulate_f32x2<MB>(reinterpret_cast<float*>(a), reinterpret_cast<const float4*>(euv),
                                  reinterpret_cast<const float2*>(ex), reinterpret_cast<const float*>(ew), s0,
                                  s1, lane, k, mb, m0 == 0);
@@ -406,7 +477,7 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
 // powers per warp block and resident CTAs per SM: FP32 runs two CTAs of 8 warps per SM
 // (3 powers per block keep the accumulators within 128 registers, and each CTA gets half
 // of the shared memory), FP64 one CTA with 3 powers per block
-template <typename R> constexpr int kMB = 3;
+template <typename R> constexpr int kMB = sizeof(R) == 4 ? 6 : 3;
 template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 
 }  // namespace
