@@ -73,6 +73,7 @@ struct ext4pcf_ctx {
   int tc_N = -1, tc_nb = -1;
   size_t tc_items_bytes = 0;
   cudaEvent_t ev[8] = {};
+  std::vector<cudaEvent_t> tev;  // per-phase timing events of one measure call (grown on demand)
 };
 
 namespace {
@@ -188,6 +189,8 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
     if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto e : ctx->tev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return EXT4PCF_OK;
 }
@@ -285,6 +288,22 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   float ms_grid = 0, ms_gather = 0, ms_contract = 0, ms_correct = 0, ms_total = 0;
   int64_t tot_centres = 0, tot_waves = 0;
   if (timing) CK(cudaEventRecord(ctx->ev[0], s));
+  // phase timing without host synchronisation: events are recorded on the stream and their
+  // intervals summed once at the end of the call (kind 0 grid, 1 gather, 2 contraction,
+  // 3 corrections)
+  struct Mark { int kind, a, b; };
+  std::vector<Mark> marks;
+  int nev = 0;
+  auto tmark = [&]() -> int {
+    if (nev >= (int)ctx->tev.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      ctx->tev.push_back(e);
+    }
+    if (cudaEventRecord(ctx->tev[nev], s) != cudaSuccess) return -1;
+    return nev++;
+  };
+  int t_grid0 = -1;
   ENSURE(ctx->counter, 16);
   CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
   const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16 || prec == EXT4PCF_3XTF32;
@@ -315,7 +334,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     const double* sh_k = d_sh + 2 * c0;
     const double* w_k = d_w + c0;
     const uint8_t* mask_k = d_mask ? d_mask + c0 : nullptr;
-    if (timing) CK(cudaEventRecord(ctx->ev[1], s));
+    if (timing) t_grid0 = tmark();
     // ---- grid
     CK(grid_bbox(pos_k, nk, (double*)ctx->bbox.p, s));
     double bb[4];
@@ -367,7 +386,8 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       CK(cudaGetLastError());
     }
     tot_centres += n_cen;
-    if (timing) CK(cudaEventRecord(ctx->ev[2], s));
+    if (timing) marks.push_back({0, t_grid0, tmark()});
+    int t_w0 = -1, t_w1 = -1, t_w2 = -1;
     // ---- waves
     const size_t cbytes = f64 ? sizeof(double2) : sizeof(float2);
     int T = ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres : (f64 ? 4096 : 8192);
@@ -386,7 +406,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     for (int w0 = 0; w0 < n_cen; w0 += T) {
       const int Tw = std::min(T, n_cen - w0);
       const int* cl = (const int*)ctx->centres.p + w0;
-      if (timing) CK(cudaEventRecord(ctx->ev[3], s));
+      if (timing) t_w0 = tmark();
       if (f64) {
         CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                                (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
@@ -397,7 +417,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
         CK(gather_wave<float>(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       }
-      if (timing) CK(cudaEventRecord(ctx->ev[4], s));
+      if (timing) t_w1 = tmark();
       if (f64) {
         CK(contract_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, ups_k, s));
       } else if (prec == EXT4PCF_FP32) {
@@ -407,7 +427,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
                             (const int4*)ctx->tc_items.p, (int)(ctx->tc_items_bytes / sizeof(int4)),
                             (float2*)ctx->tc_xb.p, (int*)ctx->status.p, timeout, s));
       }
-      if (timing) CK(cudaEventRecord(ctx->ev[5], s));
+      if (timing) t_w2 = tmark();
       if (f64) {
         CK(corrections_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw,
                                     (double*)ctx->corr.p, xi_k, s));
@@ -416,24 +436,15 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
                                    (double*)ctx->corr.p, xi_k, s));
       }
       if (timing) {
-        CK(cudaEventRecord(ctx->ev[6], s));
-        CK(cudaEventSynchronize(ctx->ev[6]));
-        float a = 0, b = 0, c = 0;
-        cudaEventElapsedTime(&a, ctx->ev[3], ctx->ev[4]);
-        cudaEventElapsedTime(&b, ctx->ev[4], ctx->ev[5]);
-        cudaEventElapsedTime(&c, ctx->ev[5], ctx->ev[6]);
-        ms_gather += a; ms_contract += b; ms_correct += c;
+        const int t_w3 = tmark();
+        marks.push_back({1, t_w0, t_w1});
+        marks.push_back({2, t_w1, t_w2});
+        marks.push_back({3, t_w2, t_w3});
       }
       ++tot_waves;
     }
     CK(corrections_apply(L, (const double*)ctx->corr.p, ups_k, s));
-    if (timing) {
-      CK(cudaEventRecord(ctx->ev[7], s));
-      CK(cudaEventSynchronize(ctx->ev[7]));
-      float g = 0;
-      cudaEventElapsedTime(&g, ctx->ev[1], ctx->ev[2]);
-      ms_grid += g;
-    }
+
   }
   if (tc) {
     int st = 0;
@@ -450,6 +461,14 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     CK(cudaEventRecord(ctx->ev[7], s));
     CK(cudaEventSynchronize(ctx->ev[7]));
     cudaEventElapsedTime(&ms_total, ctx->ev[0], ctx->ev[7]);
+    for (const Mark& m : marks) {
+      float t = 0.f;
+      if (m.a < 0 || m.b < 0 || cudaEventElapsedTime(&t, ctx->tev[m.a], ctx->tev[m.b]) != cudaSuccess) continue;
+      if (m.kind == 0) ms_grid += t;
+      else if (m.kind == 1) ms_gather += t;
+      else if (m.kind == 2) ms_contract += t;
+      else ms_correct += t;
+    }
     stats->pairs = (int64_t)pairs;
     stats->centres = tot_centres;
     stats->waves = tot_waves;
