@@ -178,7 +178,7 @@ __device__ __forceinline__ void accumulate_f32x2(float* a, const float4* __restr
 template <int MB>
 __device__ __forceinline__ void accumulate1_f32x2(float* a, const float4* __restrict__ euv,
                                                   const float2* __restrict__ ex, const float* __restrict__ ew,
-                                                  int s0, int s1, int lane, int k, int mb, bool first) {
+                                                  int s0, int s1, int lane, int k, int mb, int tr_nsub) {
   float2 acc[7 * MB];
 #pragma unroll
   for (int j = 0; j < 7 * MB; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -207,13 +207,15 @@ __device__ __forceinline__ void accumulate1_f32x2(float* a, const float4* __rest
   }
 #pragma unroll
   for (int j = 0; j < 7 * MB; ++j) { a[2 * j] = acc[j].x; a[2 * j + 1] = acc[j].y; }
-  // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3: a pass of its own, taken by the block
-  // that holds u^0, so that these sums hold no registers in the power loop
+  // x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3: a pass of its own (so that these sums
+  // hold no registers in the power loop), shared by the tr_nsub power blocks of the bin:
+  // block k takes the 32-pair groups k, k + tr_nsub, ...  The caller adds the blocks'
+  // partial sums in a fixed order.
   float tr[10];
 #pragma unroll
   for (int j = 0; j < 10; ++j) tr[j] = 0.f;
-  if (first) {
-    for (int e = s0 + lane; e < s1; e += 32) {
+  {
+    for (int e = s0 + lane + 32 * k; e < s1; e += 32 * tr_nsub) {
       const float4 q = euv[e];
       const float2 xx = ex[e];
       const float w = ew[e];
@@ -265,7 +267,11 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   int* rstart = wcnt + kWarps * 64;
   int* rpre = rstart + kMaxRows;
   int* misc = rpre + kMaxRows + 1;
-  signed char* cbin = reinterpret_cast<signed char*>(misc + 8);  // bin of each candidate of a chunk
+  // FP32 with 6-power blocks: the triple terms are split over the power blocks, whose
+  // partial sums wait in trs [nb][nblk][10] until the end of the chunk
+  constexpr bool kTrSplit = sizeof(R) == 4 && MB >= 6;
+  R* trs = reinterpret_cast<R*>(misc + 8);
+  signed char* cbin = reinterpret_cast<signed char*>(trs + (kTrSplit ? nb * args.nblk * 10 : 0));  // bin of each candidate
 
   for (int b = tid; b <= nb; b += kThreads) {
     e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b]; win[b] = args.win[b];
@@ -404,10 +410,10 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
               }
             }
           };
-          if constexpr (sizeof(R) == 4 && MB >= 6)
+          if constexpr (kTrSplit)
             accumulate1_f32x2<MB>(reinterpret_cast<float*>(a), reinterpret_cast<const float4*>(euv),
                                   reinterpret_cast<const float2*>(ex), reinterpret_cast<const float*>(ew), s0,
-                                  s1, lane, k, mb, m0 == 0);
+                                  s1, lane, k, mb, args.nblk);
           else if constexpr (sizeof(R) == 4)
             accumulate_f32x2<MB>(reinterpret_cast<float*>(a), reinterpret_cast<const float4*>(euv),
                                  reinterpret_cast<const float2*>(ex), reinterpret_cast<const float*>(ew), s0,
@@ -448,14 +454,26 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
                   default: if (m <= 2 * L.N) idx = L.WW(m, b); break;
                 }
               }
-            } else if (slot < 14 * MB + 10 && m0 == 0) {
-              idx = L.TR((slot - 14 * MB) >> 1, b);
+            } else if (slot < 14 * MB + 10) {
+              if (kTrSplit) trs[(b * args.nblk + k) * 10 + (slot - 14 * MB)] = a[j];
+              else if (m0 == 0) idx = L.TR((slot - 14 * MB) >> 1, b);
             }
             if (idx >= 0) accr[2 * idx + comp] += a[j];
           }
         }
       }
       __syncthreads();
+      if (kTrSplit) {
+        // triple terms: the power blocks' partial sums, in block order
+        R* accr = reinterpret_cast<R*>(acc);
+        for (int i = tid; i < nb * 10; i += kThreads) {
+          const int b = i / 10, q = i % 10;
+          if (off[b + 1] == off[b]) continue;
+          R sum = R(0);
+          for (int k = 0; k < args.nblk; ++k) sum += trs[(b * args.nblk + k) * 10 + q];
+          accr[2 * L.TR(q >> 1, b) + (q & 1)] += sum;
+        }
+      }
       pairs_here += (unsigned long long)off[nb];
       cpos = cend;
       __syncthreads();
@@ -503,7 +521,8 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   a.mb = (npow + nblk - 1) / nblk;
   a.nblk = (npow + a.mb - 1) / a.mb;
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
-                       (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64;
+                       (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64 +
+                       (sizeof(R) == 4 && MB >= 6 ? (size_t)bins.nb * a.nblk * 10 * sizeof(R) : 0);
   const size_t budget = MINB == 1 ? 227 * 1024 : 113 * 1024;
   constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R) + 1;
   if (fixed + per_pair * kThreads > budget) return cudaErrorInvalidConfiguration;
