@@ -36,6 +36,7 @@ N_SM = 152
 FP32_LANES_PER_SM = 128
 N_PHI = 129
 AP_RADII = np.geomspace(1.0, 32.0, 24)
+TRAFFIC_PER_LAUNCH = {"gather": 0.212e9, "contraction": 1.337e9}
 METRIC = "galaxy pairs/s + Upsilon contraction TFLOP/s; mixed vs FP64 form at stated rel err"
 
 
@@ -353,6 +354,13 @@ def run_ours(args):
               "peak_note": "tf32 dense: measured sustained bf16 (%s TFLOP/s, %s) x 1.1/2.25"
                            % (pk.get("bf16_tflops_sustained"), pk.get("source")),
               "algorithmic_flop_per_centre": 8 * 9 * (2 * nmax + 1) ** 2 * nb ** 3}
+    # DRAM bytes (read + write) of one full-size launch, from the ncu capture summarised in
+    # profiles/gather_contract_wave_grf2e6.md (8192 centres of this workload, 3xTF32);
+    # null for other configurations
+    if args.precision == "3xtf32" and args.n_gal is None and args.centres is None:
+        roof_g["traffic"] = TRAFFIC_PER_LAUNCH["gather"]
+        roof_c["traffic"] = TRAFFIC_PER_LAUNCH["contraction"]
+        roof_g["traffic_unit"] = roof_c["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
     roof_main, roof_other = (roof_c, roof_g) if c_ms >= g_ms else (roof_g, roof_c)
 
     fp64_info = None
