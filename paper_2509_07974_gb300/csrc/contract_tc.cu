@@ -162,9 +162,13 @@ __global__ void xb_kernel(const Layout L, const float2* __restrict__ rec, const 
 }
 
 constexpr int kStageBufs = 3;  // staging ring: stage k + 2 is fetched while k is formed
-// staged complex values per centre: a zero, the x~B and C blocks of at most the tile's n2
-// values (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two A
-// rows; rounded up to an odd count so that consecutive centres fall in different banks
+// A staged stage is [slot][centre]: slot e of the 32 centres is one row of kCS complex values
+// (32 + 2 padding, so that rows start 4 banks apart and eight lanes reading eight slots of
+// the same centres hit different banks).  A thread's eight centres are contiguous: it reads
+// them with four 16-byte loads at fixed offsets.
+constexpr int kCS = 34;
+// staged slots per centre: a zero, the x~B and C blocks of at most the tile's n2 values
+// (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two A rows
 __host__ __device__ inline int stage_values(int nb, int N) {
   int rows = 128 / (nb * nb) + 2;
   if (rows > 2 * N + 1) rows = 2 * N + 1;
@@ -203,7 +207,7 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
   constexpr int stage_bytes = P::kAtoms * tile_bytes;
   const int sc_max = stage_values(nb, N);
   float2* stg = reinterpret_cast<float2*>(sm + kSt * stage_bytes);
-  int* gmap = reinterpret_cast<int*>(stg + kStageBufs * kStageCentres * sc_max);  // [sc_max]
+  int* gmap = reinterpret_cast<int*>(stg + kStageBufs * sc_max * kCS);  // [sc_max]
   uint64_t* full = reinterpret_cast<uint64_t*>(gmap + ((sc_max + 1) & ~1));
   uint64_t* empty = full + kSt;
   uint64_t* dfull = empty + kSt;  // [2]: a D buffer holds a finished partial sum
@@ -285,8 +289,6 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       for (int j = 0; j < 4; ++j)
         boff[j] = PREC == EXT4PCF_SPLIT_BF16 ? sw128_word_off(bn, bq * 4 + j, kMaxNpad)
                                              : sw128_word_off(bn, 2 * (bq * 4 + j), kMaxNpad);
-      const float2* const a_base = nullptr;  // (the A values are read at st + i * sc + iA)
-      (void)a_base;
       int iA = 0, bo = 0;
       float sgnA = 1.f;
       if (bn < ncols) {
@@ -322,19 +324,19 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       // copy one stage's slices (stages are fetched in order); tails are zero-filled
       auto issue = [&](int k) {
         if (k < nstage) {
-          float2* d = stg + (size_t)fetch_buf * kStageCentres * sc_max + ci0 * sc;
+          float2* d = stg + (size_t)fetch_buf * sc_max * kCS + ci0;  // slot e at d[e * kCS]
           const int c = k * kStageCentres + ci0;
           if (c < args.T) {
             if (sub == 0) d[0] = make_float2(0.f, 0.f);
-            float2* dd = d + 1 + sub;
+            float2* dd = d + (1 + sub) * kCS;
 #pragma unroll
             for (int j = 0; j < kMaxCopies; ++j) {
               if (j >= jr) break;
-              if (j < jx) cp_async8(dd + 16 * j, xs_next + 16 * j);
-              else cp_async8(dd + 16 * j, rc_next + ((coff2[j / 2] >> (16 * (j & 1))) & 0xFFFFu));
+              if (j < jx) cp_async8(dd + 16 * kCS * j, xs_next + 16 * j);
+              else cp_async8(dd + 16 * kCS * j, rc_next + ((coff2[j / 2] >> (16 * (j & 1))) & 0xFFFFu));
             }
           } else {
-            for (int e = sub; e < sc; e += 16) d[e] = make_float2(0.f, 0.f);
+            for (int e = sub; e < sc; e += 16) d[e * kCS] = make_float2(0.f, 0.f);
           }
           xs_next += xs_step;
           rc_next += rc_step;
@@ -367,17 +369,20 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         cp_async_wait<1>();
         producers_sync();
         issue(k + 2);
-        const float2* st = stg + (size_t)read_buf * kStageCentres * sc_max;
+        const float2* st = stg + (size_t)read_buf * sc_max * kCS;
         read_buf = read_buf == kStageBufs - 1 ? 0 : read_buf + 1;
         if (!mbar_wait(&empty[slot], ph ^ 1u, budget)) err = 1;
         tc_fence_after();
         // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
         unsigned char* bt = sm + slot * stage_bytes;
         if (bn < npad) {
-          const float2* ap = st + bq * 4 * sc + iA;
+          const float4* ap4 = reinterpret_cast<const float4*>(st + iA * kCS + bq * 4);
+          const float4 a01 = ap4[0], a23 = ap4[1];
+          const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
+                                make_float2(a23.z, a23.w)};
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            float2 a = ap[j * sc];
+            float2 a = av[j];
             a.y *= sgnA;
             const float v0 = bo ? a.y : a.x;
             const float v1 = bo ? a.x : -a.y;
@@ -398,15 +403,27 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           }
         }
         // A operand (TMEM): this row's Khatri-Rao values x~B * C for 8 centres
-        const float2* qB = st + quarter * kQuarter * sc + iB;
-        const float2* qC = st + quarter * kQuarter * sc + iC;
+        // x~B and C of this row for the quarter's eight centres (contiguous in the slot rows)
+        float2 xbv[kQuarter], cvv[kQuarter];
+        {
+          const float4* b4 = reinterpret_cast<const float4*>(st + iB * kCS + quarter * kQuarter);
+          const float4* c4 = reinterpret_cast<const float4*>(st + iC * kCS + quarter * kQuarter);
+#pragma unroll
+          for (int q = 0; q < kQuarter / 2; ++q) {
+            const float4 tb = b4[q], tc = c4[q];
+            xbv[2 * q] = make_float2(tb.x, tb.y);
+            xbv[2 * q + 1] = make_float2(tb.z, tb.w);
+            cvv[2 * q] = make_float2(tc.x, tc.y);
+            cvv[2 * q + 1] = make_float2(tc.z, tc.w);
+          }
+        }
         const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * P::kStageCols;
         if (PREC == EXT4PCF_SPLIT_BF16) {
           uint32_t w[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
-            const float2 xb = qB[j * sc];
-            float2 cv = qC[j * sc];
+            const float2 xb = xbv[j];
+            float2 cv = cvv[j];
             cv.y *= sgnC;
             split_bf16(xb.x * cv.x - xb.y * cv.y, xb.x * cv.y + xb.y * cv.x, w[j], w[8 + j]);
           }
@@ -416,8 +433,8 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           uint32_t w[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
-            const float2 xb = qB[j * sc];
-            float2 cv = qC[j * sc];
+            const float2 xb = xbv[j];
+            float2 cv = cvv[j];
             cv.y *= sgnC;
             w[2 * j] = __float_as_uint(xb.x * cv.x - xb.y * cv.y);
             w[2 * j + 1] = __float_as_uint(xb.x * cv.y + xb.y * cv.x);
@@ -427,8 +444,8 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           uint32_t wh[16], wl[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
-            const float2 xb = qB[j * sc];
-            float2 cv = qC[j * sc];
+            const float2 xb = xbv[j];
+            float2 cv = cvv[j];
             cv.y *= sgnC;
             split_tf32(xb.x * cv.x - xb.y * cv.y, wh[2 * j], wl[2 * j]);
             split_tf32(xb.x * cv.y + xb.y * cv.x, wh[2 * j + 1], wl[2 * j + 1]);
@@ -535,7 +552,7 @@ size_t tc_smem_bytes(int nb, int N, int prec) {
   const int st = x3 ? TcPrec<EXT4PCF_3XTF32>::kStages : 4;
   const int atoms = x3 ? TcPrec<EXT4PCF_3XTF32>::kAtoms : 2;
   const int sc = stage_values(nb, N);
-  return (size_t)st * atoms * kMaxNpad * 128 + (size_t)kStageBufs * kStageCentres * sc * 8 +
+  return (size_t)st * atoms * kMaxNpad * 128 + (size_t)kStageBufs * sc * kCS * 8 +
          (size_t)((sc + 1) & ~1) * 4 + 1024 + 256;
 }
 
