@@ -131,6 +131,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory"); }
+// the four producer warps of one centre quarter (barriers 2..5): within a stage a quarter
+// reads only the staged slices that its own warps copied
+__device__ __forceinline__ void quarter_sync(int q) { asm volatile("bar.sync %0, 128;" ::"r"(2 + q) : "memory"); }
 
 // x~ times the row factor B, per centre: [5][2N+1][nb] complex, indexed by n2:
 //   0: x G[-n2-2]   1: x G[n2-2]^*   2: x^* G[-n2-2]   3: x^* G[n2-2]^*   4: w W[-n2]
@@ -282,13 +285,18 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       int iC = bC + blk_index(bkC, kr.C, n3, b3, nb, cjC);
       const float sgnC = cjC ? -1.f : 1.f;
       if (!row_ok) { iB = 0; iC = 0; }
-      // B-operand words of this thread: column bn, centres [4 bq, 4 bq + 4)
-      const int bn = tid >> 3, bq = tid & 7;
+      // B-operand words of this thread: the quarter's 128 threads write the tile's K range of
+      // its eight centres; column bn, centres 8 quarter + cpt bq + j (j < cpt)
+      const int tq = tid & 127;
+      const int cpt = npad <= 16 ? 1 : (npad <= 32 ? 2 : 4);
+      const int tpc = 8 / cpt;
+      const int bn = tq / tpc, bq = tq % tpc;
+      const int cb0 = quarter * kQuarter + bq * cpt;
       uint32_t boff[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        boff[j] = PREC == EXT4PCF_SPLIT_BF16 ? sw128_word_off(bn, bq * 4 + j, kMaxNpad)
-                                             : sw128_word_off(bn, 2 * (bq * 4 + j), kMaxNpad);
+        boff[j] = PREC == EXT4PCF_SPLIT_BF16 ? sw128_word_off(bn, cb0 + j, kMaxNpad)
+                                             : sw128_word_off(bn, 2 * (cb0 + j), kMaxNpad);
       int iA = 0, bo = 0;
       float sgnA = 1.f;
       if (bn < ncols) {
@@ -367,7 +375,7 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
       int read_buf = 0;
       for (int k = 0; k < nstage; ++k, ++gk) {
         cp_async_wait<1>();
-        producers_sync();
+        quarter_sync(quarter);
         issue(k + 2);
         const float2* st = stg + (size_t)read_buf * sc_max * kCS;
         read_buf = read_buf == kStageBufs - 1 ? 0 : read_buf + 1;
@@ -376,13 +384,11 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
         // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
         unsigned char* bt = sm + slot * stage_bytes;
         if (bn < npad) {
-          const float4* ap4 = reinterpret_cast<const float4*>(st + iA * kCS + bq * 4);
-          const float4 a01 = ap4[0], a23 = ap4[1];
-          const float2 av[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
-                                make_float2(a23.z, a23.w)};
+          const float2* ap = st + iA * kCS + cb0;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            float2 a = av[j];
+            if (j >= cpt) break;
+            float2 a = ap[j];
             a.y *= sgnA;
             const float v0 = bo ? a.y : a.x;
             const float v1 = bo ? a.x : -a.y;
