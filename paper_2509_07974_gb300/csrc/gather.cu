@@ -172,6 +172,26 @@ __device__ __forceinline__ void accumulate_f32x2(float* a, const float4* __restr
   for (int j = 0; j < 10; ++j) a[14 * MB + j] = tr[j];
 }
 
+// v^k for the block index k (uniform across the warp): the shortest product chain for
+// k < 8 as straight-line code behind one uniform branch, binary powering beyond
+__device__ __forceinline__ float2 cmul_f(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void vpow_block(float vr, float vi, int k, float2& P) {
+  const float2 v = make_float2(vr, vi);
+  switch (k) {
+    case 0: P = make_float2(1.f, 0.f); return;
+    case 1: P = v; return;
+    case 2: P = cmul_f(v, v); return;
+    case 3: P = cmul_f(cmul_f(v, v), v); return;
+    case 4: { const float2 v2 = cmul_f(v, v); P = cmul_f(v2, v2); return; }
+    case 5: { const float2 v2 = cmul_f(v, v); P = cmul_f(cmul_f(v2, v2), v); return; }
+    case 6: { const float2 v2 = cmul_f(v, v); P = cmul_f(cmul_f(v2, v2), v2); return; }
+    case 7: { const float2 v2 = cmul_f(v, v); P = cmul_f(cmul_f(cmul_f(v2, v2), v2), v); return; }
+    default: cpow5<float>(vr, vi, k, P.x, P.y); return;
+  }
+}
+
 // FP32 pass-3 inner loop, one pair per lane per iteration (for larger power blocks: the
 // per-pair set-up -- loads, the block's first power, the weights -- is paid once per block
 // of MB powers).  Fills a[0, 14 MB + 10) in the slot order of the scalar path.
@@ -187,7 +207,7 @@ __device__ __forceinline__ void accumulate1_f32x2(float* a, const float4* __rest
     const float2 xx = ex[e];
     const float w = ew[e];
     float2 P;
-    cpow5<float>(q.z, q.w, k, P.x, P.y);
+    vpow_block(q.z, q.w, k, P);
     const float2 U = make_float2(q.x, q.y), Us = make_float2(-q.y, q.x);
     const float wt[7] = {xx.x, xx.y, xx.x * xx.x - xx.y * xx.y, 2.f * xx.x * xx.y, w,
                          xx.x * xx.x + xx.y * xx.y, w * w};
