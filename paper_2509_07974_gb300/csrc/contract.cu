@@ -258,7 +258,15 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
       red[tid] = (double)acc.x;
       red[blockDim.x + tid] = (double)acc.y;
       __syncthreads();
-      for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      // fold the entries past the largest power of two first, then a tree (any block size)
+      int p2 = 1;
+      while (2 * p2 <= (int)blockDim.x) p2 *= 2;
+      if (tid + p2 < (int)blockDim.x) {
+        red[tid] += red[tid + p2];
+        red[blockDim.x + tid] += red[blockDim.x + tid + p2];
+      }
+      __syncthreads();
+      for (int st = p2 / 2; st > 0; st >>= 1) {
         if (tid < st) {
           red[tid] += red[tid + st];
           red[blockDim.x + tid] += red[blockDim.x + tid + st];
@@ -363,7 +371,10 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
   if (T <= 0) return cudaSuccess;
   const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
   const int blocks = 9 * (2 * nn + ns + 1);
-  const int threads = 256;
+  // 192 threads (10 resident blocks per SM) let the 9 x (2(2N+1) + 4N+2) blocks of a wave
+  // run in one round on 152 SMs; never fewer threads than 2x2 tiles of (b_a, b_b)
+  const int ntiles = ((L.nb + 1) / 2) * ((L.nb + 1) / 2);
+  const int threads = std::max(192, (ntiles + 31) / 32 * 32);
   const int nbp = 2 * ((L.nb + 1) / 2);
   const size_t smem = std::max(std::max((size_t)kCorrChunk * 2 * nbp * sizeof(cplx_t<R>),
                                         (size_t)threads * 4 * sizeof(cplx_t<R>)),
