@@ -9,6 +9,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import shutil
 import subprocess
 import sys
 
@@ -49,14 +50,17 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if not force and up_to_date():
         return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    # objects in a directory of this process: concurrent builds (one per rank) do not share
+    # object files; the library itself is replaced atomically
+    obj_dir = os.path.join(BUILD_DIR, "p%d" % os.getpid())
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     flags = NVCC_FLAGS + list(extra_flags or [])
     if verbose:
         flags = flags + ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -77,6 +81,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    shutil.rmtree(obj_dir, ignore_errors=True)
     return LIB
 
 
