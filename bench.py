@@ -36,7 +36,7 @@ N_SM = 152
 FP32_LANES_PER_SM = 128
 N_PHI = 129
 AP_RADII = np.geomspace(1.0, 32.0, 24)
-TRAFFIC_PER_LAUNCH = {"gather": 0.213e9, "contraction": 1.344e9}
+TRAFFIC_PER_LAUNCH = {"gather": 0.212e9, "contraction": 1.344e9}
 METRIC = "galaxy pairs/s + Upsilon contraction TFLOP/s; mixed vs FP64 form at stated rel err"
 
 

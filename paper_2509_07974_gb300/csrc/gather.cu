@@ -280,10 +280,8 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   double* e2 = reinterpret_cast<double*>(acc + L.rec);
   float* e2f = reinterpret_cast<float*>(e2 + 65);
   float* win = e2f + 65;
-  int* cnt = reinterpret_cast<int*>(win + 65);
-  int* off = cnt + 64;
-  int* run = off + 65;
-  int* wcnt = run + 64;
+  int* off = reinterpret_cast<int*>(win + 65);  // [65] bin offsets of the chunk
+  int* wcnt = off + 65;                          // [warps][64] per-warp bin counts / positions
   int* rstart = wcnt + kWarps * 64;
   int* rpre = rstart + kMaxRows;
   int* misc = rpre + kMaxRows + 1;
@@ -541,7 +539,7 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   a.mb = (npow + nblk - 1) / nblk;
   a.nblk = (npow + a.mb - 1) / a.mb;
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
-                       (64 + 65 + 64 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64 +
+                       (65 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64 +
                        (sizeof(R) == 4 && MB >= 6 ? (size_t)bins.nb * a.nblk * 10 * sizeof(R) : 0);
   const size_t budget = MINB == 1 ? 227 * 1024 : 113 * 1024;
   constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R) + 1;

@@ -132,14 +132,12 @@ gather_tc_kernel(const GTcArgs args, float2* __restrict__ rec, float2* __restric
   double* e2 = reinterpret_cast<double*>(kbl + args.max_kb);
   float* e2f = reinterpret_cast<float*>(e2 + 65);
   float* win = e2f + 65;
-  int* cnt = reinterpret_cast<int*>(win + 65);
-  int* off = cnt + 64;
-  int* run = off + 65;
-  int* wcnt = run + 64;
+  int* off = reinterpret_cast<int*>(win + 65);  // [65] bin offsets of the chunk
+  int* wcnt = off + 65;                          // [warps][64] per-warp bin counts / positions
   int* rstart = wcnt + kWarps * 64;
   int* rpre = rstart + kMaxRows;
   int* misc = rpre + kMaxRows + 1;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(misc + 8);  // 8-byte aligned: offsets above are even
+  uint64_t* bars = reinterpret_cast<uint64_t*>(misc + 8);  // 8-byte aligned: 202 + 64 kWarps ints above
   uint64_t* st_full = bars;
   uint64_t* st_empty = bars + kGroups;
   uint64_t* d_full = bars + 2 * kGroups;
@@ -497,7 +495,7 @@ int gtc_npow(int N) {
 
 size_t gtc_fixed_bytes(const Layout& L, int npc, int max_kb) {
   return (size_t)kGroups * 2 * npc * 128 + (size_t)kGroups * kXpRows * kXpStride * 4 + (size_t)L.rec * 8 +
-         (size_t)max_kb * 16 + 65 * 8 + 2 * 65 * 4 + (64 + 65 + 64 + kGWarps * 64 + 2 * kMaxRows + 1 + 8) * 4 +
+         (size_t)max_kb * 16 + 65 * 8 + 2 * 65 * 4 + (65 + kGWarps * 64 + 2 * kMaxRows + 1 + 8) * 4 +
          10 * 8 + 8 + 1024;
 }
 
