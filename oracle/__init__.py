@@ -187,3 +187,8 @@ def xi_from_acc(xi_acc):
     xp = np.where(den != 0, acc[:, 0] / safe, 0)
     xm = np.where(den != 0, acc[:, 1] / safe, 0)
     return np.stack([xp.real, xp.imag, xm.real, xm.imag], axis=1)
+
+
+# direct estimator of <M_ap^2> and <M_ap^4> (Sect. 5.2, Eq. MapDirectEstimator); numpy only
+from .map_direct import (aperture_record, crittenden_q, elementary_symmetric,  # noqa: E402
+                         map_direct, moments_from_records, tangential_shear)
