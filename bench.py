@@ -233,6 +233,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def direct_estimator(est, tp, ts, tw, pos, sh, w, side, dev, stream, flush, args, baselines):
+    """Direct <M_ap^4> estimator (Sect. 5.2, Eq. MapDirectEstimator) on the same catalogue:
+    24 log radii 1'-32', aperture lattices of spacing theta at least 4 theta inside the field,
+    one ext4pcf_map_direct call per pass (grid build included).  Timed on its own, after the
+    main measurement: W warm-up passes, max(K, 5) timed passes with L2 flushed between them."""
+    import torch
+
+    import synth
+    from paper_2509_07974_gb300 import ext4pcf
+    cfg = synth.DIRECT
+    radii = np.ascontiguousarray(synth.direct_radii())
+    lat = [ext4pcf.aperture_lattice((0.0, 0.0, side, side), t, cfg["spacing"] * t) for t in radii]
+    offs = np.zeros(len(radii) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum([len(x) for x in lat])
+    cen_h = np.ascontiguousarray(np.vstack(lat))
+    cen = torch.tensor(cen_h, device=dev)
+    mom = torch.zeros((len(radii), 8), dtype=torch.float64, device=dev)
+    rec = torch.zeros((int(offs[-1]), 8), dtype=torch.float64, device=dev)
+
+    def call(p, s_, w_, c_, m_):
+        ext4pcf.ext4pcf_map_direct(est.ctx, p, s_, w_, len(w), radii, len(radii), c_, offs, rec, m_)
+
+    mom.zero_()
+    call(tp, ts, tw, cen, mom)
+    torch.cuda.synchronize()
+    pairs = float(rec[:, 6].sum().item())
+    for _ in range(args.warmup):
+        mom.zero_()
+        call(tp, ts, tw, cen, mom)
+    torch.cuda.synchronize()
+    n_t = max(args.steps, 5)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_t)]
+    for k in range(n_t):
+        flush.fill_(float(k))
+        mom.zero_()
+        evs[k][0].record(stream)
+        call(tp, ts, tw, cen, mom)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / n_t
+    # end to end: catalogue and centres from pinned host memory, moments read back
+    hp, hs, hw = (torch.tensor(a).pin_memory() for a in (pos, sh, w))
+    hc = torch.tensor(cen_h).pin_memory()
+    hm = np.zeros((len(radii), 8))
+    e2e_t = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hm[:] = 0.0
+        call(hp, hs, hw, hc, hm)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = sum(e2e_t) / len(e2e_t)
+    m = mom.cpu().numpy()
+    out = {"workload": cfg["name"], "radii": len(radii), "apertures": int(offs[-1]),
+           "pairs_per_pass": pairs, "value": pairs / (ms / 1e3), "unit": "aperture-galaxy pairs/s",
+           "ms_per_pass": ms, "dtype": "f32 terms, f64 power sums",
+           "l2": "flushed between passes (256 MB write)",
+           "e2e": {"value": pairs / e2e, "unit": "aperture-galaxy pairs/s",
+                   "h2d_bytes_per_step": int(hp.numel() * 8 + hs.numel() * 8 + hw.numel() * 8 + hc.numel() * 8),
+                   "d2h_bytes_per_step": int(hm.nbytes)},
+           "map4_by_radius": {"%.2f" % radii[i]: float(m[i, 5]) for i in (0, 12, 23)},
+           "cpu_baseline": None}
+    if baselines:
+        import oracle
+        t8 = float(radii[16])
+        pick = np.random.default_rng(5).choice(len(lat[16]), size=6, replace=False)
+        t0 = time.perf_counter()
+        opairs = sum(oracle.aperture_record(pos, sh, w, lat[16][i], t8)[6] for i in pick)
+        odt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": opairs / odt, "unit": "aperture-galaxy pairs/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "6 apertures of radius %.2f' (numpy, all galaxies tested), %d pairs, %.1f s"
+                                         % (t8, opairs, odt)}
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -328,6 +404,11 @@ def run_ours(args):
     e2e = sum(e2e_t) / len(e2e_t)
     h2d = hp.numel() * 8 + hs.numel() * 8 + hw.numel() * 8 + (hmask.numel() if hmask is not None else 0)
     d2h = m4.nbytes + eb.nbytes + disc.nbytes
+
+    direct = None
+    if rank == 0:
+        direct = direct_estimator(est, tp, ts, tw, pos, sh, w, c["side"], dev, stream, flush, args,
+                                  world == 1 and not args.no_baselines)
 
     # rooflines of the two dominant kernels, algorithmic FLOP per launch over the average
     # launch duration in the timed steps.  Gather: FP32 work on the CUDA cores against the
@@ -425,6 +506,7 @@ def run_ours(args):
                 "roofline_secondary": roof_other,
                 "fp64_form": fp64_info,
                 "cpu_baseline": cpu,
+                "next_rows": {"map_direct": direct},
                 "clocks": clocks,
                 "gpu_launches": int((bd["launches"] + map4_launches) * args.steps)}
         print(json.dumps(line), flush=True)

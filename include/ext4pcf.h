@@ -169,6 +169,37 @@ EXT4PCF_API int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const d
 EXT4PCF_API int ext4pcf_to_real_space_noalloc(const double* upsilon, int n_bins, int n_max, int n_phi,
                                               double* gamma, double* norm, void* stream);
 
+/* Direct estimator of <M_ap^2> and <M_ap^4> (paper Sect. 5.2, Eq. MapDirectEstimator) for the
+ * filter Q_theta of Eq. CrittendenQ, cut at |vartheta_i - vartheta| < 4 theta.  For each
+ * aperture (centre vartheta, radius theta) with a_i = w_i Q_theta,i gamma_t,i (gamma_t the real
+ * part of Eq. gammatx_def about the centre), the distinct quadruplet sums over the galaxies
+ * inside the cut are 4! e_4(a) (numerator) and 4! e_4(w) (denominator), e_k the elementary
+ * symmetric polynomials, computed from the power sums of a and w (Newton's identities):
+ * linear in the galaxies.  Per-galaxy terms are FP32, power sums FP64.
+ *   positions, shears, weights  device or host, as for ext4pcf_measure (one catalogue)
+ *   n_gal           0 .. 2^31-1
+ *   thetas          host, double [n_theta], finite and > 0 (1 <= n_theta <= 4096)
+ *   centres         device or host, double [n_centres][2]: aperture centres, those of radius
+ *                   thetas[t] in rows centre_offsets[t] .. centre_offsets[t+1]-1 (the caller
+ *                   chooses them, e.g. a lattice at least 4 theta inside the field)
+ *   centre_offsets  host, int64 [n_theta+1], centre_offsets[0] = 0, non-decreasing
+ *   ap_records      device or host, double [n_centres][8] or NULL, WRITTEN (not accumulated):
+ *                   e1(a), e2(a), e4(a), e1(w), e2(w), e4(w), galaxies inside the cut, 0
+ *   moments         device or host, double [n_theta][8]: entries 0..4 ACCUMULATED
+ *                   (sum e4(a), sum e4(w), sum e2(a), sum e2(w), apertures), so patches add
+ *                   up; entries 5..7 recomputed from them on every call:
+ *                   <M_ap^4> = A^4 [0]/[1], <M_ap^2> = A^2 [2]/[3], A = pi (4 theta)^2 the
+ *                   area of the cut disc, and the connected part <M_ap^4> - 3 <M_ap^2>^2.
+ *                   Summing numerators and denominators weights each aperture's ratio by
+ *                   its denominator (inverse shot-noise weights).
+ * Device-only calls are stream-ordered after one synchronisation (the bounding box of the
+ * catalogue is read back to size the grid); host outputs make the call synchronous.
+ * Returns EXT4PCF_OK, EXT4PCF_E_INVALID_ARG, EXT4PCF_E_OOM or EXT4PCF_E_CUDA. */
+EXT4PCF_API int ext4pcf_map_direct(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                                   const double* weights, int64_t n_gal, const double* thetas,
+                                   int n_theta, const double* centres, const int64_t* centre_offsets,
+                                   double* ap_records, double* moments);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 EXT4PCF_API const char* ext4pcf_last_error(const ext4pcf_ctx* ctx);
 

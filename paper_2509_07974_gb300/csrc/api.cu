@@ -1,6 +1,7 @@
 // C ABI of libext4pcf: argument checking, scratch management and the per-catalogue
 // pipeline  grid build -> [gather -> contraction -> correction sums] per centre wave ->
 // correction application.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -21,6 +22,9 @@ cudaError_t map4_partials(const double* ups, const double* edges_host, int nb, i
 cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const double* d_xipm,
                                const double* d_tb, const double* d_area, int nb, const double* d_ap,
                                double* d_m4, double* d_eb, double* d_disc, cudaStream_t s);
+int map_direct_splits(int n_ap, int sm_count, double theta, double cell);
+cudaError_t map_direct_radius(const SortedCat& cat, const double* centres, int n_ap, double theta,
+                              int nsplit, double* sums, double* rec, double* mom, cudaStream_t s);
 }  // namespace ext4pcf
 
 namespace ext4pcf {
@@ -68,6 +72,8 @@ struct ext4pcf_ctx {
   DBuf centres, flags, rec, xw, corr, counter, ncen;
   // transforms
   DBuf t_norm, t_gam, t_E, t_part, t_small;
+  // direct aperture estimator: centres, per-split sums, staged outputs
+  DBuf ap_cen, ap_sums, io_rec, io_mom;
   // tensor-core contraction: work items (built once per shape) and the device status word
   DBuf tc_items, tc_xb, status;
   int tc_N = -1, tc_nb = -1;
@@ -560,6 +566,132 @@ int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radia
     map4_eb[k] += res[16 * n_ap + k];
     if (map4_disc && xi_acc) map4_disc[k] += res[32 * n_ap + k];
   }
+  return EXT4PCF_OK;
+}
+
+int ext4pcf_map_direct(ext4pcf_ctx* ctx, const double* positions, const double* shears, const double* weights,
+                       int64_t n_gal, const double* thetas, int n_theta, const double* centres,
+                       const int64_t* centre_offsets, double* ap_records, double* moments) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  ctx->err.clear();
+  if (!thetas || !centre_offsets || !moments || n_theta < 1 || n_theta > 4096)
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "thetas, centre_offsets and moments are required (1 <= n_theta <= 4096)");
+  if (n_gal < 0 || n_gal > 2147483647LL) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_gal out of range");
+  if (n_gal > 0 && (!positions || !shears || !weights)) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null catalogue");
+  double tmin = 0, tmax = 0;
+  for (int t = 0; t < n_theta; ++t) {
+    if (!(thetas[t] > 0) || !std::isfinite(thetas[t]))
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "aperture radii must be finite and > 0");
+    tmin = t ? std::fmin(tmin, thetas[t]) : thetas[t];
+    tmax = t ? std::fmax(tmax, thetas[t]) : thetas[t];
+  }
+  if (centre_offsets[0] != 0) return fail(ctx, EXT4PCF_E_INVALID_ARG, "centre_offsets[0] must be 0");
+  for (int t = 0; t < n_theta; ++t)
+    if (centre_offsets[t + 1] < centre_offsets[t] || centre_offsets[t + 1] - centre_offsets[t] > 2147483647LL)
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "centre_offsets must be non-decreasing");
+  const int64_t n_cen = centre_offsets[n_theta];
+  if (n_cen > 0 && !centres) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null centres");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t s = ctx->stream;
+  const size_t n = (size_t)n_gal;
+  // ---- stage host inputs / outputs
+  const double* d_pos = positions;
+  const double* d_sh = shears;
+  const double* d_w = weights;
+  const double* d_cen = centres;
+  if (n > 0 && !is_device_ptr(positions)) {
+    ENSURE(ctx->in_pos, n * 16);
+    CK(cudaMemcpyAsync(ctx->in_pos.p, positions, n * 16, cudaMemcpyHostToDevice, s));
+    d_pos = (const double*)ctx->in_pos.p;
+  }
+  if (n > 0 && !is_device_ptr(shears)) {
+    ENSURE(ctx->in_shear, n * 16);
+    CK(cudaMemcpyAsync(ctx->in_shear.p, shears, n * 16, cudaMemcpyHostToDevice, s));
+    d_sh = (const double*)ctx->in_shear.p;
+  }
+  if (n > 0 && !is_device_ptr(weights)) {
+    ENSURE(ctx->in_w, n * 8);
+    CK(cudaMemcpyAsync(ctx->in_w.p, weights, n * 8, cudaMemcpyHostToDevice, s));
+    d_w = (const double*)ctx->in_w.p;
+  }
+  if (n_cen > 0 && !is_device_ptr(centres)) {
+    ENSURE(ctx->ap_cen, (size_t)n_cen * 16);
+    CK(cudaMemcpyAsync(ctx->ap_cen.p, centres, (size_t)n_cen * 16, cudaMemcpyHostToDevice, s));
+    d_cen = (const double*)ctx->ap_cen.p;
+  }
+  const bool host_rec = ap_records && !is_device_ptr(ap_records);
+  double* d_rec = ap_records;
+  if (!ap_records || host_rec) {
+    ENSURE(ctx->io_rec, (size_t)n_cen * 64);
+    d_rec = (double*)ctx->io_rec.p;
+  }
+  const bool host_mom = !is_device_ptr(moments);
+  double* d_mom = moments;
+  if (host_mom) {
+    ENSURE(ctx->io_mom, (size_t)n_theta * 64);
+    CK(cudaMemcpyAsync(ctx->io_mom.p, moments, (size_t)n_theta * 64, cudaMemcpyHostToDevice, s));
+    d_mom = (double*)ctx->io_mom.p;
+  }
+  // ---- grid: power-of-two cells (exact float corner arithmetic), about eight per cut
+  // radius of the smallest aperture, at most ~4096 per axis and per largest cut diameter
+  SortedCat cat;
+  cat.n = 0;
+  double cell = 1.0;
+  if (n > 0) {
+    const int nk = (int)n;
+    ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
+    CK(grid_bbox(d_pos, nk, (double*)ctx->bbox.p, s));
+    double bb[4];
+    CK(cudaMemcpyAsync(bb, ctx->bbox.p, 32, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!std::isfinite(bb[0]) || !std::isfinite(bb[1]) || !std::isfinite(bb[2]) || !std::isfinite(bb[3]))
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "non-finite positions");
+    const double extent = std::fmax(bb[2] - bb[0], bb[3] - bb[1]);
+    const double target = std::fmax(0.5 * tmin, std::fmax(extent / 2048.0, 4.0 * tmax / 2048.0));
+    int ex;
+    std::frexp(target, &ex);
+    cell = std::ldexp(1.0, ex - 1);  // largest power of two <= target
+    const int ncx = (int)std::floor((bb[2] - bb[0]) / cell) + 1;
+    const int ncy = (int)std::floor((bb[3] - bb[1]) / cell) + 1;
+    const size_t ncells = (size_t)ncx * ncy;
+    const int ntiles = (nk + 2047) / 2048;
+    ENSURE(ctx->keys, n * 4); ENSURE(ctx->keys_alt, n * 4);
+    ENSURE(ctx->perm, n * 4); ENSURE(ctx->perm_alt, n * 4);
+    ENSURE(ctx->cell_start, (ncells + 1) * 4);
+    ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
+    ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
+    ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
+    ENSURE(ctx->p4, n * 16); ENSURE(ctx->s4, n * 16);
+    GridBuffers gb;
+    gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+    gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+    gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ncells + 1;
+    gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+    gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
+    gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
+    gb.p4 = (float4*)ctx->p4.p; gb.s4 = (float4*)ctx->s4.p; gb.bbox = (double*)ctx->bbox.p;
+    CK(grid_sort(d_pos, d_sh, d_w, nk, bb[0], bb[1], cell, ncx, ncy, true, gb, cat, s));
+  }
+  // ---- apertures, one radius at a time
+  size_t sums_need = 16;
+  std::vector<int> splits(n_theta);
+  for (int t = 0; t < n_theta; ++t) {
+    const int na = (int)(centre_offsets[t + 1] - centre_offsets[t]);
+    splits[t] = map_direct_splits(na, ctx->sm_count, thetas[t], cell);
+    sums_need = std::max(sums_need, (size_t)na * splits[t] * 9 * 8);
+  }
+  ENSURE(ctx->ap_sums, sums_need);
+  for (int t = 0; t < n_theta; ++t) {
+    const int64_t c0 = centre_offsets[t];
+    const int na = (int)(centre_offsets[t + 1] - c0);
+    CK(map_direct_radius(cat, d_cen + 2 * c0, na, thetas[t], splits[t], (double*)ctx->ap_sums.p, d_rec + 8 * c0,
+                         d_mom + 8 * t, s));
+  }
+  if (host_rec && n_cen > 0)
+    CK(cudaMemcpyAsync(ap_records, d_rec, (size_t)n_cen * 64, cudaMemcpyDeviceToHost, s));
+  if (host_mom) CK(cudaMemcpyAsync(moments, d_mom, (size_t)n_theta * 64, cudaMemcpyDeviceToHost, s));
+  if (host_rec || host_mom) CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
   return EXT4PCF_OK;
 }
 

@@ -1,8 +1,8 @@
 """ctypes binding of libext4pcf (include/ext4pcf.h): argument marshalling only.
 
 The functions ``ext4pcf_create``, ``ext4pcf_destroy``, ``ext4pcf_measure``,
-``ext4pcf_to_real_space``, ``ext4pcf_to_map4`` and ``ext4pcf_last_error`` mirror the C ABI
-one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
+``ext4pcf_to_real_space``, ``ext4pcf_to_map4``, ``ext4pcf_to_real_space_noalloc``,
+``ext4pcf_map_direct`` and ``ext4pcf_last_error`` mirror the C ABI one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
 integer addresses or None.  ``Estimator`` wraps them for torch users: it allocates outputs
 and passes the current CUDA stream.  Every computation happens in the CUDA library; there
 is no fallback, and loading fails loudly if the library has not been built.
@@ -67,10 +67,11 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_to_map4.argtypes = [P, P, P, I, I, I, P, I, P, P, P, P]
     lib.ext4pcf_to_real_space_noalloc.argtypes = [P, I, I, I, P, P, P]
     lib.ext4pcf_to_real_space_noalloc.restype = I
+    lib.ext4pcf_map_direct.argtypes = [P, P, P, P, I64, P, I, P, P, P, P]
     lib.ext4pcf_last_error.argtypes = [P]
     lib.ext4pcf_last_error.restype = ctypes.c_char_p
     for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_to_real_space",
-              "ext4pcf_to_map4"):
+              "ext4pcf_to_map4", "ext4pcf_map_direct"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -145,6 +146,29 @@ def ext4pcf_to_real_space_noalloc(upsilon, n_bins, n_max, n_phi, gamma, norm, st
     st = getattr(stream, "cuda_stream", stream)
     return load().ext4pcf_to_real_space_noalloc(_addr(upsilon), int(n_bins), int(n_max), int(n_phi),
                                                 _addr(gamma), _addr(norm), st)
+
+
+def ext4pcf_map_direct(ctx, positions, shears, weights, n_gal, thetas, n_theta, centres,
+                       centre_offsets, ap_records, moments) -> int:
+    rc = load().ext4pcf_map_direct(ctx, _addr(positions), _addr(shears), _addr(weights), int(n_gal),
+                                   _addr(thetas), int(n_theta), _addr(centres), _addr(centre_offsets),
+                                   _addr(ap_records), _addr(moments))
+    return _check(ctx, rc)
+
+
+def aperture_lattice(field, theta, spacing):
+    """Aperture centres on a square lattice of the given spacing, at least 4 theta inside
+    the rectangle field = (x_min, y_min, x_max, y_max), so that no aperture's cut disc leaves
+    the field (float64 [n][2], possibly empty).  Host-side sampling only."""
+    import numpy as np
+    x0, y0, x1, y1 = (float(v) for v in field)
+    m = 4.0 * theta
+    axes = []
+    for lo, hi in ((x0 + m, x1 - m), (y0 + m, y1 - m)):
+        k = int(np.floor((hi - lo) / spacing + 1e-9)) + 1 if hi >= lo else 0
+        axes.append(lo + 0.5 * ((hi - lo) - (k - 1) * spacing) + spacing * np.arange(k))
+    gx, gy = np.meshgrid(axes[0], axes[1])
+    return np.ascontiguousarray(np.stack([gx.ravel(), gy.ravel()], 1), dtype=np.float64)
 
 
 # ---- torch convenience wrapper ---------------------------------------------------------
@@ -226,6 +250,26 @@ class Estimator:
             xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64))
         ext4pcf_to_map4(self.ctx, upsilon, edges, nb, n_max, n_phi, ap, n_ap, xi, m4, eb, disc)
         return m4[..., 0] + 1j * m4[..., 1], eb, disc
+
+    def map_direct(self, positions, shears, weights, thetas, centres, moments=None,
+                   want_records=False):
+        """Direct <M_ap^2>, <M_ap^4> estimator.  ``centres`` is a list (one per radius) of [n][2]
+        arrays (numpy or torch).  Returns (moments [n_theta][8], records [sum n][8] or None) as
+        torch float64 tensors on the catalogue's device."""
+        torch = self.torch
+        import numpy as np
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64)).ravel()
+        cen = [torch.as_tensor(c, dtype=torch.float64).reshape(-1, 2) for c in centres]
+        offs = np.zeros(th.size + 1, dtype=np.int64)
+        offs[1:] = np.cumsum([c.shape[0] for c in cen])
+        dev = positions.device
+        cen_all = (torch.cat(cen) if cen else torch.zeros((0, 2), dtype=torch.float64)).to(dev).contiguous()
+        if moments is None:
+            moments = torch.zeros((th.size, 8), dtype=torch.float64, device=dev)
+        rec = torch.zeros((int(offs[-1]), 8), dtype=torch.float64, device=dev) if want_records else None
+        ext4pcf_map_direct(self.ctx, positions, shears, weights, positions.shape[0], th, th.size,
+                           cen_all if offs[-1] > 0 else None, offs, rec, moments)
+        return moments, rec
 
 
 def as_complex(t):

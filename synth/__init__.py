@@ -89,3 +89,15 @@ def grf2e6_workload(n: int | None = None, grid: int | None = None):
     c = GRF2E6
     pos, shear, w = grf_catalog(n or c["n"], c["side"], c["seed"], grid=grid or c["grid"])
     return pos, shear, w, log_edges(c["lo"], c["hi"], c["nb"]), c["nmax"]
+
+
+# Direct aperture-mass estimator: the GRF catalogue above, 24 logarithmically spaced aperture
+# radii 1'-32' (the radii of the paper's comparison of the two estimators, Sect. 5.3),
+# centres on a square lattice of spacing theta at least 4 theta inside the field.
+DIRECT = dict(name="direct M_ap^4: GRF 2e6 gal, 600'x600', 24 log radii 1'-32', lattice spacing theta",
+              lo=1.0, hi=32.0, n_radii=24, spacing=1.0)
+
+
+def direct_radii():
+    c = DIRECT
+    return np.geomspace(c["lo"], c["hi"], c["n_radii"])

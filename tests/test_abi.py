@@ -58,3 +58,24 @@ def test_create_without_gpu_is_an_error_code(lib):
     cfg = ext4pcf.Config(device=0, precision=0)
     with pytest.raises(ext4pcf.Ext4pcfError):
         ext4pcf.ext4pcf_create(cfg)
+
+
+def test_aperture_lattice_stays_four_radii_inside():
+    """Host-side aperture sampling of the direct estimator: a square lattice of the given
+    spacing whose centres all lie at least 4 theta inside the field, centred in it."""
+    import numpy as np
+    from paper_2509_07974_gb300 import ext4pcf
+    for field, theta, sp in (((0, 0, 60, 40), 1.3, 1.3), ((-5, 2, 30, 9), 0.5, 0.7), ((0, 0, 10, 10), 3.0, 1.0)):
+        c = ext4pcf.aperture_lattice(field, theta, sp)
+        if len(c) == 0:
+            assert field[2] - field[0] < 8 * theta or field[3] - field[1] < 8 * theta
+            continue
+        assert c[:, 0].min() >= field[0] + 4 * theta - 1e-12 and c[:, 0].max() <= field[2] - 4 * theta + 1e-12
+        assert c[:, 1].min() >= field[1] + 4 * theta - 1e-12 and c[:, 1].max() <= field[3] - 4 * theta + 1e-12
+        xs, ys = np.unique(c[:, 0]), np.unique(c[:, 1])
+        assert len(c) == len(xs) * len(ys)
+        for a in (xs, ys):
+            if len(a) > 1:
+                np.testing.assert_allclose(np.diff(a), sp, rtol=1e-12)
+        # no room for another lattice column or row
+        assert (xs.max() - xs.min()) + sp > (field[2] - field[0]) - 8 * theta
