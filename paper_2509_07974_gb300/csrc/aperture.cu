@@ -13,20 +13,30 @@
 // the factor 1 / r^2 of cos 2 zeta and sin 2 zeta cancelling the r^2 of the filter.
 //
 // Kernels (one launch of each per radius):
-//   aperture_sums    one CTA per (aperture, row split): scans the cell rows that meet the disc
-//                    (each row is one contiguous range of the cell-sorted catalogue), evaluates
-//                    a_i in FP32 and accumulates the eight power sums of a and w in FP32 over
-//                    at most 32 galaxies per thread before promoting them to FP64;
-//   aperture_finish  one thread per aperture: adds the splits in order, applies Newton's
-//                    identities in FP64 and writes the aperture record;
-//   aperture_moments one CTA: adds the records of all apertures (fixed order) into the
-//                    per-radius sums and derives <M_ap^4>, <M_ap^2> and the connected part.
+//   aperture_prep    one thread per aperture: the cell of the centre and its offset inside the
+//                    cell (FP64 once per aperture; the kernels below use no FP64 on their
+//                    per-galaxy path);
+//   aperture_sums    one WARP per (aperture, row split): scans the cell rows that meet the disc
+//                    (each row a contiguous range of the cell-sorted catalogue), evaluates a_i
+//                    in FP32 and accumulates the eight power sums of a and w, in FP32 over at
+//                    most 32 galaxies per lane and then into unevaluated FP32 pairs (hi + lo,
+//                    error-free two-sum), reduced across the warp the same way;
+//   aperture_finish  one thread per aperture: adds the splits in order in FP64, applies
+//                    Newton's identities and writes the aperture record; one partial sum of
+//                    the records per block;
+//   aperture_moments one CTA: adds the block partials in order into the per-radius sums and
+//                    derives <M_ap^4>, <M_ap^2> and the connected part.
 //
-// Cut decisions: the FP32 distance is exact enough (relative error < 1e-6) that galaxies
-// further than a relative 1e-5 from the cut radius are classified correctly in FP32; those
-// inside that band are decided again in FP64 as (x - x_c)^2 + (y - y_c)^2 < (4 theta)^2
-// with separately rounded products.
+// Row and chord limits are computed in FP32 in cell units relative to the aperture's cell:
+// every bound is widened by a slack (1e-3 cell, above the FP32 rounding of quantities up to
+// the largest cut radius of 4096 cells) and the squared half-chord by a bound on its rounding
+// error, so every galaxy inside the cut lies in a scanned cell; scanning a few extra cells is
+// harmless (the cut decides).  Cut decisions: the FP32 distance is exact enough (relative
+// error < 1e-6) that galaxies further than a relative 1e-5 from the cut radius are classified
+// correctly in FP32; those inside that band are decided again in FP64 as
+// (x - x_c)^2 + (y - y_c)^2 < (4 theta)^2 with separately rounded products.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "common.cuh"
@@ -36,8 +46,10 @@ namespace {
 
 constexpr int kApThreads = 128;
 constexpr int kApWarps = kApThreads / 32;
-constexpr int kRowsChunk = 1024;
-constexpr int kPromote = 32;
+constexpr int kWarpRows = 256;  // rows per chunk of one warp
+constexpr int kPromote = 32;    // galaxies per lane between FP32 partial flushes
+constexpr float kSlack = 1e-3f; // cell units
+constexpr int kSumFloats = 20;  // per work item: 8 (hi, lo) pairs, count, padding
 
 struct ApArgs {
   const float4* p4;
@@ -46,101 +58,113 @@ struct ApArgs {
   const double* py;
   const int* cell_start;
   int ncx, ncy;
-  double x0, y0, cell, inv_cell;
   float cellf;
+  float rc;               // cut radius 4 theta in cells (float)
+  float invt;             // 1 / theta
   const double* centres;  // [n_ap][2]
-  int n_ap, nsplit;
-  double theta;
-  double* sums;  // [n_ap][nsplit][9]: power sums of a/c (k = 1..4), of w (k = 1..4), count
+  const int4* prep;       // [n_ap]: cell x, cell y, offset x, offset y (cells, float bits)
+  int nsplit;
+  long long n_items;      // n_ap * nsplit
+  double R2;              // (4 theta)^2
+  float* sums;            // [n_items][kSumFloats]
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+__global__ void aperture_prep(const double* __restrict__ centres, int n_ap, double x0, double y0, double cell,
+                              double inv_cell, int ncx, int ncy, double R, int4* __restrict__ prep) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_ap) return;
+  const double ax = centres[2 * a], ay = centres[2 * a + 1];
+  // a disc that cannot reach the grid (or a non-finite centre) holds no galaxy: marked empty,
+  // so that the cell indices below stay within a few thousand of the grid
+  const double mx = R + 2.0 * cell;
+  if (!(ax >= x0 - mx && ax <= x0 + ncx * cell + mx && ay >= y0 - mx && ay <= y0 + ncy * cell + mx)) {
+    prep[a] = make_int4(INT_MIN, 0, 0, 0);
+    return;
+  }
+  const double cx = floor((ax - x0) * inv_cell), cy = floor((ay - y0) * inv_cell);
+  const float ox = (float)(((ax - x0) - cx * cell) * inv_cell);
+  const float oy = (float)(((ay - y0) - cy * cell) * inv_cell);
+  prep[a] = make_int4((int)cx, (int)cy, __float_as_int(ox), __float_as_int(oy));
+}
+
+// (hi, lo) += b with the rounding error of hi + b kept in lo (two-sum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
+  const float s = hi + b;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (b - bb);
+  hi = s;
 }
 
 __global__ void __launch_bounds__(kApThreads) aperture_sums(ApArgs A) {
-  __shared__ int s_start[kRowsChunk];
-  __shared__ int s_pre[kRowsChunk + 1];
-  __shared__ int s_tot[kApWarps];
-  __shared__ double s_red[kApWarps][9];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int ap = blockIdx.x / A.nsplit, sp = blockIdx.x % A.nsplit;
-  const double ax = A.centres[2 * ap], ay = A.centres[2 * ap + 1];
-  double P[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  __shared__ int s_start[kApWarps][kWarpRows];
+  __shared__ int s_pre[kApWarps][kWarpRows + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long item = (long long)blockIdx.x * kApWarps + wid;
+  if (item >= A.n_items) return;  // whole warp; no block-level barrier below
+  const int ap = (int)(item / A.nsplit), sp = (int)(item % A.nsplit);
+  const int4 pr = A.prep[ap];
+  float H[8] = {0, 0, 0, 0, 0, 0, 0, 0}, L[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int cnt = 0;
-  if (isfinite(ax) && isfinite(ay)) {
-    const double theta = A.theta, R = 4.0 * theta, R2 = __dmul_rn(R, R);
-    // slack in position units that covers the rounding of cell indices and of the chord
-    const double sl = A.cell * 1e-6 +
-                      1e-14 * (fabs(ax) + fabs(ay) + fabs(A.x0) + fabs(A.y0) + (A.ncx + A.ncy) * A.cell);
-    const double Rs = R + sl;
-    double ylo = floor((ay - Rs - A.y0) * A.inv_cell), yhi = floor((ay + Rs - A.y0) * A.inv_cell);
-    ylo = fmax(ylo, 0.0);
-    yhi = fmin(yhi, (double)(A.ncy - 1));
+  if (pr.x != INT_MIN) {
+    const int acx = pr.x, acy = pr.y;
+    const float ox = __int_as_float(pr.z), oy = __int_as_float(pr.w);
+    const float Rs = A.rc + kSlack;
+    const float h2err = 1e-6f * (A.rc + 2.f) * (A.rc + 2.f);
+    const int ylo = max(acy + (int)floorf(oy - Rs), 0);
+    const int yhi = min(acy + (int)floorf(oy + Rs), A.ncy - 1);
     if (ylo <= yhi) {
-      // this split's rows
-      const long long nrow = (long long)(yhi - ylo) + 1;
-      const int ra = (int)ylo + (int)(nrow * sp / A.nsplit);
-      const int rz = (int)ylo + (int)(nrow * (sp + 1) / A.nsplit);  // exclusive
-      // aperture cell corner (exact multiple of the power-of-two cell) and offset
-      const double acx = fmin(fmax(floor((ax - A.x0) * A.inv_cell), -1048576.0), 1048576.0);
-      const double acy = fmin(fmax(floor((ay - A.y0) * A.inv_cell), -1048576.0), 1048576.0);
+      const int nrow = yhi - ylo + 1;
+      const int ra = ylo + (int)((long long)nrow * sp / A.nsplit);
+      const int rz = ylo + (int)((long long)nrow * (sp + 1) / A.nsplit);  // exclusive
+      // float distance: (corner_j - corner_c) is exact (power-of-two cell), offsets are small
       const float acxf = (float)acx * A.cellf, acyf = (float)acy * A.cellf;
-      const float fxf = (float)((ax - A.x0) - acx * A.cell);
-      const float fyf = (float)((ay - A.y0) - acy * A.cell);
-      const float invt = (float)(1.0 / theta);
+      const float fxf = ox * A.cellf, fyf = oy * A.cellf;
+      const float invt = A.invt;
       const float band = 16.f * 1e-5f * (1.f + A.cellf * invt);
-      for (int r0 = ra; r0 < rz; r0 += kRowsChunk) {
-        const int nr = min(kRowsChunk, rz - r0);
-        const int per = (nr + kApThreads - 1) / kApThreads;
-        const int rb = min(tid * per, nr), re = min(rb + per, nr);
+      for (int r0 = ra; r0 < rz; r0 += kWarpRows) {
+        const int nr = min(kWarpRows, rz - r0);
+        const int per = (nr + 31) >> 5;
+        const int rb = min(lane * per, nr), re = min(rb + per, nr);
         int mine = 0;
         for (int r = rb; r < re; ++r) {
           const int cy = r0 + r;
-          const double ylow = A.y0 + cy * A.cell, yhigh = ylow + A.cell;
-          const double dymin = fmax(0.0, fmax(ylow - ay, ay - yhigh));
+          const float k = (float)(cy - acy);
+          const float dymin = fmaxf(0.f, fmaxf(k - oy, oy - (k + 1.f)));
           int b = 0, len = 0;
           if (dymin < Rs) {
-            const double h = sqrt(Rs * Rs - dymin * dymin);
-            double xl = floor((ax - h - A.x0) * A.inv_cell), xh = floor((ax + h - A.x0) * A.inv_cell);
-            xl = fmax(xl, 0.0);
-            xh = fmin(xh, (double)(A.ncx - 1));
+            const float h = sqrtf(fmaf(Rs, Rs, -dymin * dymin) + h2err) + kSlack;
+            const int xl = max(acx + (int)floorf(ox - h), 0);
+            const int xh = min(acx + (int)floorf(ox + h), A.ncx - 1);
             if (xl <= xh) {
               const int row = cy * A.ncx;
-              b = A.cell_start[row + (int)xl];
-              len = A.cell_start[row + (int)xh + 1] - b;
+              b = A.cell_start[row + xl];
+              len = A.cell_start[row + xh + 1] - b;
             }
           }
-          s_start[r] = b;
-          s_pre[r] = len;
+          s_start[wid][r] = b;
+          s_pre[wid][r] = len;
           mine += len;
         }
-        // block-wide exclusive scan of the per-thread galaxy counts
+        // exclusive scan of the per-lane galaxy counts over the warp
         int incl = mine;
         for (int o = 1; o < 32; o <<= 1) {
           const int t = __shfl_up_sync(0xffffffffu, incl, o);
           if (lane >= o) incl += t;
         }
-        if (lane == 31) s_tot[wid] = incl;
-        __syncthreads();
-        int run = incl - mine, total = 0;
-        for (int q = 0; q < kApWarps; ++q) {
-          if (q < wid) run += s_tot[q];
-          total += s_tot[q];
-        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int run = incl - mine;
         for (int r = rb; r < re; ++r) {
-          const int len = s_pre[r];
-          s_pre[r] = run;
+          const int len = s_pre[wid][r];
+          s_pre[wid][r] = run;
           run += len;
         }
-        if (tid == 0) s_pre[nr] = total;
-        __syncthreads();
+        if (lane == 0) s_pre[wid][nr] = total;
+        __syncwarp();
         float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int k = 0, r = 0;
-        for (int v = tid; v < total; v += kApThreads) {
-          while (s_pre[r + 1] <= v) ++r;
-          const int j = s_start[r] + (v - s_pre[r]);
+        int kk = 0, r = 0;
+        for (int v = lane; v < total; v += 32) {
+          while (s_pre[wid][r + 1] <= v) ++r;
+          const int j = s_start[wid][r] + (v - s_pre[wid][r]);
           const float4 p = A.p4[j];
           const float4 g = A.s4[j];
           const float dx = (p.x - acxf) + (p.z - fxf);
@@ -149,8 +173,8 @@ __global__ void __launch_bounds__(kApThreads) aperture_sums(ApArgs A) {
           const float r2n = fmaf(u, u, w * w);
           bool in = r2n < 16.f;
           if (fabsf(r2n - 16.f) <= band) {
-            const double ddx = A.px[j] - ax, ddy = A.py[j] - ay;
-            in = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < R2;
+            const double ddx = A.px[j] - A.centres[2 * ap], ddy = A.py[j] - A.centres[2 * ap + 1];
+            in = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)) < A.R2;
           }
           if (in) {
             const float e = expf(-0.5f * r2n);
@@ -160,32 +184,37 @@ __global__ void __launch_bounds__(kApThreads) aperture_sums(ApArgs A) {
             f[4] += g.z; f[5] += w2; f[6] += w2 * g.z; f[7] += w2 * w2;
             ++cnt;
           }
-          if (++k == kPromote) {
+          if (++kk == kPromote) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) { P[i] += (double)f[i]; f[i] = 0.f; }
-            k = 0;
+            for (int i = 0; i < 8; ++i) { two_sum_acc(H[i], L[i], f[i]); f[i] = 0.f; }
+            kk = 0;
           }
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) P[i] += (double)f[i];
-        __syncthreads();  // s_start / s_pre / s_tot are rewritten by the next chunk
+        for (int i = 0; i < 8; ++i) two_sum_acc(H[i], L[i], f[i]);
+        __syncwarp();  // s_start / s_pre are rewritten by the next chunk
       }
     }
   }
-  // block reduction in a fixed order
-  double c = warp_sum((double)cnt);
+  // warp reduction of the (hi, lo) pairs and the count
 #pragma unroll
-  for (int i = 0; i < 8; ++i) P[i] = warp_sum(P[i]);
-  if (lane == 0) {
+  for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s_red[wid][i] = P[i];
-    s_red[wid][8] = c;
+    for (int i = 0; i < 8; ++i) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, H[i], o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, L[i], o);
+      two_sum_acc(H[i], L[i], h2);
+      L[i] += l2;
+    }
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   }
-  __syncthreads();
-  if (tid < 9) {
-    double t = 0;
-    for (int q = 0; q < kApWarps; ++q) t += s_red[q][tid];
-    A.sums[((size_t)ap * A.nsplit + sp) * 9 + tid] = t;
+  if (lane == 0) {
+    float4* o = reinterpret_cast<float4*>(A.sums + item * kSumFloats);
+    o[0] = make_float4(H[0], L[0], H[1], L[1]);
+    o[1] = make_float4(H[2], L[2], H[3], L[3]);
+    o[2] = make_float4(H[4], L[4], H[5], L[5]);
+    o[3] = make_float4(H[6], L[6], H[7], L[7]);
+    o[4] = make_float4(__int_as_float(cnt), 0.f, 0.f, 0.f);
   }
 }
 
@@ -201,33 +230,55 @@ __device__ __forceinline__ void newton(const double p[5], double n, double& e1, 
   if (n < 1.0) e1 = 0.0;
 }
 
-__global__ void aperture_finish(const double* __restrict__ sums, int n_ap, int nsplit, double theta,
-                                double* __restrict__ rec) {
-  const int ap = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ap >= n_ap) return;
-  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int sp = 0; sp < nsplit; ++sp)
-    for (int i = 0; i < 9; ++i) s[i] += sums[((size_t)ap * nsplit + sp) * 9 + i];
-  const double c = 1.0 / (4.0 * M_PI * theta * theta);  // a = b c
-  const double pa[5] = {0.0, s[0] * c, s[1] * c * c, s[2] * c * c * c, s[3] * (c * c) * (c * c)};
-  const double pw[5] = {0.0, s[4], s[5], s[6], s[7]};
-  double a1, a2, a4, w1, w2, w4;
-  newton(pa, s[8], a1, a2, a4);
-  newton(pw, s[8], w1, w2, w4);
-  double* o = rec + (size_t)ap * 8;
-  o[0] = a1; o[1] = a2; o[2] = a4; o[3] = w1; o[4] = w2; o[5] = w4; o[6] = s[8]; o[7] = 0.0;
+constexpr int kFinThreads = 128;
+
+__global__ void __launch_bounds__(kFinThreads) aperture_finish(const float* __restrict__ sums, int n_ap, int nsplit,
+                                                               double theta, double* __restrict__ rec,
+                                                               double* __restrict__ part) {
+  __shared__ double red[4][kFinThreads];
+  const int ap = blockIdx.x * kFinThreads + threadIdx.x;
+  double t[4] = {0, 0, 0, 0};
+  if (ap < n_ap) {
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long n = 0;
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const float4* q = reinterpret_cast<const float4*>(sums + ((long long)ap * nsplit + sp) * kSumFloats);
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = q[i];
+        s[2 * i] += (double)v.x + (double)v.y;
+        s[2 * i + 1] += (double)v.z + (double)v.w;
+      }
+      n += __float_as_int(q[4].x);
+    }
+    const double c = 1.0 / (4.0 * M_PI * theta * theta);  // a = b c
+    const double pa[5] = {0.0, s[0] * c, s[1] * c * c, s[2] * c * c * c, s[3] * (c * c) * (c * c)};
+    const double pw[5] = {0.0, s[4], s[5], s[6], s[7]};
+    const double nn = (double)n;
+    double a1, a2, a4, w1, w2, w4;
+    newton(pa, nn, a1, a2, a4);
+    newton(pw, nn, w1, w2, w4);
+    double* o = rec + (size_t)ap * 8;
+    o[0] = a1; o[1] = a2; o[2] = a4; o[3] = w1; o[4] = w2; o[5] = w4; o[6] = nn; o[7] = 0.0;
+    t[0] = a4; t[1] = w4; t[2] = a2; t[3] = w2;
+  }
+  for (int i = 0; i < 4; ++i) red[i][threadIdx.x] = t[i];
+  __syncthreads();
+  for (int st = kFinThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int i = 0; i < 4; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[(size_t)blockIdx.x * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 
 constexpr int kMomThreads = 256;
 
-__global__ void __launch_bounds__(kMomThreads) aperture_moments(const double* __restrict__ rec, int n_ap,
+__global__ void __launch_bounds__(kMomThreads) aperture_moments(const double* __restrict__ part, int nblk, int n_ap,
                                                                double theta, double* __restrict__ mom) {
   __shared__ double red[4][kMomThreads];
   double t[4] = {0, 0, 0, 0};
-  for (int a = threadIdx.x; a < n_ap; a += kMomThreads) {
-    const double* r = rec + (size_t)a * 8;
-    t[0] += r[2]; t[1] += r[5]; t[2] += r[1]; t[3] += r[4];
-  }
+  for (int b = threadIdx.x; b < nblk; b += kMomThreads)
+    for (int i = 0; i < 4; ++i) t[i] += part[(size_t)b * 4 + i];
   for (int i = 0; i < 4; ++i) red[i][threadIdx.x] = t[i];
   __syncthreads();
   for (int st = kMomThreads / 2; st > 0; st >>= 1) {
@@ -249,32 +300,49 @@ __global__ void __launch_bounds__(kMomThreads) aperture_moments(const double* __
 }  // namespace
 
 int map_direct_splits(int n_ap, int sm_count, double theta, double cell) {
-  // enough CTAs for a few waves of the GPU, never more splits than about one per 8 rows
+  // enough warps for several waves of the GPU, never more splits than about one per 4 rows
   const int rows = (int)std::min(1.0e6, 8.0 * theta / cell) + 2;
-  int ns = (8 * sm_count + n_ap - 1) / std::max(n_ap, 1);
-  ns = std::max(1, std::min(ns, std::max(1, rows / 8)));
-  while (ns > 1 && (long long)ns * n_ap > 2147483647LL) --ns;
+  int ns = (32 * sm_count + n_ap - 1) / std::max(n_ap, 1);
+  ns = std::max(1, std::min(ns, std::max(1, rows / 4)));
+  while (ns > 1 && (long long)ns * n_ap > (1LL << 34)) --ns;
   return ns;
 }
 
+size_t map_direct_scratch(int n_ap, int nsplit) {
+  const size_t nblk = (size_t)(n_ap + kFinThreads - 1) / kFinThreads;
+  return (size_t)n_ap * 16 + (size_t)n_ap * nsplit * kSumFloats * 4 + nblk * 32 + 256;
+}
+
 cudaError_t map_direct_radius(const SortedCat& cat, const double* centres, int n_ap, double theta,
-                              int nsplit, double* sums, double* rec, double* mom, cudaStream_t s) {
+                              int nsplit, void* scratch, double* rec, double* mom, cudaStream_t s) {
+  const int nblk = (n_ap + kFinThreads - 1) / kFinThreads;
+  int4* prep = (int4*)scratch;
+  float* sums = (float*)((char*)scratch + (size_t)n_ap * 16);
+  double* part = (double*)((char*)sums + (((size_t)n_ap * nsplit * kSumFloats * 4 + 255) / 256) * 256);
+  const long long n_items = (long long)n_ap * nsplit;
   if (n_ap > 0) {
     if (cat.n > 0) {
+      aperture_prep<<<(n_ap + 127) / 128, 128, 0, s>>>(centres, n_ap, cat.x0, cat.y0, cat.cell, 1.0 / cat.cell,
+                                                        cat.ncx, cat.ncy, 4.0 * theta, prep);
       ApArgs A;
       A.p4 = cat.p4; A.s4 = cat.s4; A.px = cat.px; A.py = cat.py; A.cell_start = cat.cell_start;
-      A.ncx = cat.ncx; A.ncy = cat.ncy; A.x0 = cat.x0; A.y0 = cat.y0; A.cell = cat.cell;
-      A.inv_cell = 1.0 / cat.cell; A.cellf = cat.cellf;
-      A.centres = centres; A.n_ap = n_ap; A.nsplit = nsplit; A.theta = theta; A.sums = sums;
-      aperture_sums<<<(unsigned)((long long)n_ap * nsplit), kApThreads, 0, s>>>(A);
+      A.ncx = cat.ncx; A.ncy = cat.ncy; A.cellf = cat.cellf;
+      A.rc = (float)(4.0 * theta / cat.cell);
+      A.invt = (float)(1.0 / theta);
+      A.centres = centres; A.prep = prep; A.nsplit = nsplit; A.n_items = n_items;
+      const double R = 4.0 * theta;
+      A.R2 = R * R;  // the oracle's (4 theta)^2, one rounding
+      A.sums = sums;
+      aperture_sums<<<(unsigned)((n_items + kApWarps - 1) / kApWarps), kApThreads, 0, s>>>(A);
+      g_launches += 2;
     } else {
-      cudaError_t e = cudaMemsetAsync(sums, 0, (size_t)n_ap * nsplit * 9 * sizeof(double), s);
+      cudaError_t e = cudaMemsetAsync(sums, 0, (size_t)n_items * kSumFloats * 4, s);
       if (e != cudaSuccess) return e;
     }
-    aperture_finish<<<(n_ap + 127) / 128, 128, 0, s>>>(sums, n_ap, nsplit, theta, rec);
-    g_launches += cat.n > 0 ? 2 : 1;
+    aperture_finish<<<nblk, kFinThreads, 0, s>>>(sums, n_ap, nsplit, theta, rec, part);
+    ++g_launches;
   }
-  aperture_moments<<<1, kMomThreads, 0, s>>>(rec, n_ap, theta, mom);
+  aperture_moments<<<1, kMomThreads, 0, s>>>(part, nblk, n_ap, theta, mom);
   ++g_launches;
   return cudaGetLastError();
 }

@@ -23,8 +23,9 @@ cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const 
                                const double* d_tb, const double* d_area, int nb, const double* d_ap,
                                double* d_m4, double* d_eb, double* d_disc, cudaStream_t s);
 int map_direct_splits(int n_ap, int sm_count, double theta, double cell);
+size_t map_direct_scratch(int n_ap, int nsplit);
 cudaError_t map_direct_radius(const SortedCat& cat, const double* centres, int n_ap, double theta,
-                              int nsplit, double* sums, double* rec, double* mom, cudaStream_t s);
+                              int nsplit, void* scratch, double* rec, double* mom, cudaStream_t s);
 }  // namespace ext4pcf
 
 namespace ext4pcf {
@@ -678,13 +679,13 @@ int ext4pcf_map_direct(ext4pcf_ctx* ctx, const double* positions, const double* 
   for (int t = 0; t < n_theta; ++t) {
     const int na = (int)(centre_offsets[t + 1] - centre_offsets[t]);
     splits[t] = map_direct_splits(na, ctx->sm_count, thetas[t], cell);
-    sums_need = std::max(sums_need, (size_t)na * splits[t] * 9 * 8);
+    sums_need = std::max(sums_need, map_direct_scratch(na, splits[t]));
   }
   ENSURE(ctx->ap_sums, sums_need);
   for (int t = 0; t < n_theta; ++t) {
     const int64_t c0 = centre_offsets[t];
     const int na = (int)(centre_offsets[t + 1] - c0);
-    CK(map_direct_radius(cat, d_cen + 2 * c0, na, thetas[t], splits[t], (double*)ctx->ap_sums.p, d_rec + 8 * c0,
+    CK(map_direct_radius(cat, d_cen + 2 * c0, na, thetas[t], splits[t], ctx->ap_sums.p, d_rec + 8 * c0,
                          d_mom + 8 * t, s));
   }
   if (host_rec && n_cen > 0)
