@@ -191,7 +191,7 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
                  &ctx->px, &ctx->py, &ctx->xr, &ctx->xi, &ctx->w, &ctx->p4, &ctx->s4, &ctx->bbox,
                  &ctx->centres, &ctx->flags, &ctx->rec, &ctx->xw, &ctx->corr, &ctx->counter, &ctx->ncen,
                  &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small, &ctx->tc_items,
-                 &ctx->tc_xb, &ctx->status};
+                 &ctx->tc_xb, &ctx->status, &ctx->ap_cen, &ctx->ap_sums, &ctx->io_rec, &ctx->io_mom};
   for (DBuf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
