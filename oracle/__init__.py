@@ -192,3 +192,6 @@ def xi_from_acc(xi_acc):
 # direct estimator of <M_ap^2> and <M_ap^4> (Sect. 5.2, Eq. MapDirectEstimator); numpy only
 from .map_direct import (aperture_record, crittenden_q, elementary_symmetric,  # noqa: E402
                          map_direct, moments_from_records, tangential_shear)
+
+# N-th order natural components and multipoles by brute force (App. F); numpy only
+from .nth_order import beta_matrix, bruteforce_multipoles  # noqa: E402
