@@ -200,6 +200,39 @@ EXT4PCF_API int ext4pcf_map_direct(ext4pcf_ctx* ctx, const double* positions, co
                                    int n_theta, const double* centres, const int64_t* centre_offsets,
                                    double* ap_records, double* moments);
 
+/* Natural components of the shear N-point function (paper App. F.1).  The 2^{N-1} rows of
+ * the sign matrix beta (beta[mu][l] = -1 where the l-th shear of Gamma_mu is complex
+ * conjugated, else +1), in the paper's order: p = 0, 1, ..., floor(N/2) conjugated shears,
+ * for each p the conjugated positions in lexicographic order, and for even N only the first
+ * half of the p = N/2 rows (the others are their complex conjugates).  At N = 4 the rows are
+ * the components Gamma_0 .. Gamma_7 of ext4pcf_measure.
+ *   order  N, 2 .. 16
+ *   beta   host, int [2^{N-1}][N], or NULL to query the count
+ *   cap    ints available in beta
+ * Host only (no device, no context).  Returns 2^{N-1}, or EXT4PCF_E_INVALID_ARG. */
+EXT4PCF_API int ext4pcf_nth_order_components(int order, int* beta, int cap);
+
+/* Multipole factorisation of component mu in the x-projection (paper App. F.2):
+ *   Upsilon_{mu,n}(Theta_1 .. Theta_{N-1}) = sign * sum_i t_i * prod_{l=1}^{N-1} F_l(theta_i, Theta_l)
+ * with n = (n_2 .. n_{N-1}); t_i = w_i gamma_c,i (centre code 0), w_i gamma_c,i^* (1) or w_i (2);
+ * F_l = G_m, conj(G_m), or W_m for the normalisation (mu = -1), where
+ * m = sum_k a_{l,k} n_k + b_l and G_m(theta_i, Theta) = sum_j w_j gamma_c,j e^{i m phi_ij}.
+ *   order  N, 2 .. 16;  mu  0 .. 2^{N-1}-1, or -1 for the normalisation
+ *   table  host, int, or NULL to query the size 2 + (N-1)(N+1):
+ *          [0] sign (-1)^N (+1 for the normalisation), [1] centre code, then for
+ *          l = 1 .. N-1 a row of N+1 ints: array (0 G, 1 W), conj (0/1), a_{l,2} .. a_{l,N-1}, b_l
+ *   cap    ints available in table
+ * Host only.  Returns the size, or EXT4PCF_E_INVALID_ARG. */
+EXT4PCF_API int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap);
+
+/* The factor tables compiled into the 4PCF contraction kernels, for inspection, in the
+ * layout of ext4pcf_nth_order_factors at order 4 (row mu = 0..7, row 8 the normalisation;
+ * 17 ints per row).
+ *   which  0: CUDA-core contraction (FP64 / FP32 forms), 1: tensor-core contraction
+ *   table  host, int [9][17], or NULL to query the size;  cap  ints available
+ * Host only.  Returns 153, or EXT4PCF_E_INVALID_ARG. */
+EXT4PCF_API int ext4pcf_contraction_tables(int which, int* table, int cap);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 EXT4PCF_API const char* ext4pcf_last_error(const ext4pcf_ctx* ctx);
 

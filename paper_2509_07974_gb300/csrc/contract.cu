@@ -21,17 +21,21 @@ struct Comp {
 };
 
 // Upsilon_0..7 (x-projection) and N: xt * A[s] * B[n2] * C[n3].
-__constant__ Comp kComp[9] = {
-    {0, {kG, 1, -3, 0}, {kG, -1, -2, 0}, {kG, -1, -3, 0}},
-    {1, {kG, 1, -1, 0}, {kG, -1, -2, 0}, {kG, -1, -1, 0}},
-    {0, {kG, -1, -1, 1}, {kG, -1, -2, 0}, {kG, -1, -3, 0}},
-    {0, {kG, 1, -3, 0}, {kG, 1, -2, 1}, {kG, -1, -3, 0}},
-    {0, {kG, 1, -3, 0}, {kG, -1, -2, 0}, {kG, 1, -1, 1}},
-    {1, {kG, -1, -3, 1}, {kG, -1, -2, 0}, {kG, -1, -1, 0}},
-    {1, {kG, 1, -1, 0}, {kG, 1, -2, 1}, {kG, -1, -1, 0}},
-    {1, {kG, 1, -1, 0}, {kG, -1, -2, 0}, {kG, 1, -3, 1}},
-    {2, {kW, 1, 0, 0}, {kW, -1, 0, 0}, {kW, -1, 0, 0}},
-};
+#define EXT4PCF_COMP_TABLE                                                          \
+  {                                                                               \
+    {0, {kG, 1, -3, 0}, {kG, -1, -2, 0}, {kG, -1, -3, 0}},                        \
+    {1, {kG, 1, -1, 0}, {kG, -1, -2, 0}, {kG, -1, -1, 0}},                        \
+    {0, {kG, -1, -1, 1}, {kG, -1, -2, 0}, {kG, -1, -3, 0}},                       \
+    {0, {kG, 1, -3, 0}, {kG, 1, -2, 1}, {kG, -1, -3, 0}},                         \
+    {0, {kG, 1, -3, 0}, {kG, -1, -2, 0}, {kG, 1, -1, 1}},                         \
+    {1, {kG, -1, -3, 1}, {kG, -1, -2, 0}, {kG, -1, -1, 0}},                       \
+    {1, {kG, 1, -1, 0}, {kG, 1, -2, 1}, {kG, -1, -1, 0}},                         \
+    {1, {kG, 1, -1, 0}, {kG, -1, -2, 0}, {kG, 1, -3, 1}},                         \
+    {2, {kW, 1, 0, 0}, {kW, -1, 0, 0}, {kW, -1, 0, 0}},                           \
+  }
+__constant__ Comp kComp[9] = EXT4PCF_COMP_TABLE;
+// host copy of the same initializer (inspection through ext4pcf_contraction_tables)
+const Comp kCompHost[9] = EXT4PCF_COMP_TABLE;
 
 // Double-counting terms: xt * P(merged slots; bin Theta_a) * O(remaining slot; Theta_b).
 // kind 0: Theta1 = Theta2 (index n3), kind 1: Theta1 = Theta3 (index n2),
@@ -405,4 +409,26 @@ template cudaError_t contract_wave<double>(const Layout&, const double2*, const 
 template cudaError_t corrections_wave<float>(const Layout&, const float2*, const float2*, int, double*, double*, cudaStream_t);
 template cudaError_t corrections_wave<double>(const Layout&, const double2*, const double2*, int, double*, double*, cudaStream_t);
 
+// kComp in the layout of ext4pcf_nth_order_factors at order 4: sign, centre code, then per
+// bin (array, conj, coefficient of n2, coefficient of n3, constant); A reads s = n2 + n3.
+int contraction_table_cc(int* out) {
+  for (int mu = 0; mu < 9; ++mu) {
+    const Comp& c = kCompHost[mu];
+    int* t = out + mu * 17;
+    t[0] = 1;
+    t[1] = c.xconj;
+    const Factor f[3] = {c.A, c.B, c.C};
+    for (int l = 0; l < 3; ++l) {
+      int* r = t + 2 + 5 * l;
+      r[0] = f[l].arr == kW ? 1 : 0;
+      r[1] = f[l].conj;
+      r[2] = (l == 0 || l == 1) ? f[l].sgn : 0;
+      r[3] = (l == 0 || l == 2) ? f[l].sgn : 0;
+      r[4] = f[l].off;
+    }
+  }
+  return 9 * 17;
+}
+
 }  // namespace ext4pcf
+

@@ -55,15 +55,19 @@ struct KRType {
 };
 
 // Khatri-Rao row types and the components that use them
-__constant__ KRType kKR[7] = {
-    {0, {0, -1, -2, 0}, {0, -1, -3, 0}, 2, {0, 2}, {{0, 1, -3, 0}, {0, -1, -1, 1}}},
-    {0, {0, 1, -2, 1}, {0, -1, -3, 0}, 1, {3, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},
-    {0, {0, -1, -2, 0}, {0, 1, -1, 1}, 1, {4, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},
-    {1, {0, -1, -2, 0}, {0, -1, -1, 0}, 2, {1, 5}, {{0, 1, -1, 0}, {0, -1, -3, 1}}},
-    {1, {0, 1, -2, 1}, {0, -1, -1, 0}, 1, {6, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},
-    {1, {0, -1, -2, 0}, {0, 1, -3, 1}, 1, {7, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},
-    {2, {1, -1, 0, 0}, {1, -1, 0, 0}, 1, {8, 0}, {{1, 1, 0, 0}, {0, 0, 0, 0}}},
-};
+#define EXT4PCF_KR_TABLE                                                                                  \
+  {                                                                                                     \
+    {0, {0, -1, -2, 0}, {0, -1, -3, 0}, 2, {0, 2}, {{0, 1, -3, 0}, {0, -1, -1, 1}}},                    \
+    {0, {0, 1, -2, 1}, {0, -1, -3, 0}, 1, {3, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},                       \
+    {0, {0, -1, -2, 0}, {0, 1, -1, 1}, 1, {4, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},                       \
+    {1, {0, -1, -2, 0}, {0, -1, -1, 0}, 2, {1, 5}, {{0, 1, -1, 0}, {0, -1, -3, 1}}},                    \
+    {1, {0, 1, -2, 1}, {0, -1, -1, 0}, 1, {6, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},                       \
+    {1, {0, -1, -2, 0}, {0, 1, -3, 1}, 1, {7, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},                       \
+    {2, {1, -1, 0, 0}, {1, -1, 0, 0}, 1, {8, 0}, {{1, 1, 0, 0}, {0, 0, 0, 0}}},                         \
+  }
+__constant__ KRType kKR[7] = EXT4PCF_KR_TABLE;
+// host copy of the same initializer (inspection through ext4pcf_contraction_tables)
+const KRType kKRHost[7] = EXT4PCF_KR_TABLE;
 constexpr int kKRTypes = 7;
 
 struct TcArgs {
@@ -618,4 +622,30 @@ cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* x
   return e;
 }
 
+// kKR expanded per component, in the layout of ext4pcf_nth_order_factors at order 4 (row mu;
+// row 8 the normalisation): sign, centre code, then per bin (array, conj, coefficient of n2,
+// coefficient of n3, constant); the column factor A reads s = n2 + n3.
+int contraction_table_tc(int* out) {
+  for (int i = 0; i < 9 * 17; ++i) out[i] = 0;
+  for (int t = 0; t < kKRTypes; ++t) {
+    const KRType& k = kKRHost[t];
+    for (int j = 0; j < k.nmu; ++j) {
+      int* r = out + k.mu[j] * 17;
+      r[0] = 1;
+      r[1] = k.xconj;
+      const KF f[3] = {k.A[j], k.B, k.C};
+      for (int l = 0; l < 3; ++l) {
+        int* q = r + 2 + 5 * l;
+        q[0] = f[l].arr;
+        q[1] = f[l].conj;
+        q[2] = (l == 0 || l == 1) ? f[l].sgn : 0;
+        q[3] = (l == 0 || l == 2) ? f[l].sgn : 0;
+        q[4] = f[l].off;
+      }
+    }
+  }
+  return 9 * 17;
+}
+
 }  // namespace ext4pcf
+

@@ -2,7 +2,8 @@
 
 The functions ``ext4pcf_create``, ``ext4pcf_destroy``, ``ext4pcf_measure``,
 ``ext4pcf_to_real_space``, ``ext4pcf_to_map4``, ``ext4pcf_to_real_space_noalloc``,
-``ext4pcf_map_direct`` and ``ext4pcf_last_error`` mirror the C ABI one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
+``ext4pcf_map_direct``, ``ext4pcf_nth_order_components``, ``ext4pcf_nth_order_factors``,
+``ext4pcf_contraction_tables`` and ``ext4pcf_last_error`` mirror the C ABI one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
 integer addresses or None.  ``Estimator`` wraps them for torch users: it allocates outputs
 and passes the current CUDA stream.  Every computation happens in the CUDA library; there
 is no fallback, and loading fails loudly if the library has not been built.
@@ -68,6 +69,11 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_to_real_space_noalloc.argtypes = [P, I, I, I, P, P, P]
     lib.ext4pcf_to_real_space_noalloc.restype = I
     lib.ext4pcf_map_direct.argtypes = [P, P, P, P, I64, P, I, P, P, P, P]
+    lib.ext4pcf_nth_order_components.argtypes = [I, P, I]
+    lib.ext4pcf_nth_order_factors.argtypes = [I, I, P, I]
+    lib.ext4pcf_contraction_tables.argtypes = [I, P, I]
+    for f in ("ext4pcf_nth_order_components", "ext4pcf_nth_order_factors", "ext4pcf_contraction_tables"):
+        getattr(lib, f).restype = I
     lib.ext4pcf_last_error.argtypes = [P]
     lib.ext4pcf_last_error.restype = ctypes.c_char_p
     for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_to_real_space",
@@ -154,6 +160,43 @@ def ext4pcf_map_direct(ctx, positions, shears, weights, n_gal, thetas, n_theta, 
                                    _addr(thetas), int(n_theta), _addr(centres), _addr(centre_offsets),
                                    _addr(ap_records), _addr(moments))
     return _check(ctx, rc)
+
+
+def _host_table(rc):
+    if rc < 0:
+        raise Ext4pcfError(rc, "invalid argument")
+    return rc
+
+
+def ext4pcf_nth_order_components(order):
+    """Sign matrix beta of the natural components of order N (host only): int32 [2^{N-1}][N]."""
+    import numpy as np
+    lib = load()
+    n = _host_table(lib.ext4pcf_nth_order_components(int(order), None, 0))
+    beta = np.zeros((n, int(order)), dtype=np.int32)
+    _host_table(lib.ext4pcf_nth_order_components(int(order), beta.ctypes.data, beta.size))
+    return beta
+
+
+def ext4pcf_nth_order_factors(order, mu):
+    """Factor table of component mu (-1: normalisation) at order N (host only): int32 array
+    [sign, centre code, then per bin (array, conj, a_2 .. a_{N-1}, b)]."""
+    import numpy as np
+    lib = load()
+    n = _host_table(lib.ext4pcf_nth_order_factors(int(order), int(mu), None, 0))
+    t = np.zeros(n, dtype=np.int32)
+    _host_table(lib.ext4pcf_nth_order_factors(int(order), int(mu), t.ctypes.data, t.size))
+    return t
+
+
+def ext4pcf_contraction_tables(which):
+    """The 4PCF contraction kernels' own factor tables (0 CUDA-core, 1 tensor-core), int32 [9][17]."""
+    import numpy as np
+    lib = load()
+    n = _host_table(lib.ext4pcf_contraction_tables(int(which), None, 0))
+    t = np.zeros(n, dtype=np.int32)
+    _host_table(lib.ext4pcf_contraction_tables(int(which), t.ctypes.data, t.size))
+    return t.reshape(9, 17)
 
 
 def aperture_lattice(field, theta, spacing):
