@@ -191,18 +191,9 @@ def test_global_shear_phase(oracle):
 # --------------------------------------------------------------------------------------
 # Table tab:4PCFSymm: permutations of the radial bins
 # --------------------------------------------------------------------------------------
-# columns: (Theta2,Theta3,Theta1), (Theta3,Theta1,Theta2), (Theta1,Theta3,Theta2),
-#          (Theta2,Theta1,Theta3), (Theta3,Theta2,Theta1)
-_BIN_PERM = [(1, 2, 0), (2, 0, 1), (0, 2, 1), (1, 0, 2), (2, 1, 0)]
-_MU_MAP = {0: [0, 0, 0, 0, 0], 1: [1, 1, 1, 1, 1], 2: [4, 3, 2, 3, 4], 3: [2, 4, 4, 2, 3],
-           4: [3, 2, 3, 4, 2], 5: [7, 6, 5, 6, 7], 6: [5, 7, 7, 5, 6], 7: [6, 5, 6, 7, 5],
-           8: [8, 8, 8, 8, 8]}
-
-
-def _n_map(mu, col, n2, n3):
-    s = n2 + n3
-    o = {0: 1, 2: 1, 3: 1, 4: 1, 1: -1, 5: -1, 6: -1, 7: -1, 8: 0}[mu]
-    return [(n3 + o, -s), (-s + o, n2 - o), (n3 + o, n2 - o), (-s + o, n3), (n2, -s)][col]
+# the table as typed into the oracle (bin permutation per column, mu' per (mu, column) and the
+# multipole map); pinned here against the estimator itself
+from oracle.symmetry import BIN_PERM as _BIN_PERM, MU_MAP as _MU_MAP, n_map as _n_map  # noqa: E402
 
 
 def test_symmetry_table(oracle):
