@@ -288,7 +288,7 @@ def direct_estimator(est, tp, ts, tw, pos, sh, w, side, dev, stream, flush, args
     m = mom.cpu().numpy()
     out = {"workload": cfg["name"], "radii": len(radii), "apertures": int(offs[-1]),
            "pairs_per_pass": pairs, "value": pairs / (ms / 1e3), "unit": "aperture-galaxy pairs/s",
-           "ms_per_pass": ms, "dtype": "f32 terms, f64 power sums",
+           "ms_per_pass": ms, "dtype": "f32 terms, compensated f32 power sums, f64 per aperture",
            "l2": "flushed between passes (256 MB write)",
            "e2e": {"value": pairs / e2e, "unit": "aperture-galaxy pairs/s",
                    "h2d_bytes_per_step": int(hp.numel() * 8 + hs.numel() * 8 + hw.numel() * 8 + hc.numel() * 8),

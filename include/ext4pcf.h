@@ -175,7 +175,8 @@ EXT4PCF_API int ext4pcf_to_real_space_noalloc(const double* upsilon, int n_bins,
  * part of Eq. gammatx_def about the centre), the distinct quadruplet sums over the galaxies
  * inside the cut are 4! e_4(a) (numerator) and 4! e_4(w) (denominator), e_k the elementary
  * symmetric polynomials, computed from the power sums of a and w (Newton's identities):
- * linear in the galaxies.  Per-galaxy terms are FP32, power sums FP64.
+ * linear in the galaxies.  Per-galaxy terms are FP32; the power sums are kept as FP32 (hi, lo)
+ * pairs (error-free two-sum) and combined per aperture in FP64.
  *   positions, shears, weights  device or host, as for ext4pcf_measure (one catalogue)
  *   n_gal           0 .. 2^31-1
  *   thetas          host, double [n_theta], finite and > 0 (1 <= n_theta <= 4096)
