@@ -47,11 +47,12 @@ def _projected(gc, zeta2, beta):
     return g if beta > 0 else np.conj(g)
 
 
-def bruteforce_multipoles(order, pos, shear, w, edges, nmax):
+def bruteforce_multipoles(order, pos, shear, w, edges, nmax, distinct=False):
     """Upsilon_{mu, n}(Theta_1..Theta_{N-1}) for every natural component (rows 0 .. 2^{N-1}-1)
-    and the normalisation (last row), all index tuples (no exclusion of coinciding
-    neighbours).  Shape [2^{N-1} + 1] + [2 nmax + 1] * (N - 2) + [nb] * (N - 1), axes n_l + nmax
-    for l = 2..N-1, complex128."""
+    and the normalisation (last row), over all neighbour tuples, or (distinct=True) only over
+    tuples of pairwise different galaxies (the centre always differs from its neighbours).
+    Shape [2^{N-1} + 1] + [2 nmax + 1] * (N - 2) + [nb] * (N - 1), axes n_l + nmax for
+    l = 2..N-1, complex128."""
     pos = np.asarray(pos, dtype=np.float64)
     gc_all = np.asarray(shear, dtype=np.float64) @ np.array([1.0, 1j])
     w = np.asarray(w, dtype=np.float64)
@@ -77,6 +78,10 @@ def bruteforce_multipoles(order, pos, shear, w, edges, nmax):
             grids = np.meshgrid(*sets, indexing="ij")   # neighbour index per tuple slot
             ph = [phi[g] for g in grids]                  # phi_1 .. phi_{N-1}
             wt = w[i] * np.prod([w[g] for g in grids], axis=0)
+            if distinct:
+                for a in range(k):
+                    for b in range(a + 1, k):
+                        wt = np.where(grids[a] == grids[b], 0.0, wt)
             # Fourier kernel exp(-i sum_{l=2}^{N-1} n_l (phi_l - phi_1)) for every n
             if order > 2:
                 rel = np.stack([ph[l] - ph[0] for l in range(1, k)], axis=0)   # [N-2][...]

@@ -50,6 +50,17 @@ def test_fourth_order_matches_the_pinned_quadruplet_brute_force():
     np.testing.assert_allclose(g, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
 
 
+def test_distinct_tuples_match_the_pinned_quadruplet_brute_force():
+    """Excluding coinciding neighbours gives the distinct-quadruplet estimator."""
+    pos, sh, w = _catalogue(40, 6.0, 7)
+    edges = np.array([0.8, 1.6, 3.0])
+    g = oracle.bruteforce_multipoles(4, pos, sh, w, edges, 2, distinct=True)
+    ref = oracle.bruteforce(pos, sh, w, edges, 2, distinct=True)
+    np.testing.assert_allclose(g, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    full = oracle.bruteforce_multipoles(4, pos, sh, w, edges, 2)
+    assert np.abs(full - g).max() > 1e-3 * np.abs(ref).max()  # coinciding neighbours matter
+
+
 def test_second_order_is_the_xi_accumulators():
     """N = 2: Upsilon_0 = sum_i x_i G_-4, Upsilon_1 = sum_i x_i^* G_0 and the normalisation
     sum_i w_i W_0, the accumulators of xi_- and xi_+."""
