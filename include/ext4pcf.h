@@ -226,6 +226,25 @@ EXT4PCF_API int ext4pcf_nth_order_components(int order, int* beta, int cap);
  * Host only.  Returns the size, or EXT4PCF_E_INVALID_ARG. */
 EXT4PCF_API int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap);
 
+/* Multipoles of the shear 3PCF, the order-3 case of the N-th order estimator (paper App. F),
+ * FP64.  The neighbour multipoles are gathered as for ext4pcf_measure; the contraction reads
+ * the tables of ext4pcf_nth_order_factors(3, mu), and when Theta1 = Theta2 it subtracts the
+ * term in which both neighbours are the same galaxy, so that only triplets of distinct
+ * galaxies remain:
+ *   Upsilon_{mu,n}(Theta1, Theta2) = sign sum_{i, j != k} t_i F1_j F2_k  (mu = 0..3, natural
+ *   components Gamma_0..3 in the order of ext4pcf_nth_order_components(3)), and the
+ *   normalisation N_n = sum_{i, j != k} w_i w_j w_k e^{i n (phi_ij - phi_ik)}.
+ *   positions, shears, weights  device, as for ext4pcf_measure (one catalogue)
+ *   radial_bins  host [n_bins+1] as for ext4pcf_measure;  n_bins 1..32;  n_max 0..40
+ *   upsilon3     device, double [5][2 n_max + 1][n_bins][n_bins][2] (index 4 the
+ *                normalisation; axes n + n_max, Theta1, Theta2), accumulated into
+ * Stream-ordered after one synchronisation (the catalogue's bounding box).  Waves hold
+ * ext4pcf_config.wave_centres centres (0: 4096).  Returns EXT4PCF_OK, EXT4PCF_E_INVALID_ARG
+ * (including host pointers), EXT4PCF_E_OOM or EXT4PCF_E_CUDA. */
+EXT4PCF_API int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                                 const double* weights, int64_t n_gal, const double* radial_bins,
+                                 int n_bins, int n_max, double* upsilon3);
+
 /* The factor tables compiled into the 4PCF contraction kernels, for inspection, in the
  * layout of ext4pcf_nth_order_factors at order 4 (row mu = 0..7, row 8 the normalisation;
  * 17 ints per row).

@@ -24,6 +24,9 @@ cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const 
                                double* d_m4, double* d_eb, double* d_disc, cudaStream_t s);
 int map_direct_splits(int n_ap, int sm_count, double theta, double cell);
 size_t map_direct_scratch(int n_ap, int nsplit);
+bool contract3_supported(int N);
+cudaError_t contract3_wave(const Layout& L, const double2* rec, const double2* xw, int T, double* ups3,
+                           cudaStream_t s);
 cudaError_t map_direct_radius(const SortedCat& cat, const double* centres, int n_ap, double theta,
                               int nsplit, void* scratch, double* rec, double* mom, cudaStream_t s);
 }  // namespace ext4pcf
@@ -567,6 +570,87 @@ int ext4pcf_to_map4(ext4pcf_ctx* ctx, const double* upsilon, const double* radia
     map4_eb[k] += res[16 * n_ap + k];
     if (map4_disc && xi_acc) map4_disc[k] += res[32 * n_ap + k];
   }
+  return EXT4PCF_OK;
+}
+
+int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* shears, const double* weights,
+                     int64_t n_gal, const double* radial_bins, int n_bins, int n_max, double* upsilon3) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  ctx->err.clear();
+  if (n_gal < 0 || n_gal > (int64_t)2000000000) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_gal out of range");
+  if (n_bins < 1 || n_bins > 32) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_bins must be in 1..32");
+  if (n_max < 0 || n_max > 40) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_max must be in 0..40");
+  if (!radial_bins || !upsilon3) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null radial_bins or upsilon3");
+  if (n_gal > 0 && (!positions || !shears || !weights)) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null input");
+  if (!(radial_bins[0] > 0.0) || !std::isfinite(radial_bins[n_bins]))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "radial_bins[0] must be > 0 and finite");
+  for (int b = 0; b < n_bins; ++b)
+    if (!(radial_bins[b + 1] > radial_bins[b])) return fail(ctx, EXT4PCF_E_INVALID_ARG, "radial_bins must increase");
+  if (!is_device_ptr(upsilon3) ||
+      (n_gal > 0 && (!is_device_ptr(positions) || !is_device_ptr(shears) || !is_device_ptr(weights))))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "ext4pcf_measure3 takes device pointers");
+  if (!contract3_supported(n_max)) return fail(ctx, EXT4PCF_E_UNSUPPORTED, "order-3 tables outside the record");
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (n_gal == 0) return EXT4PCF_OK;
+  cudaStream_t s = ctx->stream;
+  const int nk = (int)n_gal;
+  const size_t n = (size_t)n_gal;
+  const Layout L = Layout::make(n_max, n_bins);
+  Bins bins;
+  bins.nb = n_bins;
+  for (int b = 0; b <= n_bins; ++b) {
+    bins.e2[b] = radial_bins[b] * radial_bins[b];
+    bins.e2f[b] = (float)bins.e2[b];
+  }
+  bins.rmax = radial_bins[n_bins];
+  // ---- grid (FP64 sorted catalogue)
+  ENSURE(ctx->counter, 16);
+  CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
+  ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
+  CK(grid_bbox(positions, nk, (double*)ctx->bbox.p, s));
+  double bb[4];
+  CK(cudaMemcpyAsync(bb, ctx->bbox.p, 32, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!std::isfinite(bb[0]) || !std::isfinite(bb[1]) || !std::isfinite(bb[2]) || !std::isfinite(bb[3]))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "non-finite positions");
+  const double extent = std::fmax(bb[2] - bb[0], bb[3] - bb[1]);
+  const double cell = choose_cell(bins.rmax, extent);
+  const int ncx = (int)std::floor((bb[2] - bb[0]) / cell) + 1;
+  const int ncy = (int)std::floor((bb[3] - bb[1]) / cell) + 1;
+  const size_t ncells = (size_t)ncx * ncy;
+  const int ntiles = (nk + 2047) / 2048;
+  ENSURE(ctx->keys, n * 4); ENSURE(ctx->keys_alt, n * 4);
+  ENSURE(ctx->perm, n * 4); ENSURE(ctx->perm_alt, n * 4);
+  ENSURE(ctx->cell_start, (ncells + 1) * 4);
+  ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
+  ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
+  ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
+  GridBuffers gb;
+  gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+  gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+  gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ncells + 1;
+  gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+  gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
+  gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
+  gb.p4 = nullptr; gb.s4 = nullptr; gb.bbox = (double*)ctx->bbox.p;
+  SortedCat cat;
+  CK(grid_sort(positions, shears, weights, nk, bb[0], bb[1], cell, ncx, ncy, false, gb, cat, s));
+  // ---- every galaxy a centre; waves of FP64 records, contracted with the order-3 tables
+  ENSURE(ctx->centres, n * 4);
+  iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
+  ++g_launches;
+  CK(cudaGetLastError());
+  const int T = std::min(ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres : 4096, nk);
+  ENSURE(ctx->rec, (size_t)T * L.rec * sizeof(double2));
+  ENSURE(ctx->xw, (size_t)T * 2 * sizeof(double2));
+  for (int w0 = 0; w0 < nk; w0 += T) {
+    const int Tw = std::min(T, nk - w0);
+    const int* cl = (const int*)ctx->centres.p + w0;
+    CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+                           (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+    CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3, s));
+  }
+  CK(cudaGetLastError());
   return EXT4PCF_OK;
 }
 

@@ -2,7 +2,7 @@
 
 The functions ``ext4pcf_create``, ``ext4pcf_destroy``, ``ext4pcf_measure``,
 ``ext4pcf_to_real_space``, ``ext4pcf_to_map4``, ``ext4pcf_to_real_space_noalloc``,
-``ext4pcf_map_direct``, ``ext4pcf_nth_order_components``, ``ext4pcf_nth_order_factors``,
+``ext4pcf_map_direct``, ``ext4pcf_measure3``, ``ext4pcf_nth_order_components``, ``ext4pcf_nth_order_factors``,
 ``ext4pcf_contraction_tables`` and ``ext4pcf_last_error`` mirror the C ABI one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
 integer addresses or None.  ``Estimator`` wraps them for torch users: it allocates outputs
 and passes the current CUDA stream.  Every computation happens in the CUDA library; there
@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_to_real_space_noalloc.argtypes = [P, I, I, I, P, P, P]
     lib.ext4pcf_to_real_space_noalloc.restype = I
     lib.ext4pcf_map_direct.argtypes = [P, P, P, P, I64, P, I, P, P, P, P]
+    lib.ext4pcf_measure3.argtypes = [P, P, P, P, I64, P, I, I, P]
+    lib.ext4pcf_measure3.restype = I
     lib.ext4pcf_nth_order_components.argtypes = [I, P, I]
     lib.ext4pcf_nth_order_factors.argtypes = [I, I, P, I]
     lib.ext4pcf_contraction_tables.argtypes = [I, P, I]
@@ -159,6 +161,12 @@ def ext4pcf_map_direct(ctx, positions, shears, weights, n_gal, thetas, n_theta, 
     rc = load().ext4pcf_map_direct(ctx, _addr(positions), _addr(shears), _addr(weights), int(n_gal),
                                    _addr(thetas), int(n_theta), _addr(centres), _addr(centre_offsets),
                                    _addr(ap_records), _addr(moments))
+    return _check(ctx, rc)
+
+
+def ext4pcf_measure3(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, upsilon3) -> int:
+    rc = load().ext4pcf_measure3(ctx, _addr(positions), _addr(shears), _addr(weights), int(n_gal),
+                                 _addr(radial_bins), int(n_bins), int(n_max), _addr(upsilon3))
     return _check(ctx, rc)
 
 
