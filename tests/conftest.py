@@ -18,3 +18,8 @@ def oracle():
     import oracle as o
     o.build()
     return o
+
+# tests/ holds helper modules (metric.py) next to the test files
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
