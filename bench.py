@@ -36,7 +36,6 @@ N_SM = 152
 FP32_LANES_PER_SM = 128
 N_PHI = 129
 AP_RADII = np.geomspace(1.0, 32.0, 24)
-TRAFFIC_PER_LAUNCH = {"gather": 0.212e9, "contraction": 1.344e9}
 METRIC = "galaxy pairs/s + Upsilon contraction TFLOP/s; mixed vs FP64 form at stated rel err"
 
 
@@ -55,6 +54,23 @@ def peaks():
     return d
 
 
+def measured_traffic(kernel):
+    """DRAM bytes (read + write) per launch of a kernel from the committed ncu summaries under
+    profiles/: a line 'traffic <kernel> <bytes per launch> <source file> <sha256 prefix>'.  The
+    figure is used only while the kernel's source file still has that hash (a changed kernel
+    needs a new capture); otherwise None."""
+    import glob
+    import hashlib
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            f = line.split()
+            if len(f) == 5 and f[0] == "traffic" and f[1] == kernel:
+                src = os.path.join(ROOT, "paper_2509_07974_gb300", "csrc", f[3])
+                if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == f[4]:
+                    return float(f[2])
+    return None
+
+
 def gather_flop_per_pair(nmax):
     """Algorithmic FP32 work of one (centre, neighbour) pair in the gather: complex
     accumulations x u^n (4N+3 values) and x^2 u^n (4N+5), real-weighted w u^m (2N+1),
@@ -66,6 +82,17 @@ def gather_flop_per_pair(nmax):
 def contraction_flop(n_centres, nmax, nb):
     """One complex multiply-add per output element per centre: 8 * centres * 9 (2N+1)^2 nb^3."""
     return 8.0 * n_centres * 9 * (2 * nmax + 1) ** 2 * nb ** 3
+
+
+def reduced_contraction_flop(n_centres, nmax, nb):
+    """The complex multiply-adds the tensor-core contraction computes under the exchange of
+    Theta2 and Theta3 (Table tab:4PCFSymm): bin pairs Theta2 <= Theta3 only, and for the eight
+    components with offset o = +-1 one more n2 per s (the multipoles the map reaches), i.e.
+    (2N+1)^2 + 4N+1 multipole pairs instead of (2N+1)^2; the normalisation keeps (2N+1)^2."""
+    pairs = nb * (nb + 1) // 2
+    n_sq = (2 * nmax + 1) ** 2
+    per_centre = 8 * (n_sq + 4 * nmax + 1) * pairs * nb + n_sq * pairs * nb
+    return 8.0 * n_centres * per_centre
 
 
 class ClockSampler:
@@ -420,9 +447,12 @@ def run_ours(args):
     g_ms = bd["ms_gather"] / waves
     g_ach = flop_pair * pairs / waves / (g_ms / 1e3) / 1e12
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    c_flop = contraction_flop(bd["centres"], nmax, nb)
+    tc_form = args.precision in ("tf32", "3xtf32", "bf16x3")
+    c_flop_full = contraction_flop(bd["centres"], nmax, nb)
+    c_flop = reduced_contraction_flop(bd["centres"], nmax, nb) if tc_form else c_flop_full
     c_ms = bd["ms_contract"] / waves
     contraction_tflops = c_flop / (bd["ms_contract"] / 1e3) / 1e12 if bd["ms_contract"] > 0 else None
+    passes = {"3xtf32": 3, "bf16x3": 3, "tf32": 1}.get(args.precision, 1)
     tf32_peak = pk.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
     roof_g = {"bound": "alu", "kernel": "gather", "achieved": g_ach, "peak": fp32_peak, "unit": "TFLOP/s",
               "frac": g_ach / fp32_peak, "traffic": None, "ms_per_launch": g_ms,
@@ -432,15 +462,21 @@ def run_ours(args):
     roof_c = {"bound": "tensor", "kernel": "contraction", "achieved": contraction_tflops, "peak": tf32_peak,
               "unit": "TFLOP/s", "frac": (contraction_tflops or 0.0) / tf32_peak, "traffic": None,
               "ms_per_launch": c_ms,
-              "peak_note": "tf32 dense: measured sustained bf16 (%s TFLOP/s, %s) x 1.1/2.25"
-                           % (pk.get("bf16_tflops_sustained"), pk.get("source")),
-              "algorithmic_flop_per_centre": 8 * 9 * (2 * nmax + 1) ** 2 * nb ** 3}
-    # DRAM bytes (read + write) of one full-size launch, from the ncu capture summarised in
-    # profiles/gather_contract_wave_grf2e6.md (8192 centres of this workload, 3xTF32);
-    # null for other configurations
+              "frac_issued": (contraction_tflops or 0.0) * passes / tf32_peak,
+              "passes": passes,
+              "peak_note": "tf32 dense: measured sustained bf16 (%s TFLOP/s, %s) x the nominal ratio 1.1/2.25 "
+                           "(not a measured tf32 rate)" % (pk.get("bf16_tflops_sustained"), pk.get("source")),
+              "algorithmic_flop_per_centre": c_flop / max(1, bd["centres"]),
+              "algorithmic_note": ("complex multiply-adds of the symmetry-reduced contraction (bin pairs "
+                                   "Theta2 <= Theta3); all ordered triples would be %.4g FLOP per centre, "
+                                   "%.3g TFLOP/s equivalent" % (c_flop_full / max(1, bd["centres"]),
+                                   c_flop_full / (bd["ms_contract"] / 1e3) / 1e12 if bd["ms_contract"] > 0 else 0.0))
+                                  if tc_form else "complex multiply-adds of all ordered bin triples"}
+    # DRAM bytes (read + write) of one full-size launch of the default configuration, from the
+    # committed ncu summaries (null when the kernel source changed since the capture)
     if args.precision == "3xtf32" and args.n_gal is None and args.centres is None:
-        roof_g["traffic"] = TRAFFIC_PER_LAUNCH["gather"]
-        roof_c["traffic"] = TRAFFIC_PER_LAUNCH["contraction"]
+        roof_g["traffic"] = measured_traffic("gather_kernel")
+        roof_c["traffic"] = measured_traffic("contract_tc_kernel")
         roof_g["traffic_unit"] = roof_c["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
     roof_main, roof_other = (roof_c, roof_g) if c_ms >= g_ms else (roof_g, roof_c)
 

@@ -26,9 +26,6 @@
  *  - Errors: every entry point returns EXT4PCF_OK (0) or a negative code; no exception
  *    crosses the ABI.  ext4pcf_last_error() gives a message for the last failure.  A
  *    context may be used by one host thread at a time.
- *  - Environment: EXT4PCF_GATHER=tc makes the tensor-core precisions (TF32, 3XTF32,
- *    SPLIT_BF16) use the tensor-core neighbour gather (3xTF32 products) instead of the
- *    CUDA-core FP32 gather; both give the same records to FP32 rounding.
  */
 #ifndef EXT4PCF_H
 #define EXT4PCF_H
@@ -104,7 +101,9 @@ EXT4PCF_API int ext4pcf_destroy(ext4pcf_ctx* ctx);
  *   weights     device or host, double [n_gal]
  *   n_gal       total galaxies over all catalogues (>= 0)
  *   radial_bins host, double [n_bins+1], strictly increasing, radial_bins[0] > 0
- *   n_bins      1..32;  n_max >= 0 (<= 40)
+ *   n_bins      1..32 (1..16 for the tensor-core precisions TF32, 3XTF32 and SPLIT_BF16, whose
+ *               B tile holds at most 64 columns, 4 per bin; larger n_bins return
+ *               EXT4PCF_E_UNSUPPORTED before any work);  n_max >= 0 (<= 40)
  *   cat_offsets host, int64 [n_cat+1] or NULL: catalogue k is galaxies
  *               [cat_offsets[k], cat_offsets[k+1]); NULL means one catalogue (n_cat = 1)
  *   centre_mask device or host, uint8 [n_gal] or NULL: only galaxies with a non-zero entry
@@ -240,7 +239,9 @@ EXT4PCF_API int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap
  *                normalisation; axes n + n_max, Theta1, Theta2), accumulated into
  * Stream-ordered after one synchronisation (the catalogue's bounding box).  Waves hold
  * ext4pcf_config.wave_centres centres (0: 4096).  Returns EXT4PCF_OK, EXT4PCF_E_INVALID_ARG
- * (including host pointers), EXT4PCF_E_OOM or EXT4PCF_E_CUDA. */
+ * (including host pointers), EXT4PCF_E_OOM, EXT4PCF_E_CUDA, or EXT4PCF_E_UNSUPPORTED when a
+ * factor index of the generated order-3 tables falls outside the gathered multipole range
+ * for this n_max (checked before any work; no n_max in 0..40 does this today). */
 EXT4PCF_API int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* shears,
                                  const double* weights, int64_t n_gal, const double* radial_bins,
                                  int n_bins, int n_max, double* upsilon3);
@@ -248,9 +249,14 @@ EXT4PCF_API int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, cons
 /* The factor tables compiled into the 4PCF contraction kernels, for inspection, in the
  * layout of ext4pcf_nth_order_factors at order 4 (row mu = 0..7, row 8 the normalisation;
  * 17 ints per row).
- *   which  0: CUDA-core contraction (FP64 / FP32 forms), 1: tensor-core contraction
- *   table  host, int [9][17], or NULL to query the size;  cap  ints available
- * Host only.  Returns 153, or EXT4PCF_E_INVALID_ARG. */
+ *   which  0: CUDA-core contraction (FP64 / FP32 forms), 1: tensor-core contraction,
+ *          2: the exchange of Theta2 and Theta3 used by the tensor-core contraction (Table
+ *          tab:4PCFSymm): per component mu the pair (mu', o) with
+ *          Upsilon_mu[n2, n3](Th1, Th2, Th3) = Upsilon_mu'[n3 + o, n2 - o](Th1, Th3, Th2),
+ *          derived from the tensor-core factor table (18 ints)
+ *   table  host, int [9][17] (which 0, 1) or [9][2] (which 2), or NULL to query the size;
+ *   cap    ints available
+ * Host only.  Returns 153 (18 for which = 2), or EXT4PCF_E_INVALID_ARG. */
 EXT4PCF_API int ext4pcf_contraction_tables(int which, int* table, int cap);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */

@@ -79,7 +79,7 @@ struct ext4pcf_ctx {
   // direct aperture estimator: centres, per-split sums, staged outputs
   DBuf ap_cen, ap_sums, io_rec, io_mom;
   // tensor-core contraction: work items (built once per shape) and the device status word
-  DBuf tc_items, tc_xb, status;
+  DBuf tc_items, tc_xb, tc_red, status;
   int tc_N = -1, tc_nb = -1;
   size_t tc_items_bytes = 0;
   cudaEvent_t ev[8] = {};
@@ -194,7 +194,7 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
                  &ctx->px, &ctx->py, &ctx->xr, &ctx->xi, &ctx->w, &ctx->p4, &ctx->s4, &ctx->bbox,
                  &ctx->centres, &ctx->flags, &ctx->rec, &ctx->xw, &ctx->corr, &ctx->counter, &ctx->ncen,
                  &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small, &ctx->tc_items,
-                 &ctx->tc_xb, &ctx->status, &ctx->ap_cen, &ctx->ap_sums, &ctx->io_rec, &ctx->io_mom};
+                 &ctx->tc_xb, &ctx->tc_red, &ctx->status, &ctx->ap_cen, &ctx->ap_sums, &ctx->io_rec, &ctx->io_mom};
   for (DBuf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
@@ -320,7 +320,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   if (tc) {
     if (ctx->tc_N != n_max || ctx->tc_nb != n_bins) {
       std::vector<int4> items;
-      tc_build_items(L, items);
+      if (!tc_build_items(L, items)) return fail(ctx, EXT4PCF_E_UNSUPPORTED, "no symmetry map for the contraction table");
       ENSURE(ctx->tc_items, items.size() * sizeof(int4));
       CK(cudaMemcpy(ctx->tc_items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
       ctx->tc_items_bytes = items.size() * sizeof(int4);
@@ -409,10 +409,11 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     const size_t corr_doubles = corrections_size(L);
     ENSURE(ctx->corr, corr_doubles * 8);
     CK(cudaMemsetAsync(ctx->corr.p, 0, corr_doubles * 8, s));
-    // the tensor-core gather (gather_tc.cu) is selected with EXT4PCF_GATHER=tc; the CUDA-core
-    // gather is the default because it is faster on the workloads measured so far
-    const char* gsel = std::getenv("EXT4PCF_GATHER");
-    const bool use_tc_gather = gsel && std::strcmp(gsel, "tc") == 0;
+    if (tc) {
+      const size_t red_bytes = tc_reduced_doubles(L) * 8;
+      ENSURE(ctx->tc_red, red_bytes);
+      CK(cudaMemsetAsync(ctx->tc_red.p, 0, red_bytes, s));
+    }
     for (int w0 = 0; w0 < n_cen; w0 += T) {
       const int Tw = std::min(T, n_cen - w0);
       const int* cl = (const int*)ctx->centres.p + w0;
@@ -420,9 +421,6 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       if (f64) {
         CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                                (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
-      } else if (tc && use_tc_gather && gather_tc_supported(L)) {
-        CK(gather_wave_tc(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
-                          (unsigned long long*)ctx->counter.p, ctx->sm_count, (int*)ctx->status.p, timeout, s));
       } else {
         CK(gather_wave<float>(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
@@ -433,7 +431,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       } else if (prec == EXT4PCF_FP32) {
         CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, s));
       } else {
-        CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, prec,
+        CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, (double*)ctx->tc_red.p, prec,
                             (const int4*)ctx->tc_items.p, (int)(ctx->tc_items_bytes / sizeof(int4)),
                             (float2*)ctx->tc_xb.p, (int*)ctx->status.p, timeout, s));
       }
@@ -453,6 +451,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       }
       ++tot_waves;
     }
+    if (tc) CK(tc_expand(L, (const double*)ctx->tc_red.p, ups_k, s));
     CK(corrections_apply(L, (const double*)ctx->corr.p, ups_k, s));
 
   }

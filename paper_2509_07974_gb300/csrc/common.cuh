@@ -67,10 +67,27 @@ struct Layout {
 };
 
 // ---------------------------------------------------------------------------------------
+// Cell grid of a catalogue.  The measure path computes it on the device (from the bounding
+// box, without a host round trip) and the kernels read it from there; the direct aperture
+// estimator chooses its own grid on the host.
+// ---------------------------------------------------------------------------------------
+struct GridGeom {
+  double x0, y0;    // grid origin
+  double cell;      // cell side (12 significant bits, so cx*cell is exact in float)
+  double inv_cell;
+  int ncx, ncy;     // cells per axis
+  float cellf;
+  int bad;          // 1 if the positions are not all finite
+};
+// cells per axis never exceed this (the cell side is at least 1/4000 of the extent)
+constexpr int kMaxCellsPerAxis = 4003;
+
+// ---------------------------------------------------------------------------------------
 // A catalogue sorted by cell (built by the grid kernels).
 // ---------------------------------------------------------------------------------------
 struct SortedCat {
   int n;            // galaxies
+  const GridGeom* geom;  // device grid of the measure path (nullptr: the host fields below)
   int ncx, ncy;     // cells per axis
   double x0, y0;    // grid origin (double)
   double cell;      // cell side (few significant bits, so cx*cell is exact in float)
@@ -114,19 +131,18 @@ cudaError_t grid_bbox(const double* pos, int n, double* d_bbox, cudaStream_t s);
 cudaError_t grid_sort(const double* pos, const double* shear, const double* wts, int n,
                       double x0, double y0, double cell, int ncx, int ncy, bool want_f32,
                       GridBuffers& gb, SortedCat& out, cudaStream_t s);
+// the measure path: the grid chosen on the device from the bounding box d_bbox (written by
+// grid_bbox) for separations up to rmax, then the sort; cell_start must hold
+// kMaxCellsPerAxis^2 + 1 entries
+cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n,
+                             const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
+                             GridBuffers& gb, SortedCat& out, cudaStream_t s);
 
 // gather.cu: per-centre multipole records for centres[c0 .. c0+T) (sorted positions).
 template <typename R>
 cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
                         const int* centres, int T, cplx_t<R>* rec, cplx_t<R>* xw,
                         unsigned long long* pair_count, int sm_count, cudaStream_t s);
-
-// gather_tc.cu: the same records by a tensor-core gather (FP32 inputs, 3xTF32 products);
-// status receives 1 if a bounded wait ran out.
-bool gather_tc_supported(const Layout& L);
-cudaError_t gather_wave_tc(const SortedCat& cat, const Bins& bins, const Layout& L, const int* centres, int T,
-                           float2* rec, float2* xw, unsigned long long* pair_count, int sm_count, int* status,
-                           long long timeout, cudaStream_t s);
 
 // contract.cu
 template <typename R>
@@ -138,12 +154,16 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
 cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, cudaStream_t s);
 size_t corrections_size(const Layout& L);  // doubles
 
-// contract_tc.cu (tensor cores)
+// contract_tc.cu (tensor cores).  The wave is contracted into the reduced array of the
+// Theta2 <-> Theta3 symmetry (tc_reduced_doubles doubles, zeroed per catalogue); tc_expand adds
+// every ordered triple at |n| <= N from it into the output.
 bool tc_supported(const Layout& L, int precision);
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T,
-                             double* ups, int precision, const int4* items, int n_items, float2* xb,
+                             double* red, int precision, const int4* items, int n_items, float2* xb,
                              int* status, long long timeout, cudaStream_t s);
 size_t contract_tc_xb_bytes(const Layout& L, int T);
-void tc_build_items(const Layout& L, std::vector<int4>& items);
+size_t tc_reduced_doubles(const Layout& L);
+bool tc_build_items(const Layout& L, std::vector<int4>& items);
+cudaError_t tc_expand(const Layout& L, const double* red, double* ups, cudaStream_t s);
 
 }  // namespace ext4pcf

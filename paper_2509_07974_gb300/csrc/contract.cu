@@ -175,7 +175,7 @@ contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx
 // Correction sums over the wave: block (mu, kind, index); thread (2x2 tile of (ba, bb), slice
 // of the centres), or, for the triple term, threads over the centres.
 template <typename R>
-__global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
+__global__ void __launch_bounds__(256, 8) corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
                                    const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ corr) {
   using Cx = cplx_t<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,9 +203,11 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
     const int tile = tid % ntiles, slice = tid / ntiles;
     const bool active = slice < nslices;
     const int ta = 2 * (tile / nt2), tb = 2 * (tile % nt2);
-    Cx acc[2][2];
+    // products in R; each chunk's partial sums (at most kCorrChunk / nslices centres) are
+    // added into FP64 registers, so no R-precision sum runs over more than one chunk
+    double acc64[2][2][2];
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) acc[i][j] = cmk<Cx>(R(0), R(0));
+      for (int j = 0; j < 2; ++j) acc64[i][j][0] = acc64[i][j][1] = 0.0;
     for (int c0 = 0; c0 < T; c0 += kCorrChunk) {
       const int nc = min(kCorrChunk, T - c0);
       for (int k = tid; k < nc * 2 * nbp; k += blockDim.x) {
@@ -221,7 +223,10 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
         }
       }
       __syncthreads();
-      if (active)
+      if (active) {
+        Cx acc[2][2];
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j) acc[i][j] = cmk<Cx>(R(0), R(0));
         for (int cc = slice; cc < nc; cc += nslices) {
           const Cx p0 = sP[cc * nbp + ta], p1 = sP[cc * nbp + ta + 1];
           const Cx o0 = sO[cc * nbp + tb], o1 = sO[cc * nbp + tb + 1];
@@ -230,21 +235,28 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
           acc[1][0] = cadd(acc[1][0], cmul(p1, o0));
           acc[1][1] = cadd(acc[1][1], cmul(p1, o1));
         }
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j) {
+            acc64[i][j][0] += (double)acc[i][j].x;
+            acc64[i][j][1] += (double)acc[i][j].y;
+          }
+      }
       __syncthreads();
     }
-    // fixed-order sum over the slices
-    Cx* red = reinterpret_cast<Cx*>(smem_raw);  // [nslices][ntiles][4]
+    // fixed-order sum over the slices (FP64)
+    double2* red = reinterpret_cast<double2*>(smem_raw);  // [nslices][ntiles][4]
     if (active)
-      for (int q = 0; q < 4; ++q) red[((size_t)slice * ntiles + tile) * 4 + q] = acc[q >> 1][q & 1];
+      for (int q = 0; q < 4; ++q)
+        red[((size_t)slice * ntiles + tile) * 4 + q] = make_double2(acc64[q >> 1][q & 1][0], acc64[q >> 1][q & 1][1]);
     __syncthreads();
     for (int o = tid; o < nb * nb; o += blockDim.x) {
       const int ba = o / nb, bb = o % nb;
       const int t = (ba >> 1) * nt2 + (bb >> 1), q = (ba & 1) * 2 + (bb & 1);
       double re = 0, im = 0;
       for (int sl = 0; sl < nslices; ++sl) {
-        const Cx v = red[((size_t)sl * ntiles + t) * 4 + q];
-        re += (double)v.x;
-        im += (double)v.y;
+        const double2 v = red[((size_t)sl * ntiles + t) * 4 + q];
+        re += v.x;
+        im += v.y;
       }
       double* out = corr + 2 * (mu_base + (size_t)row * nb2 + o);
       out[0] += re;
@@ -256,11 +268,14 @@ __global__ void corrections_kernel(const Layout L, const cplx_t<R>* __restrict__
     const int k = kTriple[mu];
     double* red = reinterpret_cast<double*>(smem_raw);  // [2][blockDim]
     for (int b = 0; b < nb; ++b) {
-      Cx acc = cmk<Cx>(R(0), R(0));
-      for (int c = tid; c < T; c += blockDim.x)
-        acc = cadd(acc, cmul(centre_factor(xw, c, cp.xconj), rec[(size_t)c * L.rec + L.TR(k, b)]));
-      red[tid] = (double)acc.x;
-      red[blockDim.x + tid] = (double)acc.y;
+      double ar = 0.0, ai = 0.0;  // products in R, summed in FP64
+      for (int c = tid; c < T; c += blockDim.x) {
+        const Cx v = cmul(centre_factor(xw, c, cp.xconj), rec[(size_t)c * L.rec + L.TR(k, b)]);
+        ar += (double)v.x;
+        ai += (double)v.y;
+      }
+      red[tid] = ar;
+      red[blockDim.x + tid] = ai;
       __syncthreads();
       // fold the entries past the largest power of two first, then a tree (any block size)
       int p2 = 1;
@@ -381,7 +396,7 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
   const int threads = std::max(192, (ntiles + 31) / 32 * 32);
   const int nbp = 2 * ((L.nb + 1) / 2);
   const size_t smem = std::max(std::max((size_t)kCorrChunk * 2 * nbp * sizeof(cplx_t<R>),
-                                        (size_t)threads * 4 * sizeof(cplx_t<R>)),
+                                        (size_t)threads * 4 * sizeof(double2)),
                                (size_t)2 * threads * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(corrections_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

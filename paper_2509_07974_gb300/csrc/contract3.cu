@@ -97,6 +97,9 @@ bool build_table3(int N, Table3& t) {
     const F3 &f0 = c.f[0], &f1 = c.f[1];
     if (f0.arr != f1.arr) return false;
     if (f0.arr == 1) {  // w_j e^{i m0 phi} w_j e^{i m1 phi}
+      // the same-galaxy term below is W W at the summed index, valid only when neither W
+      // factor is conjugated; a table with a conjugated W factor is refused
+      if (f0.conj || f1.conj) return false;
       if (f0.a + f1.a != 0) return false;
       c.d = D3{2, f0.b + f1.b, 0};
       if (!in_range(f0, N, -2 * N, 2 * N) || !in_range(f1, N, -2 * N, 2 * N) || std::abs(c.d.idx) > 2 * N)

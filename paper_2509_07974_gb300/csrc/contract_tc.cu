@@ -5,26 +5,38 @@
 //   KR_i = xt_i * B_i[n2](Th2) * C_i[n3](Th3)   (a Khatri-Rao product over the centre i),
 // i.e. a complex GEMM over the centre index.  Components that share KR (mu = 0 and 2;
 // mu = 1 and 5) share the GEMM.  Mapping onto tcgen05.mma (M = 128, K along centres):
-//   * A operand (TMEM): 128 KR rows (n2, Th2, Th3) of one s.  Row r of the tile is TMEM
+//   * A operand (TMEM): 128 KR rows (n2, Th2 <= Th3) of one s.  Row r of the tile is TMEM
 //     lane r; centre i occupies K elements (2i, 2i+1) = (re, im).  Sixteen producer warps
 //     form KR on the CUDA cores and write it with tcgen05.st (warp w owns lanes
 //     32 (w % 4) ..; the four warps of a lane group split the 32 centres of a stage).
-//     Each stage's record slices (x~ B rows, C rows, A rows) are staged in shared memory
-//     with cp.async two stages ahead.
 //   * B operand (shared memory, K-major, 128-byte swizzle): column (mu, Th1, re|im) holds
 //     the real embedding of A_i^mu(Th1): K rows (2i, 2i+1) = (Ar, -Ai) for the real output
 //     and (Ai, Ar) for the imaginary output, so that D = A_op B_op is the complex product.
 //   * D (TMEM, FP32): 128 rows x (2 * #mu * nb, padded to 16) columns.  Every 64 centres the
 //     partial sum is promoted out of TMEM into FP32 registers (two D buffers alternate, so
 //     the MMAs run on meanwhile); the long FP32 accumulation inside the tensor core would
-//     otherwise lose bits.  The epilogue adds the sums into the FP64 output.
+//     otherwise lose bits.  The epilogue adds the sums into the FP64 reduced output.
+// Staging: a pre-pass writes the wave's x~B values and G, W multipoles transposed (one row
+// per (quantity, multipole, bin), the centres along the row); a loader warp copies each
+// stage's rows (32 centres) into shared memory with 2D TMA boxes of 16 centres x 8 rows
+// (128-byte swizzle, so that eight lanes reading eight rows hit different banks).
 // Precision: BF16x3 splits every operand into bf16 hi + lo and accumulates
 // hi*hi + hi*lo + lo*hi (kind::f16); 3xTF32 does the same with tf32 hi + lo (kind::tf32,
 // ~22 mantissa bits per operand); TF32 uses one kind::tf32 pass.
-// x~ B is formed for the whole wave by xb_kernel before the contraction.
-// Pipeline: 4 (3 for 3xTF32) stages of 32 centres; full/empty mbarriers between the producers and the one
-// thread that issues the MMAs; tcgen05.commit releases a stage.  Every wait is bounded by
-// a clock budget; on expiry the kernel records an error code and runs to its end.
+// Every wait is bounded by a clock budget; on expiry the kernel records an error code, runs
+// to its end, waits for its own MMAs and copies and frees its TMEM.
+//
+// Symmetry reduction (Table tab:4PCFSymm, the column that swaps Theta2 and Theta3): for
+// every component mu there is a component mu' and an offset o with
+//   Upsilon_mu[n2, n3](Th1, Th2, Th3) = Upsilon_mu'[n3 + o, n2 - o](Th1, Th3, Th2).
+// The tile rows therefore run over the bin pairs Th2 <= Th3 only (nb (nb + 1) / 2 of nb^2),
+// and over the multipoles the map reaches from |n2|, |n3| <= N (one more n2 per s); the
+// results go to a reduced FP64 array [9][2N+3][2N+3][nb][pairs], from which tc_expand adds
+// every ordered triple at |n| <= N into the output once per catalogue.  mu' and o are derived
+// on the host from the factor table below (derive_swap_map), not typed in.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -38,7 +50,7 @@ namespace {
 constexpr int kStageCentres = 32;
 constexpr int kProducerWarps = 16;
 constexpr int kProducers = kProducerWarps * 32;
-constexpr int kThreads = kProducers + 32;
+constexpr int kThreads = kProducers + 64;  // + the MMA issuer warp and the TMA loader warp
 constexpr uint32_t kTmemCols = 512;
 constexpr int kDCols = 128;          // D region: two 64-column buffers
 constexpr int kMaxNpad = 64;         // B columns: 2 * #mu * nb padded to 16 (nb <= 16)
@@ -70,17 +82,57 @@ __constant__ KRType kKR[7] = EXT4PCF_KR_TABLE;
 const KRType kKRHost[7] = EXT4PCF_KR_TABLE;
 constexpr int kKRTypes = 7;
 
-struct TcArgs {
-  Layout L;
-  const float2* rec;
-  const float2* xw;
-  int T;
-  double* ups;
-  const int4* items;  // (type, s, row0, nrows)
-  int n_items;
-  long long timeout;
-  int* status;
-};
+bool same_kf(KF a, KF b) { return a.arr == b.arr && a.sgn == b.sgn && a.off == b.off && a.conj == b.conj; }
+
+// Partner mu' and offset o of every component under the exchange of Theta2 and Theta3, from
+// the factor table: the centre factor and the column factor A(s) (s = n2 + n3 is kept) must be
+// the same, and the row factors must trade places, B'(n3 + o) = C(n3) and C'(n2 - o) = B(n2).
+// Returns false if a component has no partner.
+bool derive_swap_map(signed char mup[9], signed char off[9]) {
+  for (int mu = 0; mu < 9; ++mu) {
+    int t = -1, g = 0;
+    for (int k = 0; k < kKRTypes && t < 0; ++k)
+      for (int j = 0; j < kKRHost[k].nmu; ++j)
+        if (kKRHost[k].mu[j] == mu) { t = k; g = j; }
+    if (t < 0) return false;
+    const KRType& a = kKRHost[t];
+    bool found = false;
+    for (int k = 0; k < kKRTypes && !found; ++k)
+      for (int j = 0; j < kKRHost[k].nmu && !found; ++j) {
+        const KRType& b = kKRHost[k];
+        if (b.xconj != a.xconj || !same_kf(b.A[j], a.A[g])) continue;
+        for (int o = -1; o <= 1 && !found; ++o) {
+          KF bB = b.B, bC = b.C;  // B'(n3 + o) = C(n3): sgn' = sgn_C, off' + sgn' o = off_C
+          if (bB.arr != a.C.arr || bB.conj != a.C.conj || bB.sgn != a.C.sgn || bB.off + bB.sgn * o != a.C.off) continue;
+          if (bC.arr != a.B.arr || bC.conj != a.B.conj || bC.sgn != a.B.sgn || bC.off - bC.sgn * o != a.B.off) continue;
+          mup[mu] = b.mu[j];
+          off[mu] = (signed char)o;
+          found = true;
+        }
+      }
+    if (!found) return false;
+  }
+  return true;
+}
+
+// offset o shared by the components of row type t (the rows of a type serve all its components)
+int type_offset(int t, const signed char off[9]) {
+  const int o = off[kKRHost[t].mu[0]];
+  for (int j = 1; j < kKRHost[t].nmu; ++j)
+    if (off[kKRHost[t].mu[j]] != o) return 99;
+  return o;
+}
+
+// bin pair p -> (b2, b3), b2 <= b3, pairs in row-major order of (b2, b3)
+__device__ __forceinline__ void pair_of(int p, int nb, int& b2, int& b3) {
+  int b = 0, first = 0;
+  while (p >= first + (nb - b)) {
+    first += nb - b;
+    ++b;
+  }
+  b2 = b;
+  b3 = b + (p - first);
+}
 
 // bf16 hi/lo split of a pair (re, im) packed as bf16x2 (re in the low half)
 __device__ __forceinline__ void split_bf16(float re, float im, uint32_t& hi, uint32_t& lo) {
@@ -93,34 +145,103 @@ __device__ __forceinline__ void split_bf16(float re, float im, uint32_t& hi, uin
   lo = l;
 }
 
-// One staged block of a per-centre record: `len` consecutive complex values starting at
-// record element `rec_off`; `lo` is the first multipole index (n for G, m = |n| for W).
-struct Blk {
-  int rec_off, len, lo, is_w;
+struct TcArgs {
+  Layout L;
+  int T;              // centres of the wave
+  double* red;        // reduced output [9][2N+3][2N+3][nb][npairs] (complex, FP64)
+  int npairs;         // nb (nb + 1) / 2
+  const int4* items;  // (type, s, row0, nrows | (n2 of row 0 of the s block + 64) << 8)
+  int n_items;
+  int row_g, row_w;   // first row of G and of W in the transposed wave array (x~B rows from 0)
+  int in_stages;      // depth of the staged-input ring
+  int stage_rows;     // rows per staged stage and half (multiple of 8)
+  long long timeout;
+  int* status;
 };
 
-__device__ __forceinline__ Blk make_blk(const Layout& L, KF f, int va, int vb) {
-  int nlo = f.sgn > 0 ? va + f.off : -vb + f.off;
-  int nhi = f.sgn > 0 ? vb + f.off : -va + f.off;
-  Blk b;
+// The transposed wave array (one row per (quantity, multipole, bin), the wave's centres along
+// the row, padded to a multiple of 32):
+//   rows [0, row_g)       x~ B per row type of B: (xb type, n2 + N + 1, bin), n2 in [-N-1, N+1]
+//   rows [row_g, row_w)   G_n(bin), n in [-2N-3, 2N-1]
+//   rows [row_w, rows)    W_m(bin), m in [0, 2N]
+// x~ B: 0: x G[-n2-2]   1: x G[n2-2]^*   2: x^* G[-n2-2]   3: x^* G[n2-2]^*   4: w W[-n2] (|n2| <= N)
+constexpr int kXBTypes = 5;
+__constant__ signed char kXBOfType[7] = {0, 1, 0, 2, 3, 2, 4};
+
+__device__ __forceinline__ float2 wave_value(const Layout& L, const float2* __restrict__ rc, float2 x, float w,
+                                             int r, int row_g, int row_w) {
+  const int nb = L.nb, N = L.N, nx = 2 * N + 3;
+  if (r >= row_w) return rc[L.oW + (r - row_w)];
+  if (r >= row_g) return rc[L.oG + (r - row_g)];
+  const int t = r / (nx * nb), n2 = (r / nb) % nx - N - 1, b = r % nb;
+  float2 f;
+  if (t == 4) {
+    // the normalisation rows keep |n2| <= N (its swap partner is itself, o = 0)
+    const int m = -n2;
+    f = (m <= N && m >= -N) ? rc[L.W(m >= 0 ? m : -m, b)] : make_float2(0.f, 0.f);
+    if (m < 0) f.y = -f.y;
+    x = make_float2(w, 0.f);
+  } else {
+    f = (t & 1) ? rc[L.G(n2 - 2, b)] : rc[L.G(-n2 - 2, b)];
+    if (t & 1) f.y = -f.y;
+    if (t >= 2) x.y = -x.y;
+  }
+  return make_float2(x.x * f.x - x.y * f.y, x.x * f.y + x.y * f.x);
+}
+
+// 32 rows x 32 centres per block through shared memory: reads along each centre's record,
+// writes along the centres of each row (both coalesced)
+__global__ void __launch_bounds__(256) transpose_wave_kernel(const Layout L, const float2* __restrict__ rec,
+                                                             const float2* __restrict__ xw, int T, int Tp,
+                                                             int row_g, int row_w, int rows,
+                                                             float2* __restrict__ out) {
+  __shared__ float2 tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = c0 + ty + 8 * k, r = r0 + tx;
+    float2 v = make_float2(0.f, 0.f);
+    if (c < T && r < rows)
+      v = wave_value(L, rec + (size_t)c * L.rec, xw[2 * (size_t)c], xw[2 * (size_t)c + 1].x, r, row_g, row_w);
+    tile[ty + 8 * k][tx] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = r0 + ty + 8 * k, c = c0 + tx;
+    if (r < rows && c < T) out[(size_t)r * Tp + c] = tile[tx][ty + 8 * k];
+  }
+}
+
+// Rows of the transposed array holding factor f for its variable in [va, vb]; `lo` is the
+// first multipole index (n for G, m = |n| for W).
+struct RowBlk {
+  int row0, len, lo, is_w;
+};
+__device__ __forceinline__ RowBlk row_blk(const TcArgs& a, KF f, int va, int vb) {
+  const int nb = a.L.nb, N = a.L.N;
+  const int nlo = f.sgn > 0 ? va + f.off : -vb + f.off;
+  const int nhi = f.sgn > 0 ? vb + f.off : -va + f.off;
+  RowBlk b;
   b.is_w = f.arr;
   if (f.arr == 0) {
     b.lo = nlo;
-    b.rec_off = L.G(nlo, 0);
-    b.len = (nhi - nlo + 1) * L.nb;
+    b.row0 = a.row_g + (nlo + 2 * N + 3) * nb;
+    b.len = (nhi - nlo + 1) * nb;
   } else {
     int mlo, mhi;
     if (nlo >= 0) { mlo = nlo; mhi = nhi; }
     else if (nhi <= 0) { mlo = -nhi; mhi = -nlo; }
     else { mlo = 0; mhi = max(-nlo, nhi); }
     b.lo = mlo;
-    b.rec_off = L.W(mlo, 0);
-    b.len = (mhi - mlo + 1) * L.nb;
+    b.row0 = a.row_w + mlo * nb;
+    b.len = (mhi - mlo + 1) * nb;
   }
   return b;
 }
-// staged index (within the block) and conjugation of factor f at variable v, bin b
-__device__ __forceinline__ int blk_index(const Blk& k, KF f, int v, int b, int nb, bool& cj) {
+// row (within the block) and conjugation of factor f at variable v, bin b
+__device__ __forceinline__ int blk_index(const RowBlk& k, KF f, int v, int b, int nb, bool& cj) {
   const int n = f.sgn * v + f.off;
   cj = f.conj != 0;
   if (!k.is_w) return (n - k.lo) * nb + b;
@@ -128,65 +249,51 @@ __device__ __forceinline__ int blk_index(const Blk& k, KF f, int v, int b, int n
   return ((n < 0 ? -n : n) - k.lo) * nb + b;
 }
 
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory"); }
-// the four producer warps of one centre quarter (barriers 2..5): within a stage a quarter
-// reads only the staged slices that its own warps copied
-__device__ __forceinline__ void quarter_sync(int q) { asm volatile("bar.sync %0, 128;" ::"r"(2 + q) : "memory"); }
-
-// x~ times the row factor B, per centre: [5][2N+1][nb] complex, indexed by n2:
-//   0: x G[-n2-2]   1: x G[n2-2]^*   2: x^* G[-n2-2]   3: x^* G[n2-2]^*   4: w W[-n2]
-constexpr int kXBTypes = 5;
-__constant__ signed char kXBOfType[7] = {0, 1, 0, 2, 3, 2, 4};
-
-__global__ void xb_kernel(const Layout L, const float2* __restrict__ rec, const float2* __restrict__ xw, int T,
-                          float2* __restrict__ xb) {
-  const int nb = L.nb, N = L.N, nn = 2 * N + 1;
-  const int per = kXBTypes * nn * nb;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < (size_t)T * per;
-       k += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(k / per), r = (int)(k % per);
-    const int t = r / (nn * nb), n2 = (r / nb) % nn - N, b = r % nb;
-    const float2* rc = rec + (size_t)c * L.rec;
-    float2 x = xw[2 * (size_t)c], f;
-    if (t == 4) {
-      const int m = -n2;
-      f = rc[L.W(m >= 0 ? m : -m, b)];
-      if (m < 0) f.y = -f.y;
-      x = xw[2 * (size_t)c + 1];
-    } else {
-      f = (t & 1) ? rc[L.G(n2 - 2, b)] : rc[L.G(-n2 - 2, b)];
-      if (t & 1) f.y = -f.y;
-      if (t >= 2) x.y = -x.y;
-    }
-    xb[k] = make_float2(x.x * f.x - x.y * f.y, x.x * f.y + x.y * f.x);
-  }
+// Geometry of one work item: the staged blocks (x~B rows, C rows, A rows) of every stage and
+// their rows in the staged buffer (each block starts at a multiple of 8 rows: one TMA box).
+struct ItemGeo {
+  int type, s, row0, nrows, n2a, t2a, t2b;
+  RowBlk bx, bc, ba0, ba1;
+  int sx, sc, sa0, sa1;
+};
+__device__ __forceinline__ int round8(int v) { return (v + 7) & ~7; }
+__device__ __forceinline__ ItemGeo item_geo(const TcArgs& a, int4 item, const KRType& kr) {
+  const int nb = a.L.nb, N = a.L.N, nx = 2 * N + 3;
+  ItemGeo g;
+  g.type = item.x;
+  g.s = item.y;
+  g.row0 = item.z;
+  g.nrows = item.w & 0xFF;
+  g.n2a = (item.w >> 8) - 64;
+  g.t2a = g.n2a + g.row0 / a.npairs;
+  g.t2b = g.n2a + (g.row0 + g.nrows - 1) / a.npairs;
+  g.bx.row0 = (kXBOfType[g.type] * nx + (g.t2a + N + 1)) * nb;
+  g.bx.len = (g.t2b - g.t2a + 1) * nb;
+  g.bx.lo = g.t2a;
+  g.bx.is_w = 0;
+  g.bc = row_blk(a, kr.C, g.s - g.t2b, g.s - g.t2a);
+  g.ba0 = row_blk(a, kr.A[0], g.s, g.s);
+  g.ba1 = kr.nmu > 1 ? row_blk(a, kr.A[1], g.s, g.s) : RowBlk{0, 0, 0, 0};
+  g.sx = 0;
+  g.sc = round8(g.bx.len);
+  g.sa0 = g.sc + round8(g.bc.len);
+  g.sa1 = g.sa0 + round8(g.ba0.len);
+  return g;
 }
 
-constexpr int kStageBufs = 3;  // staging ring: stage k + 2 is fetched while k is formed
-// A staged stage is [slot][centre]: slot e of the 32 centres is one row of kCS complex values
-// (32 + 2 padding, so that rows start 4 banks apart and eight lanes reading eight slots of
-// the same centres hit different banks).  A thread's eight centres are contiguous: it reads
-// them with four 16-byte loads at fixed offsets.
-constexpr int kCS = 34;
-// staged slots per centre: a zero, the x~B and C blocks of at most the tile's n2 values
-// (128 rows = 128 / nb^2 values of n2, +2 for misalignment, at most 2N+1) and two A rows
-__host__ __device__ inline int stage_values(int nb, int N) {
-  int rows = 128 / (nb * nb) + 2;
-  if (rows > 2 * N + 1) rows = 2 * N + 1;
-  return (1 + 2 * rows * nb + 2 * nb) | 1;
-}
+// byte offset, inside one half of a staged stage, of the 16-byte chunk c of row e (the TMA's
+// 128-byte swizzle: chunk index XOR row mod 8)
+__device__ __forceinline__ uint32_t stg_off(int e, int c) { return (uint32_t)(e * 128 + ((c ^ (e & 7)) << 4)); }
+
 // stages per TMEM partial sum (64 centres): the tensor core's FP32 accumulation loses bits
 // in proportion to the MMAs it accumulates (measured: ~3e-4 over 750 MMAs, ~5e-5 over
 // 96, ~1.5e-4 over 192 for 3xTF32), so partial sums are short and summed in registers
 constexpr int kPromote = 2;
 constexpr int kDBuf = 64;    // two D buffers of 64 columns (npad <= 64)
 constexpr int kQuarter = kStageCentres / (kProducerWarps / 4);  // centres per producer warp
+constexpr int kWarpMma = kProducerWarps, kWarpLoad = kProducerWarps + 1;
+constexpr int kBoxRows = 8;     // rows per TMA box
+constexpr int kMaxInStages = 4; // staged-input ring depth (at most)
 
 // Per precision: stages, TMEM columns and 128-byte-wide shared-memory K-atoms per stage.
 template <int PREC> struct TcPrec;
@@ -200,26 +307,40 @@ template <> struct TcPrec<EXT4PCF_3XTF32> {  // A: hi | lo fp32 pairs; B: hi 2 a
   static constexpr int kStages = 3, kStageCols = 128, kAtoms = 4;
 };
 
+// Warp roles: warps 0..15 form the A operand (Khatri-Rao rows, TMEM) and the B operand
+// (shared memory) of each stage; warp 16 issues the MMAs (one thread); warp 17 stages each
+// stage's rows of the transposed wave array with TMA (one thread).  Rings and their
+// mbarriers (counts in brackets):
+//   staged input  in_full [1 + TMA bytes] / in_empty [16 producer warps]
+//   A and B       ab_full [16 producer warps] / ab_empty [1, tcgen05.commit]
+//   partial sums  dfull [1, tcgen05.commit] / dempty [16 producer warps]
+// Producer warps run on their own: a warp waits only for its stage's data and for a free
+// A/B slot, and arrives once per stage (lane 0, after __syncwarp).
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
+contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) {
   using P = TcPrec<PREC>;
   constexpr int kSt = P::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const Layout L = args.L;
-  const int nb = L.nb, N = L.N, nn = 2 * N + 1, nb2 = nb * nb;
+  const int nb = L.nb, N = L.N, npairs = args.npairs;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int tile_bytes = kMaxNpad * 128;  // one 128-byte-wide K-atom (npad <= 64)
   constexpr int stage_bytes = P::kAtoms * tile_bytes;
-  const int sc_max = stage_values(nb, N);
-  float2* stg = reinterpret_cast<float2*>(sm + kSt * stage_bytes);
-  int* gmap = reinterpret_cast<int*>(stg + kStageBufs * sc_max * kCS);  // [sc_max]
-  uint64_t* full = reinterpret_cast<uint64_t*>(gmap + ((sc_max + 1) & ~1));
-  uint64_t* empty = full + kSt;
-  uint64_t* dfull = empty + kSt;  // [2]: a D buffer holds a finished partial sum
-  uint64_t* dempty = dfull + 2;   // [2]: the producers have read it
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dempty + 2);
+  const int S_in = args.in_stages;
+  const uint32_t half_bytes = (uint32_t)args.stage_rows * 128u;
+  unsigned char* in_base = sm + kSt * stage_bytes;  // S_in stages of two halves
+  uint64_t* bars = reinterpret_cast<uint64_t*>(in_base + (size_t)S_in * 2 * half_bytes);
+  uint64_t* in_full = bars;
+  uint64_t* in_empty = in_full + kMaxInStages;
+  uint64_t* ab_full = in_empty + kMaxInStages;
+  uint64_t* ab_empty = ab_full + kSt;
+  uint64_t* dfull = ab_empty + kSt;  // [2]
+  uint64_t* dempty = dfull + 2;      // [2]
+  uint64_t* drain = dempty + 2;      // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
@@ -228,16 +349,23 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
+    for (int k = 0; k < S_in; ++k) {
+      mbar_init(&in_full[k], 1);
+      mbar_init(&in_empty[k], kProducerWarps);
+    }
     for (int k = 0; k < kSt; ++k) {
-      mbar_init(&full[k], kProducers);
-      mbar_init(&empty[k], 1);
+      mbar_init(&ab_full[k], kProducerWarps);
+      mbar_init(&ab_empty[k], 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(&dfull[k], 1);
-      mbar_init(&dempty[k], kProducers);
+      mbar_init(&dempty[k], kProducerWarps);
     }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == kWarpLoad && lane == 0) tma_prefetch_desc(&tmap);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -245,125 +373,61 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
   const long long budget = args.timeout;
   const int nstage = (args.T + kStageCentres - 1) / kStageCentres;
   const int nsub = (nstage + kPromote - 1) / kPromote;
-  const size_t xb_stride = (size_t)kXBTypes * nn * nb;
   int err = 0;
+  // bounded wait on an mbarrier phase; the first wait of the CTA that runs out of its budget
+  // raises the abort flag, after which every wait gives up at once, so that a broken
+  // pipeline ends the kernel quickly (with the status word set) instead of waiting out the
+  // budget at every stage
+  auto wait = [&](uint64_t* b, uint32_t parity) -> bool {
+    if (*abort_flag) {
+      err = 1;
+      return false;
+    }
+    if (mbar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity)) {
+      if (*abort_flag || clock64() - t0 > budget) {
+        *abort_flag = 1;
+        err = 1;
+        return false;
+      }
+    }
+    return true;
+  };
 
-  long long gk = 0;  // stages handled by this CTA (phases of full / empty)
-  long long gs = 0;  // partial sums handled by this CTA (phases of dfull / dempty)
-  for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
-    const int4 item = args.items[it];
-    const int type = item.x, s = item.y, row0 = item.z, nrows = item.w;
-    const KRType kr = kKR[type];
-    const int nmu = kr.nmu;
-    const int ncols = 2 * nmu * nb;
-    const int npad = (ncols + 15) / 16 * 16;
-    const int n2a = max(-N, s - N);
-    // the tile's rows span n2 in [t2a, t2b]; staged per centre: [0] zero, x~B rows
-    // [t2a, t2b], C rows for n3 = s - n2, A_0(s), A_1(s)
-    const int t2a = n2a + row0 / nb2, t2b = n2a + (row0 + nrows - 1) / nb2;
-    const int xb_len = (t2b - t2a + 1) * nb;
-    const int xb_off = (kXBOfType[type] * nn + (t2a + N)) * nb;
-    const Blk bkC = make_blk(L, kr.C, s - t2b, s - t2a);
-    const Blk bkA0 = make_blk(L, kr.A[0], s, s);
-    const Blk bkA1 = nmu > 1 ? make_blk(L, kr.A[1], s, s) : Blk{0, 0, 0, 0};
-    const int bC = 1 + xb_len, bA0 = bC + bkC.len, bA1 = bA0 + bkA0.len;
-    const int sc = (bA1 + bkA1.len) | 1;
-    if (warp < kProducerWarps) {
-      // ------------------------------------------------------------------ producers
-      // record offsets of the staged values after the x~B block (-1: nothing to copy)
-      for (int e = bC + tid; e < sc; e += kProducers) {
-        int m = -1;
-        if (e < bA0) m = bkC.rec_off + (e - bC);
-        else if (e < bA1) m = bkA0.rec_off + (e - bA0);
-        else if (e < bA1 + bkA1.len) m = bkA1.rec_off + (e - bA1);
-        gmap[e] = m;
-      }
-      producers_sync();
-      const int grp = warp & 3, quarter = warp >> 2;
+  if (warp < kProducerWarps) {
+    // ---------------------------------------------------------------------- producers
+    const int grp = warp & 3, quarter = warp >> 2;
+    const int h = quarter >> 1, c0 = (quarter & 1) * 4;  // half and first 16-byte chunk of my centres
+    long long qi = 0, qa = 0, gs = 0;                    // input stages, A/B stages, partial sums
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const KRType kr = kKR[args.items[it].x];
+      const ItemGeo g = item_geo(args, args.items[it], kr);
+      const int nmu = kr.nmu, ncols = 2 * nmu * nb;
       const int rl = grp * 32 + lane;  // tile row = TMEM lane
-      const bool row_ok = rl < nrows;
-      const int rr = row0 + (row_ok ? rl : 0);
-      const int n2 = n2a + rr / nb2, b2 = (rr / nb) % nb, b3 = rr % nb, n3 = s - n2;
+      const bool row_ok = rl < g.nrows;
+      const int rr = g.row0 + (row_ok ? rl : 0);
+      const int n2 = g.n2a + rr / npairs, n3 = g.s - n2;
+      int b2, b3;
+      pair_of(rr % npairs, nb, b2, b3);
       bool cjC;
-      int iB = 1 + (n2 - t2a) * nb + b2;
-      int iC = bC + blk_index(bkC, kr.C, n3, b3, nb, cjC);
+      const int eB = g.sx + (n2 - g.t2a) * nb + b2;
+      const int eC = g.sc + blk_index(g.bc, kr.C, n3, b3, nb, cjC);
       const float sgnC = cjC ? -1.f : 1.f;
-      if (!row_ok) { iB = 0; iC = 0; }
-      // B-operand words of this thread: the quarter's 128 threads write the tile's K range of
-      // its eight centres; column bn, centres 8 quarter + cpt bq + j (j < cpt)
-      const int tq = tid & 127;
-      const int cpt = npad <= 16 ? 1 : (npad <= 32 ? 2 : 4);
-      const int tpc = 8 / cpt;
-      const int bn = tq / tpc, bq = tq % tpc;
-      const int cb0 = quarter * kQuarter + bq * cpt;
-      uint32_t boff[4];
+      // byte offsets (inside a staged stage) of the four 16-byte chunks (two centres each) of
+      // this warp's eight centres in this row's x~B and C slots
+      uint32_t offB[4], offC[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        boff[j] = PREC == EXT4PCF_SPLIT_BF16 ? sw128_word_off(bn, cb0 + j, kMaxNpad)
-                                             : sw128_word_off(bn, 2 * (cb0 + j), kMaxNpad);
-      int iA = 0, bo = 0;
-      float sgnA = 1.f;
-      if (bn < ncols) {
-        const int g = bn / (2 * nb), b1 = (bn >> 1) % nb;
-        bool cjA;
-        bo = bn & 1;
-        iA = (g ? bA1 : bA0) + blk_index(g ? bkA1 : bkA0, kr.A[g], s, b1, nb, cjA);
-        sgnA = cjA ? -1.f : 1.f;
+      for (int q = 0; q < 4; ++q) {
+        offB[q] = (uint32_t)h * half_bytes + stg_off(eB, c0 + q);
+        offC[q] = (uint32_t)h * half_bytes + stg_off(eC, c0 + q);
       }
-      // copy plan of this thread for every stage (16 threads per centre): staged slots
-      // e = 1 + sub + 16 j; slots j < jx come from the x~B array (source offset e - 1 from
-      // the item's x~B row block), slots jx <= j < jr from the record (offset coff[j])
-      constexpr int kMaxCopies = 12;  // 16 * 12 >= stage_values(nb, N) for every supported shape
-      // record offsets (< 2^16 for every supported shape: at most (14 * 40 + 13) * 32
-      // elements per record), two per register
-      uint32_t coff2[kMaxCopies / 2];
-      const int sub = tid & 15;
-      const int e_end = bA1 + bkA1.len;  // slots past the A blocks are padding
-      const int jx = max(0, (bC - 1 - sub + 15) / 16), jr = max(0, (e_end - 1 - sub + 15) / 16);
-#pragma unroll
-      for (int j = 0; j < kMaxCopies; j += 2) {
-        const int e0 = 1 + sub + 16 * j, e1 = e0 + 16;
-        const uint32_t o0 = (e0 >= bC && e0 < e_end) ? (uint32_t)gmap[e0] : 0u;
-        const uint32_t o1 = (e1 >= bC && e1 < e_end) ? (uint32_t)gmap[e1] : 0u;
-        coff2[j / 2] = o0 | (o1 << 16);
-      }
-      // source pointers of the next stage to fetch (advanced by 32 centres per stage)
-      const int ci0 = tid >> 4;
-      const float2* xs_next = xbarr + (size_t)ci0 * xb_stride + xb_off + sub;
-      const float2* rc_next = args.rec + (size_t)ci0 * L.rec;
-      const size_t xs_step = (size_t)kStageCentres * xb_stride, rc_step = (size_t)kStageCentres * L.rec;
-      int fetch_buf = 0;  // staging buffer of the next stage to fetch
-      // copy one stage's slices (stages are fetched in order); tails are zero-filled
-      auto issue = [&](int k) {
-        if (k < nstage) {
-          float2* d = stg + (size_t)fetch_buf * sc_max * kCS + ci0;  // slot e at d[e * kCS]
-          const int c = k * kStageCentres + ci0;
-          if (c < args.T) {
-            if (sub == 0) d[0] = make_float2(0.f, 0.f);
-            float2* dd = d + (1 + sub) * kCS;
-#pragma unroll
-            for (int j = 0; j < kMaxCopies; ++j) {
-              if (j >= jr) break;
-              if (j < jx) cp_async8(dd + 16 * kCS * j, xs_next + 16 * j);
-              else cp_async8(dd + 16 * kCS * j, rc_next + ((coff2[j / 2] >> (16 * (j & 1))) & 0xFFFFu));
-            }
-          } else {
-            for (int e = sub; e < sc; e += 16) d[e * kCS] = make_float2(0.f, 0.f);
-          }
-          xs_next += xs_step;
-          rc_next += rc_step;
-          fetch_buf = fetch_buf == kStageBufs - 1 ? 0 : fetch_buf + 1;
-        }
-        cp_async_commit();
-      };
-      issue(0);
-      issue(1);
       float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
 #pragma unroll
       for (int j = 0; j < 16; ++j) accD[j] = 0.f;
-      auto promote = [&](long long g) {  // read partial sum g from its D buffer
-        const int buf = (int)(g & 1);
-        if (!mbar_wait(&dfull[buf], (uint32_t)((g >> 1) & 1), budget)) err = 1;
+      auto promote = [&](long long gg) {  // read partial sum gg from its D buffer
+        const int buf = (int)(gg & 1);
+        wait(&dfull[buf], (uint32_t)((gg >> 1) & 1));
         tc_fence_after();
         uint32_t v[16];
         tmem_ld16(tmem + ((uint32_t)(grp * 32) << 16) + buf * kDBuf + quarter * 16, v);
@@ -371,63 +435,63 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) accD[j] += __uint_as_float(v[j]);
         tc_fence_before();
-        mbar_arrive(&dempty[buf]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dempty[buf]);
       };
       const long long gs0 = gs;
-      int slot = (int)(gk % kSt);
-      uint32_t ph = (uint32_t)((gk / kSt) & 1);
-      int read_buf = 0;
-      for (int k = 0; k < nstage; ++k, ++gk) {
-        cp_async_wait<1>();
-        quarter_sync(quarter);
-        issue(k + 2);
-        const float2* st = stg + (size_t)read_buf * sc_max * kCS;
-        read_buf = read_buf == kStageBufs - 1 ? 0 : read_buf + 1;
-        if (!mbar_wait(&empty[slot], ph ^ 1u, budget)) err = 1;
+      for (int k = 0; k < nstage; ++k, ++qi, ++qa) {
+        const int islot = (int)(qi % S_in), aslot = (int)(qa % kSt);
+        wait(&in_full[islot], (uint32_t)((qi / S_in) & 1));
+        wait(&ab_empty[aslot], (uint32_t)(((qa / kSt) & 1) ^ 1));
         tc_fence_after();
-        // B operand (shared memory, swizzled): real embedding of A(Th1) for 4 centres
-        unsigned char* bt = sm + slot * stage_bytes;
-        if (bn < npad) {
-          const float2* ap = st + iA * kCS + cb0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            if (j >= cpt) break;
-            float2 a = ap[j];
-            a.y *= sgnA;
-            const float v0 = bo ? a.y : a.x;
-            const float v1 = bo ? a.x : -a.y;
-            if (PREC == EXT4PCF_SPLIT_BF16) {
-              uint32_t h, l;
-              split_bf16(v0, v1, h, l);
-              *reinterpret_cast<uint32_t*>(bt + boff[j]) = h;
-              *reinterpret_cast<uint32_t*>(bt + tile_bytes + boff[j]) = l;
-            } else if (PREC == EXT4PCF_TF32) {
-              *reinterpret_cast<float2*>(bt + boff[j]) = make_float2(v0, v1);
-            } else {
-              uint32_t h0, l0, h1, l1;
-              split_tf32(v0, h0, l0);
-              split_tf32(v1, h1, l1);
-              *reinterpret_cast<uint2*>(bt + boff[j]) = make_uint2(h0, h1);
-              *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + boff[j]) = make_uint2(l0, l1);
-            }
+        const unsigned char* st = in_base + (size_t)islot * 2 * half_bytes;
+        unsigned char* bt = sm + aslot * stage_bytes;
+        // B operand (shared memory, K-major, swizzled): the real embedding of A(Th1) for the
+        // 32 centres of the stage; warp v forms column pair v = (g, b1), lane = centre
+        for (int v = warp; v < nmu * nb; v += kProducerWarps) {
+          const int ga = v / nb, b1 = v % nb;
+          bool cjA;
+          const int eA = (ga ? g.sa1 : g.sa0) + blk_index(ga ? g.ba1 : g.ba0, kr.A[ga], g.s, b1, nb, cjA);
+          float2 a = *reinterpret_cast<const float2*>(st + (lane >> 4) * half_bytes + stg_off(eA, (lane & 15) >> 1) +
+                                                      (lane & 1) * 8);
+          if (cjA) a.y = -a.y;
+          const int nre = 2 * v, nim = 2 * v + 1;
+          if (PREC == EXT4PCF_SPLIT_BF16) {
+            uint32_t rh, rl, ih, il;  // column re: (Ar, -Ai), column im: (Ai, Ar), bf16x2 each
+            split_bf16(a.x, -a.y, rh, rl);
+            split_bf16(a.y, a.x, ih, il);
+            *reinterpret_cast<uint32_t*>(bt + sw128_word_off(nre, lane, kMaxNpad)) = rh;
+            *reinterpret_cast<uint32_t*>(bt + tile_bytes + sw128_word_off(nre, lane, kMaxNpad)) = rl;
+            *reinterpret_cast<uint32_t*>(bt + sw128_word_off(nim, lane, kMaxNpad)) = ih;
+            *reinterpret_cast<uint32_t*>(bt + tile_bytes + sw128_word_off(nim, lane, kMaxNpad)) = il;
+          } else if (PREC == EXT4PCF_TF32) {
+            *reinterpret_cast<float2*>(bt + sw128_word_off(nre, 2 * lane, kMaxNpad)) = make_float2(a.x, -a.y);
+            *reinterpret_cast<float2*>(bt + sw128_word_off(nim, 2 * lane, kMaxNpad)) = make_float2(a.y, a.x);
+          } else {
+            uint32_t xh, xl, yh, yl;
+            split_tf32(a.x, xh, xl);
+            split_tf32(a.y, yh, yl);
+            const uint32_t sgn = 0x80000000u;
+            *reinterpret_cast<uint2*>(bt + sw128_word_off(nre, 2 * lane, kMaxNpad)) = make_uint2(xh, yh ^ sgn);
+            *reinterpret_cast<uint2*>(bt + sw128_word_off(nim, 2 * lane, kMaxNpad)) = make_uint2(yh, xh);
+            *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + sw128_word_off(nre, 2 * lane, kMaxNpad)) =
+                make_uint2(xl, yl ^ sgn);
+            *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + sw128_word_off(nim, 2 * lane, kMaxNpad)) =
+                make_uint2(yl, xl);
           }
         }
-        // A operand (TMEM): this row's Khatri-Rao values x~B * C for 8 centres
-        // x~B and C of this row for the quarter's eight centres (contiguous in the slot rows)
+        // A operand (TMEM): this row's Khatri-Rao values x~B * C for the warp's eight centres
         float2 xbv[kQuarter], cvv[kQuarter];
-        {
-          const float4* b4 = reinterpret_cast<const float4*>(st + iB * kCS + quarter * kQuarter);
-          const float4* c4 = reinterpret_cast<const float4*>(st + iC * kCS + quarter * kQuarter);
 #pragma unroll
-          for (int q = 0; q < kQuarter / 2; ++q) {
-            const float4 tb = b4[q], tc = c4[q];
-            xbv[2 * q] = make_float2(tb.x, tb.y);
-            xbv[2 * q + 1] = make_float2(tb.z, tb.w);
-            cvv[2 * q] = make_float2(tc.x, tc.y);
-            cvv[2 * q + 1] = make_float2(tc.z, tc.w);
-          }
+        for (int q = 0; q < 4; ++q) {
+          const float4 tb = *reinterpret_cast<const float4*>(st + offB[q]);
+          const float4 tc = *reinterpret_cast<const float4*>(st + offC[q]);
+          xbv[2 * q] = make_float2(tb.x, tb.y);
+          xbv[2 * q + 1] = make_float2(tb.z, tb.w);
+          cvv[2 * q] = make_float2(tc.x, tc.y);
+          cvv[2 * q + 1] = make_float2(tc.z, tc.w);
         }
-        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + slot * P::kStageCols;
+        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + aslot * P::kStageCols;
         if (PREC == EXT4PCF_SPLIT_BF16) {
           uint32_t w[16];
 #pragma unroll
@@ -463,52 +527,57 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
           tmem_st16(acol + quarter * 16, wh);
           tmem_st16(acol + 64 + quarter * 16, wl);
         }
-        fence_async_smem();
+        // every value this warp loaded from the staged input has been used (the stores above
+        // read the products): the staged stage can be refilled
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&in_empty[islot]);
         tmem_wait_st();
+        fence_async_smem();
         tc_fence_before();
-        mbar_arrive(&full[slot]);
-        if (++slot == kSt) { slot = 0; ph ^= 1u; }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ab_full[aslot]);
         // a partial sum finished one promotion block ago is read while the MMAs run on
         if ((k % kPromote) == kPromote - 1 && k / kPromote >= 1) promote(gs0 + k / kPromote - 1);
       }
-      cp_async_wait<0>();
       // the remaining partial sums of this item: the loop read partials 0 .. F-2
       // (F = complete promotion blocks)
       const int read_in_loop = max(0, nstage / kPromote - 1);
-      for (long long g = gs0 + read_in_loop; g < gs0 + nsub; ++g) promote(g);
+      for (long long gg = gs0 + read_in_loop; gg < gs0 + nsub; ++gg) promote(gg);
       gs = gs0 + nsub;
-      // ------------------------------------------------------------------ epilogue
+      // ---------------------------------------------------------------- epilogue
       if (row_ok) {
-        const size_t nb3 = (size_t)nb2 * nb;
+        const int pr = rr % npairs, nx = 2 * N + 3;
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
           const int n = quarter * 16 + j;
           if (n < ncols) {
-            const int g = n / (2 * nb), b1 = (n >> 1) % nb;
-            const int mu = kr.mu[g];
-            const size_t o = ((((size_t)mu * nn + (n2 + N)) * nn + (n3 + N)) * nb3) + (size_t)b1 * nb2 +
-                             (size_t)b2 * nb + b3;
-            double* p = args.ups + 2 * o;
+            const int ga = n / (2 * nb), b1 = (n >> 1) % nb;
+            const int mu = kr.mu[ga];
+            const size_t o = ((((size_t)mu * nx + (n2 + N + 1)) * nx + (n3 + N + 1)) * nb + b1) * npairs + pr;
+            double* p = args.red + 2 * o;
             p[0] += (double)accD[j];
             p[1] += (double)accD[j + 1];
           }
         }
       }
-      producers_sync();
-    } else {
-      // ------------------------------------------------------------------ MMA issuer
-      if (lane == 0) {
+    }
+  } else if (warp == kWarpMma) {
+    // ---------------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      long long qa = 0, gs = 0;
+      for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+        const KRType kr = kKR[args.items[it].x];
+        const int npad = (2 * kr.nmu * nb + 15) / 16 * 16;
         const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad) : idesc(2u, npad);
-        int slot = (int)(gk % kSt);
-        uint32_t ph = (uint32_t)((gk / kSt) & 1);
-        for (int k = 0; k < nstage; ++k, ++gk) {
-          const long long g = gs + k / kPromote;
-          const int buf = (int)(g & 1);
+        for (int k = 0; k < nstage; ++k, ++qa) {
+          const long long gg = gs + k / kPromote;
+          const int buf = (int)(gg & 1);
           const bool first = (k % kPromote) == 0;
-          if (first && g >= 2) {
-            if (!mbar_wait(&dempty[buf], (uint32_t)(((g >> 1) - 1) & 1), budget)) err = 1;
+          if (first && gg >= 2) {
+            wait(&dempty[buf], (uint32_t)(((gg >> 1) - 1) & 1));
           }
-          if (!mbar_wait(&full[slot], ph, budget)) err = 1;
+          const int slot = (int)(qa % kSt);
+          wait(&ab_full[slot], (uint32_t)((qa / kSt) & 1));
           tc_fence_after();
           const uint32_t d = tmem + buf * kDBuf;
           const uint32_t a0 = tmem + kDCols + slot * P::kStageCols;
@@ -537,18 +606,57 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
               mma_tf32(d, a0 + 64 + q * 8, bh, id, 1u);
             }
           }
-          mma_commit(&empty[slot]);
+          mma_commit(&ab_empty[slot]);
           if ((k % kPromote) == kPromote - 1 || k == nstage - 1) mma_commit(&dfull[buf]);
-          if (++slot == kSt) { slot = 0; ph ^= 1u; }
         }
-      } else {
-        gk += nstage;
+        gs += nsub;
       }
-      gs += nsub;
-      __syncwarp();
+      // every MMA of this CTA has completed before the TMEM is released (also when a wait
+      // above gave up); an MMA always finishes, so this bound is generous
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0u, 4000000000LL)) err = 1;
     }
+    __syncwarp();
+  } else if (warp == kWarpLoad) {
+    // ---------------------------------------------------------------------- TMA loader
+    if (lane == 0) {
+      long long qi = 0;
+      long long last[kMaxInStages];  // last stage whose copies were issued, per slot
+      for (int k = 0; k < kMaxInStages; ++k) last[k] = -1;
+      for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+        const KRType kr = kKR[args.items[it].x];
+        const ItemGeo g = item_geo(args, args.items[it], kr);
+        const RowBlk blk[4] = {g.bx, g.bc, g.ba0, g.ba1};
+        const int srow[4] = {g.sx, g.sc, g.sa0, g.sa1};
+        if (g.sa1 + round8(g.ba1.len) > args.stage_rows) {  // never for the supported shapes
+          *abort_flag = 1;
+          err = 1;
+        }
+        uint32_t boxes = 0;
+        for (int b = 0; b < 4; ++b) boxes += (uint32_t)((blk[b].len + kBoxRows - 1) / kBoxRows);
+        const uint32_t bytes = boxes * 2u * kBoxRows * 128u;
+        for (int k = 0; k < nstage; ++k, ++qi) {
+          const int islot = (int)(qi % S_in);
+          wait(&in_empty[islot], (uint32_t)(((qi / S_in) & 1) ^ 1));
+          if (*abort_flag) continue;  // nothing more is copied once the CTA gives up
+          last[islot] = qi;
+          mbar_expect_tx(&in_full[islot], bytes);
+          unsigned char* st = in_base + (size_t)islot * 2 * half_bytes;
+          for (int b = 0; b < 4; ++b)
+            for (int r = 0; r < blk[b].len; r += kBoxRows)
+              for (int hh = 0; hh < 2; ++hh)
+                tma_load_2d(st + hh * half_bytes + (srow[b] + r) * 128, &tmap, k * kStageCentres + hh * 16,
+                            blk[b].row0 + r, &in_full[islot]);
+        }
+      }
+      // every copy has landed before the shared memory is given up: the phases of a slot
+      // complete in order, so its last issued phase covers the earlier ones (copies always
+      // complete; the bound only guards against the unforeseen)
+      for (int k = 0; k < S_in; ++k)
+        if (last[k] >= 0 && !mbar_wait(&in_full[k], (uint32_t)((last[k] / S_in) & 1), 4000000000LL)) err = 1;
+    }
+    __syncwarp();
   }
-  // drain: the last partial sum was read by the producers, so no MMA is in flight
   if (err) atomicExch(args.status, 1);
   tc_fence_before();
   __syncthreads();
@@ -557,20 +665,41 @@ contract_tc_kernel(const TcArgs args, const float2* __restrict__ xbarr) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-size_t tc_smem_bytes(int nb, int N, int prec) {
+// rows per staged stage and half: the x~B and C blocks of at most the tile's n2 values
+// (128 rows = 128 / pairs values of n2, +2 for misalignment, at most 2N+3) and two A blocks,
+// each rounded up to whole TMA boxes
+int stage_rows_for(int nb, int N) {
+  int rows = 128 / (nb * (nb + 1) / 2) + 2;
+  if (rows > 2 * N + 3) rows = 2 * N + 3;
+  auto r8 = [](int v) { return (v + 7) & ~7; };
+  return 2 * r8(rows * nb) + 2 * r8(nb);
+}
+
+size_t tc_fixed_smem(int prec) {
   const bool x3 = prec == EXT4PCF_3XTF32;
   const int st = x3 ? TcPrec<EXT4PCF_3XTF32>::kStages : 4;
   const int atoms = x3 ? TcPrec<EXT4PCF_3XTF32>::kAtoms : 2;
-  const int sc = stage_values(nb, N);
-  return (size_t)st * atoms * kMaxNpad * 128 + (size_t)kStageBufs * sc * kCS * 8 +
-         (size_t)((sc + 1) & ~1) * 4 + 1024 + 256;
+  return (size_t)st * atoms * kMaxNpad * 128 + 1024 + 512;
+}
+
+// staged-input ring depth that fits next to the B ring (0 if fewer than two stages fit)
+int tc_in_stages(int nb, int N, int prec) {
+  const size_t per = (size_t)stage_rows_for(nb, N) * 256;
+  const size_t room = 227 * 1024 - tc_fixed_smem(prec);
+  int k = (int)(room / per);
+  if (k > kMaxInStages) k = kMaxInStages;
+  return k >= 2 ? k : 0;
+}
+
+size_t tc_smem_bytes(int nb, int N, int prec) {
+  return tc_fixed_smem(prec) + (size_t)tc_in_stages(nb, N, prec) * stage_rows_for(nb, N) * 256;
 }
 
 template <int PREC>
-cudaError_t launch_tc(const TcArgs& a, const float2* xb, size_t smem, int sms, cudaStream_t s) {
+cudaError_t launch_tc(const TcArgs& a, const CUtensorMap& tm, size_t smem, int sms, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  contract_tc_kernel<PREC><<<sms, kThreads, smem, s>>>(a, xb);
+  contract_tc_kernel<PREC><<<sms, kThreads, smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
@@ -578,46 +707,158 @@ cudaError_t launch_tc(const TcArgs& a, const float2* xb, size_t smem, int sms, c
 
 bool tc_supported(const Layout& L, int precision) {
   if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32 && precision != EXT4PCF_3XTF32) return false;
-  return L.nb >= 1 && 4 * L.nb <= kMaxNpad && tc_smem_bytes(L.nb, L.N, precision) <= 227 * 1024;
+  return L.nb >= 1 && 4 * L.nb <= kMaxNpad && tc_in_stages(L.nb, L.N, precision) >= 2;
 }
 
-void tc_build_items(const Layout& L, std::vector<int4>& items) {
+// Work items of the reduced contraction: for every row type t and s = n2 + n3 the rows
+// (n2, Th2 <= Th3) with n2 over the identity range max(-N, s-N) .. min(N, s+N), widened by one
+// at the top (o = +1) or the bottom (o = -1) for the multipoles that the swap map reaches.
+bool tc_build_items(const Layout& L, std::vector<int4>& items) {
   items.clear();
-  const int N = L.N, nb2 = L.nb * L.nb;
-  for (int t = 0; t < kKRTypes; ++t)
+  signed char mup[9], off[9];
+  if (!derive_swap_map(mup, off)) return false;
+  const int N = L.N, npairs = L.nb * (L.nb + 1) / 2;
+  for (int t = 0; t < kKRTypes; ++t) {
+    const int o = type_offset(t, off);
+    if (o < -1 || o > 1) return false;
     for (int s = -2 * N; s <= 2 * N; ++s) {
-      const int lo = s - N > -N ? s - N : -N, hi = s + N < N ? s + N : N;
-      const int rows = (hi - lo + 1) * nb2;
-      for (int r0 = 0; r0 < rows; r0 += 128) items.push_back(make_int4(t, s, r0, rows - r0 < 128 ? rows - r0 : 128));
+      int lo = s - N > -N ? s - N : -N, hi = s + N < N ? s + N : N;
+      if (o > 0) ++hi;
+      if (o < 0) --lo;
+      const int rows = (hi - lo + 1) * npairs;
+      for (int r0 = 0; r0 < rows; r0 += 128)
+        items.push_back(make_int4(t, s, r0, (rows - r0 < 128 ? rows - r0 : 128) | ((lo + 64) << 8)));
     }
+  }
+  return true;
 }
+
+// rows of the transposed wave array (x~B, G, W) and its row pitch in centres
+int tc_wave_rows(const Layout& L) { return (kXBTypes * (2 * L.N + 3) + L.nG + L.nW) * L.nb; }
+int tc_wave_pitch(int T) { return (T + 31) / 32 * 32; }
 
 size_t contract_tc_xb_bytes(const Layout& L, int T) {
-  return (size_t)T * kXBTypes * (2 * L.N + 1) * L.nb * sizeof(float2);
+  return (size_t)tc_wave_rows(L) * tc_wave_pitch(T) * sizeof(float2);
 }
 
-cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, double* ups,
-                             int precision, const int4* items, int n_items, float2* xb, int* status,
+size_t tc_reduced_doubles(const Layout& L) {
+  const size_t nx = 2 * L.N + 3;
+  return (size_t)2 * 9 * nx * nx * L.nb * (L.nb * (L.nb + 1) / 2);
+}
+
+namespace {
+struct SwapArgs {
+  signed char mup[9], off[9];
+};
+// Every ordered triple at |n2|, |n3| <= N from the reduced array: Th2 <= Th3 directly, the
+// others through the swap map.  One thread per output complex value, accumulated into ups.
+__global__ void tc_expand_kernel(const Layout L, const SwapArgs sw, const double* __restrict__ red,
+                                 double* __restrict__ ups) {
+  const int N = L.N, nb = L.nb, nn = 2 * N + 1, nx = 2 * N + 3, npairs = nb * (nb + 1) / 2;
+  const size_t nb3 = (size_t)nb * nb * nb, total = (size_t)9 * nn * nn * nb3;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b3 = (int)(e % nb), b2 = (int)((e / nb) % nb), b1 = (int)((e / ((size_t)nb * nb)) % nb);
+    const size_t r = e / nb3;
+    const int n3 = (int)(r % nn) - N, n2 = (int)((r / nn) % nn) - N, mu = (int)(r / ((size_t)nn * nn));
+    int m = mu, m2 = n2, m3 = n3, p2 = b2, p3 = b3;
+    if (b2 > b3) {
+      m = sw.mup[mu];
+      m2 = n3 + sw.off[mu];
+      m3 = n2 - sw.off[mu];
+      p2 = b3;
+      p3 = b2;
+    }
+    const int pr = p2 * nb - p2 * (p2 - 1) / 2 + (p3 - p2);
+    const size_t o = ((((size_t)m * nx + (m2 + N + 1)) * nx + (m3 + N + 1)) * nb + b1) * npairs + pr;
+    ups[2 * e] += red[2 * o];
+    ups[2 * e + 1] += red[2 * o + 1];
+  }
+}
+}  // namespace
+
+cudaError_t tc_expand(const Layout& L, const double* red, double* ups, cudaStream_t s) {
+  SwapArgs sw;
+  if (!derive_swap_map(sw.mup, sw.off)) return cudaErrorInvalidValue;
+  const int nn = 2 * L.N + 1;
+  const size_t total = (size_t)9 * nn * nn * L.nb * L.nb * L.nb;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 65536);
+  tc_expand_kernel<<<blocks, 256, 0, s>>>(L, sw, red, ups);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+// mu' and o of every component (ext4pcf_contraction_tables, which = 2): 18 ints
+int contraction_swap_map(int* out) {
+  signed char mup[9], off[9];
+  if (!derive_swap_map(mup, off)) return EXT4PCF_E_UNSUPPORTED;
+  for (int mu = 0; mu < 9; ++mu) {
+    out[2 * mu] = mup[mu];
+    out[2 * mu + 1] = off[mu];
+  }
+  return 18;
+}
+
+namespace {
+// cuTensorMapEncodeTiled from the driver, found once through the runtime (no link to libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+}  // namespace
+
+cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, double* red,
+                             int precision, const int4* items, int n_items, float2* wave, int* status,
                              long long timeout, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
+  const int rows = tc_wave_rows(L), pitch = tc_wave_pitch(T);
+  const int row_g = kXBTypes * (2 * L.N + 3) * L.nb, row_w = row_g + L.nG * L.nb;
   {
-    const size_t total = (size_t)T * kXBTypes * (2 * L.N + 1) * L.nb;
-    const int blocks = (int)std::min<size_t>((total + 255) / 256, 65536);
-    xb_kernel<<<blocks, 256, 0, s>>>(L, rec, xw, T, xb);
+    dim3 grid((rows + 31) / 32, (T + 31) / 32);
+    transpose_wave_kernel<<<grid, 256, 0, s>>>(L, rec, xw, T, pitch, row_g, row_w, rows, wave);
     ++g_launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  // 2D view: x = centre (T of them, pitch elements per row), y = row; boxes of 16 centres
+  // (128 bytes, the swizzle span) by 8 rows; centres past T read as zero
+  CUtensorMap tm;
+  const cuuint64_t dims[2] = {(cuuint64_t)T, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float2)};
+  const cuuint32_t box[2] = {16, (cuuint32_t)kBoxRows};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, wave, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   TcArgs a;
-  a.L = L; a.rec = rec; a.xw = xw; a.T = T; a.ups = ups;
+  a.L = L; a.T = T; a.red = red;
+  a.npairs = L.nb * (L.nb + 1) / 2;
   a.items = items; a.n_items = n_items;
+  a.row_g = row_g; a.row_w = row_w;
+  a.in_stages = tc_in_stages(L.nb, L.N, precision);
+  a.stage_rows = stage_rows_for(L.nb, L.N);
   a.timeout = timeout; a.status = status;
+  if (a.in_stages < 2) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t smem = tc_smem_bytes(L.nb, L.N, precision);
   cudaError_t e;
-  if (precision == EXT4PCF_SPLIT_BF16) e = launch_tc<EXT4PCF_SPLIT_BF16>(a, xb, smem, sms, s);
-  else if (precision == EXT4PCF_TF32) e = launch_tc<EXT4PCF_TF32>(a, xb, smem, sms, s);
-  else e = launch_tc<EXT4PCF_3XTF32>(a, xb, smem, sms, s);
+  if (precision == EXT4PCF_SPLIT_BF16) e = launch_tc<EXT4PCF_SPLIT_BF16>(a, tm, smem, sms, s);
+  else if (precision == EXT4PCF_TF32) e = launch_tc<EXT4PCF_TF32>(a, tm, smem, sms, s);
+  else e = launch_tc<EXT4PCF_3XTF32>(a, tm, smem, sms, s);
   ++g_launches;
   return e;
 }

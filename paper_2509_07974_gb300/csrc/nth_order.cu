@@ -21,6 +21,7 @@
 namespace ext4pcf {
 int contraction_table_cc(int* out);
 int contraction_table_tc(int* out);
+int contraction_swap_map(int* out);
 }  // namespace ext4pcf
 
 namespace {
@@ -110,10 +111,11 @@ int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap) {
 }
 
 int ext4pcf_contraction_tables(int which, int* table, int cap) {
-  const int size = 9 * (2 + 3 * 5);
-  if (which != 0 && which != 1) return EXT4PCF_E_INVALID_ARG;
+  if (which < 0 || which > 2) return EXT4PCF_E_INVALID_ARG;
+  const int size = which == 2 ? 18 : 9 * (2 + 3 * 5);
   if (!table) return size;
   if (cap < size) return EXT4PCF_E_INVALID_ARG;
+  if (which == 2) return ext4pcf::contraction_swap_map(table);
   return which == 0 ? ext4pcf::contraction_table_cc(table) : ext4pcf::contraction_table_tc(table);
 }
 

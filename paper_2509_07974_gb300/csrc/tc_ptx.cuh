@@ -39,6 +39,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long lon
   }
   return true;
 }
+// arrive on an mbarrier and add `bytes` to the transaction count its phase waits for
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+// 2D tiled TMA load of one box of the tensor map at element coordinates (x, y) into shared
+// memory; completion is signalled on `bar` as transaction bytes (x * element size must be a
+// multiple of 16 bytes)
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -109,10 +126,17 @@ __device__ __forceinline__ uint32_t sw128_word_off(int n, int j, int npad) {
 }
 
 
-// tf32 hi/lo split: hi keeps sign, exponent and 10 mantissa bits; lo = x - hi is exact
+// tf32 hi/lo split: hi is x rounded to the nearest tf32 value (10 mantissa bits), lo = x - hi
+// is exact in FP32 and |lo| <= 2^-11 |x|; the tensor core reads lo to 10 bits, so hi + lo
+// carries x to about 2^-22 relative (truncating hi instead leaves |lo| up to 2^-10 |x| and
+// four times the error)
+// Rounding: adding half a tf32 unit (bit 12) to the magnitude bits before clearing the low 13
+// bits rounds to nearest, ties away from zero (a carry into the exponent gives the next binade);
+// two integer instructions, no conversion unit.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  hi = __float_as_uint(x) & 0xFFFFE000u;
-  lo = __float_as_uint(x - __uint_as_float(hi));
+  const uint32_t h = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+  hi = h;
+  lo = __float_as_uint(x - __uint_as_float(h));
 }
 
 }  // namespace

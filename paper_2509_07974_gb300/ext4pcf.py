@@ -198,13 +198,15 @@ def ext4pcf_nth_order_factors(order, mu):
 
 
 def ext4pcf_contraction_tables(which):
-    """The 4PCF contraction kernels' own factor tables (0 CUDA-core, 1 tensor-core), int32 [9][17]."""
+    """The 4PCF contraction kernels' own factor tables (0 CUDA-core, 1 tensor-core), int32 [9][17];
+    which = 2: the Theta2 <-> Theta3 map of the reduced tensor-core contraction, int32 [9][2]
+    (mu', o per component)."""
     import numpy as np
     lib = load()
     n = _host_table(lib.ext4pcf_contraction_tables(int(which), None, 0))
     t = np.zeros(n, dtype=np.int32)
     _host_table(lib.ext4pcf_contraction_tables(int(which), t.ctypes.data, t.size))
-    return t.reshape(9, 17)
+    return t.reshape(9, 2) if int(which) == 2 else t.reshape(9, 17)
 
 
 def aperture_lattice(field, theta, spacing):

@@ -68,7 +68,7 @@ def test_invalid_arguments(lib):
         with pytest.raises(Ext4pcfError):
             lib.ext4pcf_nth_order_factors(order, mu)
     with pytest.raises(Ext4pcfError):
-        lib.ext4pcf_contraction_tables(2)
+        lib.ext4pcf_contraction_tables(3)
 
 
 def evaluate(order, tables, pos, shear, w, edges, nmax):
@@ -123,3 +123,17 @@ def test_generated_tables_give_the_brute_force_multipoles(lib, order, n, side, e
     ref = oracle.bruteforce_multipoles(order, pos, sh, w, np.array(edges), nmax)
     assert got.shape == ref.shape and np.abs(ref).max() > 0
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_tensor_core_swap_map_is_the_papers_symmetry_table():
+    """The Theta2 <-> Theta3 map that the reduced tensor-core contraction derives from its own
+    factor table equals the column (Theta1, Theta3, Theta2) of Table tab:4PCFSymm in the oracle:
+    Upsilon_mu[n2, n3](b1, b2, b3) = Upsilon_mu'[n3 + o, n2 - o](b1, b3, b2)."""
+    from oracle import symmetry
+    from paper_2509_07974_gb300 import ext4pcf
+    m = ext4pcf.ext4pcf_contraction_tables(2)
+    col = symmetry.BIN_PERM.index((0, 2, 1))
+    for mu in range(9):
+        assert m[mu, 0] == symmetry.MU_MAP[mu][col]
+        for n2, n3 in ((0, 0), (3, -2), (-4, 1)):
+            assert symmetry.n_map(mu, col, n2, n3) == (n3 + m[mu, 1], n2 - m[mu, 1])
