@@ -447,13 +447,16 @@ def run_ours(args):
     g_ms = bd["ms_gather"] / waves
     g_ach = flop_pair * pairs / waves / (g_ms / 1e3) / 1e12
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    tc_form = args.precision in ("tf32", "3xtf32", "bf16x3")
+    tc_form = args.precision in ("tf32", "3xtf32", "bf16x3", "f16x3")
     c_flop_full = contraction_flop(bd["centres"], nmax, nb)
     c_flop = reduced_contraction_flop(bd["centres"], nmax, nb) if tc_form else c_flop_full
     c_ms = bd["ms_contract"] / waves
     contraction_tflops = c_flop / (bd["ms_contract"] / 1e3) / 1e12 if bd["ms_contract"] > 0 else None
-    passes = {"3xtf32": 3, "bf16x3": 3, "tf32": 1}.get(args.precision, 1)
-    tf32_peak = pk.get("bf16_tflops_sustained", 1700.0) * 1.1 / 2.25
+    passes = {"3xtf32": 3, "bf16x3": 3, "f16x3": 3, "tf32": 1}.get(args.precision, 1)
+    # the tensor rate of the contraction's operand type: kind::f16 (fp16 / bf16 halves) runs at
+    # the measured bf16 rate, kind::tf32 at that rate times the nominal ratio 1.1/2.25
+    f16_kind = args.precision in ("f16x3", "bf16x3")
+    tf32_peak = pk.get("bf16_tflops_sustained", 1700.0) * (1.0 if f16_kind else 1.1 / 2.25)
     roof_g = {"bound": "alu", "kernel": "gather", "achieved": g_ach, "peak": fp32_peak, "unit": "TFLOP/s",
               "frac": g_ach / fp32_peak, "traffic": None, "ms_per_launch": g_ms,
               "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock (%s MHz)"
@@ -464,8 +467,10 @@ def run_ours(args):
               "ms_per_launch": c_ms,
               "frac_issued": (contraction_tflops or 0.0) * passes / tf32_peak,
               "passes": passes,
-              "peak_note": "tf32 dense: measured sustained bf16 (%s TFLOP/s, %s) x the nominal ratio 1.1/2.25 "
-                           "(not a measured tf32 rate)" % (pk.get("bf16_tflops_sustained"), pk.get("source")),
+              "peak_note": ("kind::f16 dense: measured sustained bf16 (%s TFLOP/s, %s)"
+                            % (pk.get("bf16_tflops_sustained"), pk.get("source"))) if f16_kind else
+                           ("tf32 dense: measured sustained bf16 (%s TFLOP/s, %s) x the nominal ratio 1.1/2.25 "
+                            "(not a measured tf32 rate)" % (pk.get("bf16_tflops_sustained"), pk.get("source"))),
               "algorithmic_flop_per_centre": c_flop / max(1, bd["centres"]),
               "algorithmic_note": ("complex multiply-adds of the symmetry-reduced contraction (bin pairs "
                                    "Theta2 <= Theta3); all ordered triples would be %.4g FLOP per centre, "
@@ -555,7 +560,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="3xtf32", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3"])
+    ap.add_argument("--precision", default="3xtf32", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3", "f16x3"])
     ap.add_argument("--oracle-centres", type=int, default=2000)
     ap.add_argument("--fp64-centres", type=int, default=4096)
     ap.add_argument("--no-baselines", action="store_true")

@@ -21,8 +21,15 @@
  *    scratch memory (grown on demand, released by ext4pcf_destroy).
  *  - Pointers documented as "device or host" may point to either; host buffers are copied
  *    to the device inside the call (and host outputs copied back), which makes the call
- *    synchronous.  Device-only calls are stream-ordered on the configured stream and
- *    return after enqueueing unless `stats` is requested (then they synchronise).
+ *    synchronous.  ext4pcf_measure and ext4pcf_measure3 with device pointers (and no
+ *    `stats`) are stream-ordered on the configured stream and return after enqueueing: the
+ *    cell grid is chosen on the device and no value is read back.  A bounded device-side wait
+ *    that ran out, or positions that are not all finite, are recorded in the context's status
+ *    word and reported (EXT4PCF_E_TIMEOUT, EXT4PCF_E_INVALID_ARG) by the next call that
+ *    synchronises: ext4pcf_synchronize, or ext4pcf_measure with `stats` or host outputs.
+ *    Scratch buffers grow on the first call of a size, and tensor-core work tables are
+ *    uploaded on the first call of an (n_bins, n_max): both synchronise, so make one such
+ *    call before capturing the stream into a CUDA graph.
  *  - Errors: every entry point returns EXT4PCF_OK (0) or a negative code; no exception
  *    crosses the ABI.  ext4pcf_last_error() gives a message for the last failure.  A
  *    context may be used by one host thread at a time.
@@ -59,18 +66,26 @@ typedef enum {
   EXT4PCF_FP32 = 1,      /* FP32 gather and contraction, FP64 accumulation across waves */
   EXT4PCF_TF32 = 2,      /* FP32 gather, tensor-core contraction (tcgen05 kind::tf32) */
   EXT4PCF_3XTF32 = 3,    /* as TF32 with hi/lo split operands, three passes */
-  EXT4PCF_SPLIT_BF16 = 4 /* tensor-core contraction (kind::f16, bf16 hi/lo, three passes) */
+  EXT4PCF_SPLIT_BF16 = 4,/* tensor-core contraction (kind::f16, bf16 hi/lo, three passes) */
+  EXT4PCF_SPLIT_F16 = 5  /* kind::f16 with fp16 hi/lo (22 bits per operand, as 3XTF32), three
+                            passes at twice the tf32 rate; every staged row and column is
+                            scaled by a power of two so that its largest value over the wave
+                            maps to 2^14 (fp16 range), and the scale is undone exactly */
 } ext4pcf_precision;
 
 typedef struct {
   int device;              /* CUDA device ordinal */
   void* stream;            /* cudaStream_t to enqueue on (NULL = legacy default stream) */
   int precision;           /* ext4pcf_precision */
-  int autotune;            /* 1: pick wave / tile shapes by timing on first use */
-  int64_t workspace_bytes; /* soft cap on context scratch (0 = no cap) */
+  int autotune;            /* 1: the first measure call of an (precision, n_max, n_bins) times its
+                              first waves at 2048, 4096, 8192 and 16384 centres and keeps the
+                              fastest per centre for the context (those waves synchronise; needs
+                              no centre mask and enough centres, else the default is kept) */
+  int64_t workspace_bytes; /* cap on the per-wave scratch of ext4pcf_measure (records, staging):
+                              the wave shrinks by halves to fit; 0 = no cap */
   int64_t timeout_cycles;  /* bound on every device-side wait (0 = default) */
   int deterministic;       /* 1: fixed summation order (always honoured at present) */
-  int wave_centres;        /* centres per contraction wave (0 = automatic) */
+  int wave_centres;        /* centres per contraction wave (0 = autotuned or 8192, 4096 for FP64) */
 } ext4pcf_config;
 
 typedef struct {
@@ -79,6 +94,7 @@ typedef struct {
   int64_t waves;   /* contraction waves launched */
   int64_t launches; /* kernels launched by the call */
   double ms_grid, ms_gather, ms_contract, ms_correct, ms_total; /* CUDA-event times */
+  int64_t wave_centres; /* wave size of the call's last catalogue (after any autotuning) */
 } ext4pcf_stats;
 
 /* Create a context on cfg->device.  Fails with EXT4PCF_E_UNSUPPORTED unless the device is
@@ -87,6 +103,12 @@ EXT4PCF_API int ext4pcf_create(ext4pcf_ctx** out, const ext4pcf_config* cfg);
 
 /* Release the context and all its scratch memory (synchronises its stream). */
 EXT4PCF_API int ext4pcf_destroy(ext4pcf_ctx* ctx);
+
+/* Wait for the work enqueued on the context's stream and report what its status word
+ * recorded since it was last read (then clear it): EXT4PCF_OK, EXT4PCF_E_TIMEOUT (a bounded
+ * device-side wait in the tensor-core contraction ran out; that call's results are not
+ * valid), EXT4PCF_E_INVALID_ARG (positions that were not all finite), or EXT4PCF_E_CUDA. */
+EXT4PCF_API int ext4pcf_synchronize(ext4pcf_ctx* ctx);
 
 /* Multipoles of the shear 4PCF (paper Sect. 3.1 and App. A.1).
  * For every centre galaxy i and radial bin Theta, the neighbour multipoles
@@ -101,7 +123,7 @@ EXT4PCF_API int ext4pcf_destroy(ext4pcf_ctx* ctx);
  *   weights     device or host, double [n_gal]
  *   n_gal       total galaxies over all catalogues (>= 0)
  *   radial_bins host, double [n_bins+1], strictly increasing, radial_bins[0] > 0
- *   n_bins      1..32 (1..16 for the tensor-core precisions TF32, 3XTF32 and SPLIT_BF16, whose
+ *   n_bins      1..32 (1..16 for the tensor-core precisions TF32, 3XTF32, SPLIT_BF16 and SPLIT_F16, whose
  *               B tile holds at most 64 columns, 4 per bin; larger n_bins return
  *               EXT4PCF_E_UNSUPPORTED before any work);  n_max >= 0 (<= 40)
  *   cat_offsets host, int64 [n_cat+1] or NULL: catalogue k is galaxies
@@ -237,7 +259,7 @@ EXT4PCF_API int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap
  *   radial_bins  host [n_bins+1] as for ext4pcf_measure;  n_bins 1..32;  n_max 0..40
  *   upsilon3     device, double [5][2 n_max + 1][n_bins][n_bins][2] (index 4 the
  *                normalisation; axes n + n_max, Theta1, Theta2), accumulated into
- * Stream-ordered after one synchronisation (the catalogue's bounding box).  Waves hold
+ * Stream-ordered, returns after enqueueing (see the conventions above).  Waves hold
  * ext4pcf_config.wave_centres centres (0: 4096).  Returns EXT4PCF_OK, EXT4PCF_E_INVALID_ARG
  * (including host pointers), EXT4PCF_E_OOM, EXT4PCF_E_CUDA, or EXT4PCF_E_UNSUPPORTED when a
  * factor index of the generated order-3 tables falls outside the gathered multipole range

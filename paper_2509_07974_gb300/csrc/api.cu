@@ -3,6 +3,8 @@
 // correction application.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -60,6 +62,12 @@ __global__ void iota(int* a, int n) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) a[p] = p;
 }
+// status bits: 1 a bounded device-side wait ran out, 2 non-finite positions
+int status_code(int st) {
+  if (st & 1) return EXT4PCF_E_TIMEOUT;
+  if (st & 2) return EXT4PCF_E_INVALID_ARG;
+  return EXT4PCF_OK;
+}
 
 }  // namespace
 
@@ -79,11 +87,14 @@ struct ext4pcf_ctx {
   // direct aperture estimator: centres, per-split sums, staged outputs
   DBuf ap_cen, ap_sums, io_rec, io_mom;
   // tensor-core contraction: work items (built once per shape) and the device status word
-  DBuf tc_items, tc_xb, tc_red, status;
+  DBuf tc_items, tc_xb, tc_red, tc_rowmax, status, geom;
   int tc_N = -1, tc_nb = -1;
   size_t tc_items_bytes = 0;
   cudaEvent_t ev[8] = {};
   std::vector<cudaEvent_t> tev;  // per-phase timing events of one measure call (grown on demand)
+  // wave sizes chosen by the autotuner, per (precision, n_max, n_bins)
+  std::map<std::tuple<int, int, int>, int> tuned;
+  int64_t last_wave = 0;
 };
 
 namespace {
@@ -146,15 +157,17 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// cell side: about a eighth of the largest separation, at most ~4000 cells per axis, and
-// with 12 significant bits so that (cell index) * cell is exact in float
-double choose_cell(double rmax, double extent) {
-  double c = rmax / 8.0;
-  if (extent / 4000.0 > c) c = extent / 4000.0;
-  int ex;
-  double m = std::frexp(c, &ex);          // c = m 2^ex, m in [0.5, 1)
-  m = std::floor(m * 4096.0) / 4096.0;    // 12 significant bits
-  return std::ldexp(m, ex);
+// synchronise the context's stream and read (and clear) its status word; *code receives
+// the status as an error code
+int read_status(ext4pcf_ctx* ctx, int* code) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->status.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st != 0) CK(cudaMemsetAsync(ctx->status.p, 0, 4, ctx->stream));
+  *code = status_code(st);
+  if (*code == EXT4PCF_E_TIMEOUT) fail(ctx, *code, "a bounded device-side wait expired in the contraction");
+  else if (*code != EXT4PCF_OK) fail(ctx, *code, "non-finite positions");
+  return EXT4PCF_OK;
 }
 
 }  // namespace
@@ -174,13 +187,21 @@ int ext4pcf_create(ext4pcf_ctx** out, const ext4pcf_config* cfg) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, cfg->device) != cudaSuccess) return EXT4PCF_E_CUDA;
   if (!(prop.major == 10 && prop.minor == 3)) return EXT4PCF_E_UNSUPPORTED;
-  if (cfg->precision < EXT4PCF_FP64 || cfg->precision > EXT4PCF_SPLIT_BF16) return EXT4PCF_E_INVALID_ARG;
+  if (cfg->precision < EXT4PCF_FP64 || cfg->precision > EXT4PCF_SPLIT_F16) return EXT4PCF_E_INVALID_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) return EXT4PCF_E_CUDA;
   ext4pcf_ctx* ctx = new ext4pcf_ctx;
   ctx->cfg = *cfg;
   ctx->stream = static_cast<cudaStream_t>(cfg->stream);
   ctx->sm_count = prop.multiProcessorCount;
   for (auto& e : ctx->ev) cudaEventCreate(&e);
+  // the status word (bits of status_code) accumulates until a synchronising call reads it
+  if (cudaMalloc(&ctx->status.p, 16) != cudaSuccess || cudaMemset(ctx->status.p, 0, 16) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->status.p) cudaFree(ctx->status.p);
+    delete ctx;
+    return EXT4PCF_E_OOM;
+  }
+  ctx->status.bytes = 16;
   *out = ctx;
   return EXT4PCF_OK;
 }
@@ -194,7 +215,7 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
                  &ctx->px, &ctx->py, &ctx->xr, &ctx->xi, &ctx->w, &ctx->p4, &ctx->s4, &ctx->bbox,
                  &ctx->centres, &ctx->flags, &ctx->rec, &ctx->xw, &ctx->corr, &ctx->counter, &ctx->ncen,
                  &ctx->t_norm, &ctx->t_gam, &ctx->t_E, &ctx->t_part, &ctx->t_small, &ctx->tc_items,
-                 &ctx->tc_xb, &ctx->tc_red, &ctx->status, &ctx->ap_cen, &ctx->ap_sums, &ctx->io_rec, &ctx->io_mom};
+                 &ctx->tc_xb, &ctx->tc_red, &ctx->tc_rowmax, &ctx->status, &ctx->geom, &ctx->ap_cen, &ctx->ap_sums, &ctx->io_rec, &ctx->io_mom};
   for (DBuf* b : all)
     if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
@@ -206,6 +227,15 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
 }
 
 const char* ext4pcf_last_error(const ext4pcf_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int ext4pcf_synchronize(ext4pcf_ctx* ctx) {
+  if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  ctx->err.clear();
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = EXT4PCF_OK;
+  const int r = read_status(ctx, &rc);
+  return r != EXT4PCF_OK ? r : rc;
+}
 
 int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* shears,
                     const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
@@ -316,7 +346,8 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   int t_grid0 = -1;
   ENSURE(ctx->counter, 16);
   CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
-  const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16 || prec == EXT4PCF_3XTF32;
+  const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16 || prec == EXT4PCF_3XTF32 ||
+                  prec == EXT4PCF_SPLIT_F16;
   if (tc) {
     if (ctx->tc_N != n_max || ctx->tc_nb != n_bins) {
       std::vector<int4> items;
@@ -327,12 +358,13 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       ctx->tc_N = n_max;
       ctx->tc_nb = n_bins;
     }
-    ENSURE(ctx->status, 16);
-    CK(cudaMemsetAsync(ctx->status.p, 0, 4, s));
   }
   const long long timeout = ctx->cfg.timeout_cycles > 0 ? ctx->cfg.timeout_cycles : 20000000000LL;
-  ENSURE(ctx->ncen, 16);
+  ENSURE(ctx->ncen, (size_t)(n_cat + 1) * sizeof(int));
   ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
+  ENSURE(ctx->geom, sizeof(GridGeom));
+  ENSURE(ctx->cell_start, ((size_t)kMaxCellsPerAxis * kMaxCellsPerAxis + 1) * 4);
+  if (centre_mask) CK(cudaMemsetAsync(ctx->ncen.p, 0, (size_t)(n_cat + 1) * sizeof(int), s));
 
   for (int k = 0; k < n_cat; ++k) {
     const int64_t c0 = cat_offsets ? cat_offsets[k] : 0;
@@ -345,22 +377,11 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     const double* w_k = d_w + c0;
     const uint8_t* mask_k = d_mask ? d_mask + c0 : nullptr;
     if (timing) t_grid0 = tmark();
-    // ---- grid
+    // ---- grid, chosen on the device from the bounding box (no host round trip)
     CK(grid_bbox(pos_k, nk, (double*)ctx->bbox.p, s));
-    double bb[4];
-    CK(cudaMemcpyAsync(bb, ctx->bbox.p, 32, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (!std::isfinite(bb[0]) || !std::isfinite(bb[1]) || !std::isfinite(bb[2]) || !std::isfinite(bb[3]))
-      return fail(ctx, EXT4PCF_E_INVALID_ARG, "non-finite positions");
-    const double extent = std::fmax(bb[2] - bb[0], bb[3] - bb[1]);
-    const double cell = choose_cell(bins.rmax, extent);
-    const int ncx = (int)std::floor((bb[2] - bb[0]) / cell) + 1;
-    const int ncy = (int)std::floor((bb[3] - bb[1]) / cell) + 1;
-    const size_t ncells = (size_t)ncx * ncy;
     const int ntiles = (nk + 2047) / 2048;
     ENSURE(ctx->keys, (size_t)nk * 4); ENSURE(ctx->keys_alt, (size_t)nk * 4);
     ENSURE(ctx->perm, (size_t)nk * 4); ENSURE(ctx->perm_alt, (size_t)nk * 4);
-    ENSURE(ctx->cell_start, (ncells + 1) * 4);
     ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
     ENSURE(ctx->px, (size_t)nk * 8); ENSURE(ctx->py, (size_t)nk * 8);
     ENSURE(ctx->xr, (size_t)nk * 8); ENSURE(ctx->xi, (size_t)nk * 8); ENSURE(ctx->w, (size_t)nk * 8);
@@ -368,16 +389,18 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     GridBuffers gb;
     gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
     gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
-    gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ncells + 1;
+    gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ctx->cell_start.bytes / 4;
     gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
     gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
     gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
     gb.p4 = (float4*)ctx->p4.p; gb.s4 = (float4*)ctx->s4.p; gb.bbox = (double*)ctx->bbox.p;
     SortedCat cat;
-    CK(grid_sort(pos_k, sh_k, w_k, nk, bb[0], bb[1], cell, ncx, ncy, !f64, gb, cat, s));
-    // ---- centre list (sorted positions of the centres)
+    CK(grid_sort_device(pos_k, sh_k, w_k, nk, (const double*)ctx->bbox.p, bins.rmax, (GridGeom*)ctx->geom.p, !f64,
+                        gb, cat, (int*)ctx->status.p, s));
+    // ---- centre list (sorted positions of the centres); with a mask their number stays on
+    // the device (n_live) and the waves cover every galaxy, those past it doing nothing
     ENSURE(ctx->centres, (size_t)nk * 4);
-    int n_cen = nk;
+    const int* n_live = nullptr;
     if (mask_k) {
       ENSURE(ctx->flags, ((size_t)nk + (size_t)nk / 1000 + 4096) * 4);
       unsigned* flag = (unsigned*)ctx->flags.p;
@@ -386,26 +409,61 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       unsigned* tmp = (unsigned*)ctx->hist.p;  // reuse as scan scratch
       CK(scan_exclusive(flag, (size_t)nk, tmp, s));
       mask_compact<<<(nk + 255) / 256, 256, 0, s>>>(flag, mask_k, cat.perm, nk, (int*)ctx->centres.p,
-                                                   (int*)ctx->ncen.p);
+                                                   (int*)ctx->ncen.p + k);
       CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(&n_cen, ctx->ncen.p, 4, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      n_live = (const int*)ctx->ncen.p + k;
     } else {
       iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
       ++g_launches;
       CK(cudaGetLastError());
+      tot_centres += nk;
     }
-    tot_centres += n_cen;
+    const int n_cen = nk;  // waves cover at most this many centres
     if (timing) marks.push_back({0, t_grid0, tmark()});
     int t_w0 = -1, t_w1 = -1, t_w2 = -1;
-    // ---- waves
+    // ---- waves: size from the configuration, else the autotuner's choice for this shape, else
+    // the default; capped so that the per-wave scratch fits ext4pcf_config.workspace_bytes
     const size_t cbytes = f64 ? sizeof(double2) : sizeof(float2);
-    int T = ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres : (f64 ? 4096 : 8192);
+    auto wave_bytes = [&](int t) -> size_t {
+      size_t b = (size_t)t * L.rec * cbytes + (size_t)t * 2 * cbytes;
+      if (tc) b += contract_tc_xb_bytes(L, t);
+      return b;
+    };
+    const auto key = std::make_tuple(prec, n_max, n_bins);
+    const auto tit = ctx->tuned.find(key);
+    int T = ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres
+            : tit != ctx->tuned.end()  ? tit->second
+                                       : (f64 ? 4096 : 8192);
+    const size_t cap = ctx->cfg.workspace_bytes > 0 ? (size_t)ctx->cfg.workspace_bytes : (size_t)-1;
+    while (T > 32 && wave_bytes(T) > cap) T /= 2;
+    if (wave_bytes(T) > cap) return fail(ctx, EXT4PCF_E_OOM, "workspace_bytes too small for a wave of 32 centres");
+    // autotuning (first call of a shape, no centre mask, enough centres): the first waves take
+    // the candidate sizes in turn -- real waves of the result, so no work is repeated -- and
+    // are timed; the fastest per centre is kept for this shape.  These waves synchronise.
+    std::vector<int> trial;
+    if (ctx->cfg.autotune && ctx->cfg.wave_centres <= 0 && tit == ctx->tuned.end() && !mask_k) {
+      const int cand[4] = {2048, 4096, 8192, 16384};
+      int need = 0;
+      for (int c : cand)
+        if (wave_bytes(c) <= cap) {
+          trial.push_back(c);
+          need += c;
+        }
+      if (trial.empty() || need > n_cen) trial.clear();
+    }
+    int Tmax = T;
+    for (int c : trial) Tmax = std::max(Tmax, c);
+    if (Tmax > n_cen) Tmax = n_cen;
     if (T > n_cen) T = n_cen;
     if (T < 1) T = 1;
-    ENSURE(ctx->rec, (size_t)T * L.rec * cbytes);
-    if (tc) ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, T));
-    ENSURE(ctx->xw, (size_t)T * 2 * cbytes);
+    if (Tmax < T) Tmax = T;
+    ENSURE(ctx->rec, (size_t)Tmax * L.rec * cbytes);
+    if (tc) {
+      ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, Tmax));
+      ENSURE(ctx->tc_rowmax, contract_tc_rowmax_bytes(L));
+    }
+    ENSURE(ctx->xw, (size_t)Tmax * 2 * cbytes);
+    std::vector<float> trial_ms;
     const size_t corr_doubles = corrections_size(L);
     ENSURE(ctx->corr, corr_doubles * 8);
     CK(cudaMemsetAsync(ctx->corr.p, 0, corr_doubles * 8, s));
@@ -414,33 +472,37 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       ENSURE(ctx->tc_red, red_bytes);
       CK(cudaMemsetAsync(ctx->tc_red.p, 0, red_bytes, s));
     }
-    for (int w0 = 0; w0 < n_cen; w0 += T) {
-      const int Tw = std::min(T, n_cen - w0);
+    size_t wave_i = 0;
+    for (int w0 = 0; w0 < n_cen;) {
+      const bool tuning = wave_i < trial.size();
+      const int Tw = std::min(tuning ? trial[wave_i] : T, n_cen - w0);
       const int* cl = (const int*)ctx->centres.p + w0;
+      if (tuning) CK(cudaEventRecord(ctx->ev[1], s));
       if (timing) t_w0 = tmark();
       if (f64) {
-        CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+        CK(gather_wave<double>(cat, bins, L, cl, Tw, n_live, w0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                                (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       } else {
-        CK(gather_wave<float>(cat, bins, L, cl, Tw, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+        CK(gather_wave<float>(cat, bins, L, cl, Tw, n_live, w0, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       }
       if (timing) t_w1 = tmark();
       if (f64) {
-        CK(contract_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, ups_k, s));
+        CK(contract_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, n_live, w0, ups_k, s));
       } else if (prec == EXT4PCF_FP32) {
-        CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, ups_k, s));
+        CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, n_live, w0, ups_k, s));
       } else {
-        CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, (double*)ctx->tc_red.p, prec,
-                            (const int4*)ctx->tc_items.p, (int)(ctx->tc_items_bytes / sizeof(int4)),
-                            (float2*)ctx->tc_xb.p, (int*)ctx->status.p, timeout, s));
+        CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, n_live, w0,
+                            (double*)ctx->tc_red.p, prec, (const int4*)ctx->tc_items.p,
+                            (int)(ctx->tc_items_bytes / sizeof(int4)), (float2*)ctx->tc_xb.p,
+                            (unsigned*)ctx->tc_rowmax.p, (int*)ctx->status.p, timeout, s));
       }
       if (timing) t_w2 = tmark();
       if (f64) {
-        CK(corrections_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw,
+        CK(corrections_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, n_live, w0,
                                     (double*)ctx->corr.p, xi_k, s));
       } else {
-        CK(corrections_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw,
+        CK(corrections_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, n_live, w0,
                                    (double*)ctx->corr.p, xi_k, s));
       }
       if (timing) {
@@ -449,21 +511,39 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
         marks.push_back({2, t_w1, t_w2});
         marks.push_back({3, t_w2, t_w3});
       }
+      if (tuning) {
+        float ms = 0.f;
+        CK(cudaEventRecord(ctx->ev[2], s));
+        CK(cudaEventSynchronize(ctx->ev[2]));
+        CK(cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]));
+        trial_ms.push_back(ms / (float)Tw);
+        if (trial_ms.size() == trial.size()) {
+          size_t best = 0;
+          for (size_t i = 1; i < trial.size(); ++i)
+            if (trial_ms[i] < trial_ms[best]) best = i;
+          T = trial[best];
+          ctx->tuned[key] = T;
+        }
+      }
+      w0 += Tw;
+      ++wave_i;
       ++tot_waves;
     }
+    ctx->last_wave = T;
     if (tc) CK(tc_expand(L, (const double*)ctx->tc_red.p, ups_k, s));
     CK(corrections_apply(L, (const double*)ctx->corr.p, ups_k, s));
 
   }
-  if (tc) {
-    int st = 0;
-    CK(cudaMemcpyAsync(&st, ctx->status.p, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (st != 0) return fail(ctx, EXT4PCF_E_TIMEOUT, "a bounded device-side wait expired in the contraction");
-  }
   if (host_ups) CK(cudaMemcpyAsync(upsilon, d_ups, ups_bytes * n_cat, cudaMemcpyDeviceToHost, s));
   if (host_xi) CK(cudaMemcpyAsync(xi_acc, d_xi, xi_bytes * n_cat, cudaMemcpyDeviceToHost, s));
-  if (host_ups || host_xi) CK(cudaStreamSynchronize(s));
+  // a call that synchronises anyway (host outputs or statistics) reports the status word;
+  // a device-only call returns after enqueueing and leaves it to ext4pcf_synchronize
+  if (host_ups || host_xi || timing) {
+    int rc = EXT4PCF_OK;
+    const int r = read_status(ctx, &rc);
+    if (r != EXT4PCF_OK) return r;
+    if (rc != EXT4PCF_OK) return rc;
+  }
   if (timing) {
     unsigned long long pairs = 0;
     CK(cudaMemcpyAsync(&pairs, ctx->counter.p, 8, cudaMemcpyDeviceToHost, s));
@@ -478,8 +558,15 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       else if (m.kind == 2) ms_contract += t;
       else ms_correct += t;
     }
+    if (centre_mask) {
+      std::vector<int> nc(n_cat);
+      CK(cudaMemcpyAsync(nc.data(), ctx->ncen.p, (size_t)n_cat * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int k = 0; k < n_cat; ++k) tot_centres += nc[k];
+    }
     stats->pairs = (int64_t)pairs;
     stats->centres = tot_centres;
+    stats->wave_centres = ctx->last_wave;
     stats->waves = tot_waves;
     stats->launches = (int64_t)(g_launches - launches0);
     stats->ms_grid = ms_grid;
@@ -606,34 +693,26 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   ENSURE(ctx->counter, 16);
   CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
   ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
+  ENSURE(ctx->geom, sizeof(GridGeom));
   CK(grid_bbox(positions, nk, (double*)ctx->bbox.p, s));
-  double bb[4];
-  CK(cudaMemcpyAsync(bb, ctx->bbox.p, 32, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (!std::isfinite(bb[0]) || !std::isfinite(bb[1]) || !std::isfinite(bb[2]) || !std::isfinite(bb[3]))
-    return fail(ctx, EXT4PCF_E_INVALID_ARG, "non-finite positions");
-  const double extent = std::fmax(bb[2] - bb[0], bb[3] - bb[1]);
-  const double cell = choose_cell(bins.rmax, extent);
-  const int ncx = (int)std::floor((bb[2] - bb[0]) / cell) + 1;
-  const int ncy = (int)std::floor((bb[3] - bb[1]) / cell) + 1;
-  const size_t ncells = (size_t)ncx * ncy;
   const int ntiles = (nk + 2047) / 2048;
   ENSURE(ctx->keys, n * 4); ENSURE(ctx->keys_alt, n * 4);
   ENSURE(ctx->perm, n * 4); ENSURE(ctx->perm_alt, n * 4);
-  ENSURE(ctx->cell_start, (ncells + 1) * 4);
+  ENSURE(ctx->cell_start, ((size_t)kMaxCellsPerAxis * kMaxCellsPerAxis + 1) * 4);
   ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
   ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
   ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
   GridBuffers gb;
   gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
   gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
-  gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ncells + 1;
+  gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ctx->cell_start.bytes / 4;
   gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
   gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
   gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
   gb.p4 = nullptr; gb.s4 = nullptr; gb.bbox = (double*)ctx->bbox.p;
   SortedCat cat;
-  CK(grid_sort(positions, shears, weights, nk, bb[0], bb[1], cell, ncx, ncy, false, gb, cat, s));
+  CK(grid_sort_device(positions, shears, weights, nk, (const double*)ctx->bbox.p, bins.rmax, (GridGeom*)ctx->geom.p,
+                      false, gb, cat, (int*)ctx->status.p, s));
   // ---- every galaxy a centre; waves of FP64 records, contracted with the order-3 tables
   ENSURE(ctx->centres, n * 4);
   iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
@@ -645,7 +724,7 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   for (int w0 = 0; w0 < nk; w0 += T) {
     const int Tw = std::min(T, nk - w0);
     const int* cl = (const int*)ctx->centres.p + w0;
-    CK(gather_wave<double>(cat, bins, L, cl, Tw, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+    CK(gather_wave<double>(cat, bins, L, cl, Tw, nullptr, w0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                            (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
     CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3, s));
   }

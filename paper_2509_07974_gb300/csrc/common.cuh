@@ -77,7 +77,7 @@ struct GridGeom {
   double inv_cell;
   int ncx, ncy;     // cells per axis
   float cellf;
-  int bad;          // 1 if the positions are not all finite
+  int bad;          // 1 if the bounding box is not finite
 };
 // cells per axis never exceed this (the cell side is at least 1/4000 of the extent)
 constexpr int kMaxCellsPerAxis = 4003;
@@ -106,6 +106,14 @@ struct SortedCat {
 // kernels launched by this host thread (each launcher adds what it enqueues)
 extern thread_local long long g_launches;
 
+// Centres of a wave: at most T, and, when the catalogue's centre count is known only on the
+// device (a centre mask), min(T, *n_live - w0) -- a wave past the end has none.
+__device__ __forceinline__ int wave_centres(int T, const int* n_live, int w0) {
+  if (!n_live) return T;
+  const int left = *n_live - w0;
+  return left < T ? (left > 0 ? left : 0) : T;
+}
+
 struct Bins {
   int nb;
   double e2[65];   // squared edges (double)
@@ -133,24 +141,25 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
                       GridBuffers& gb, SortedCat& out, cudaStream_t s);
 // the measure path: the grid chosen on the device from the bounding box d_bbox (written by
 // grid_bbox) for separations up to rmax, then the sort; cell_start must hold
-// kMaxCellsPerAxis^2 + 1 entries
+// kMaxCellsPerAxis^2 + 1 entries; positions that are not finite set bit 1 of *status
 cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n,
                              const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
-                             GridBuffers& gb, SortedCat& out, cudaStream_t s);
+                             GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s);
 
 // gather.cu: per-centre multipole records for centres[c0 .. c0+T) (sorted positions).
+// n_live, w0: see wave_centres
 template <typename R>
 cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
-                        const int* centres, int T, cplx_t<R>* rec, cplx_t<R>* xw,
+                        const int* centres, int T, const int* n_live, int w0, cplx_t<R>* rec, cplx_t<R>* xw,
                         unsigned long long* pair_count, int sm_count, cudaStream_t s);
 
 // contract.cu
 template <typename R>
 cudaError_t contract_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                          double* ups, cudaStream_t s);
+                          const int* n_live, int w0, double* ups, cudaStream_t s);
 template <typename R>
 cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                             double* corr, double* xi_acc, cudaStream_t s);
+                             const int* n_live, int w0, double* corr, double* xi_acc, cudaStream_t s);
 cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, cudaStream_t s);
 size_t corrections_size(const Layout& L);  // doubles
 
@@ -159,9 +168,11 @@ size_t corrections_size(const Layout& L);  // doubles
 // every ordered triple at |n| <= N from it into the output.
 bool tc_supported(const Layout& L, int precision);
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T,
-                             double* red, int precision, const int4* items, int n_items, float2* xb,
-                             int* status, long long timeout, cudaStream_t s);
+                             const int* n_live, int w0, double* red, int precision, const int4* items,
+                             int n_items, float2* xb, unsigned* rowmax, int* status, long long timeout,
+                             cudaStream_t s);
 size_t contract_tc_xb_bytes(const Layout& L, int T);
+size_t contract_tc_rowmax_bytes(const Layout& L);  // per-row maxima of the split-FP16 form
 size_t tc_reduced_doubles(const Layout& L);
 bool tc_build_items(const Layout& L, std::vector<int4>& items);
 cudaError_t tc_expand(const Layout& L, const double* red, double* ups, cudaStream_t s);

@@ -113,8 +113,10 @@ constexpr int contract_threads(int nbt) {
 template <typename R, int NBT>
 __global__ void __launch_bounds__(contract_threads(NBT))
 contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx_t<R>* __restrict__ xw,
-                   int T, double* __restrict__ ups) {
+                   int T, const int* __restrict__ n_live, int w0, double* __restrict__ ups) {
   using Cx = cplx_t<R>;
+  T = wave_centres(T, n_live, w0);
+  if (T == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx* sx = reinterpret_cast<Cx*>(smem_raw);
   Cx* sA = sx + kChunk;
@@ -176,8 +178,11 @@ contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx
 // of the centres), or, for the triple term, threads over the centres.
 template <typename R>
 __global__ void __launch_bounds__(256, 8) corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
-                                   const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ corr) {
+                                   const cplx_t<R>* __restrict__ xw, int T, const int* __restrict__ n_live,
+                                   int w0, double* __restrict__ corr) {
   using Cx = cplx_t<R>;
+  T = wave_centres(T, n_live, w0);
+  if (T == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = L.N, nb = L.nb, nn = 2 * N + 1, ns = 4 * N + 1;
   const int per_mu = 2 * nn + ns;  // index rows of the three double-counting kinds
@@ -305,8 +310,11 @@ __global__ void __launch_bounds__(256, 8) corrections_kernel(const Layout L, con
 // xi accumulators per bin: (sum conj(x) G_0, sum x G_-4, sum w W_0), FP64, fixed order.
 template <typename R>
 __global__ void xi_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
-                          const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ xi) {
+                          const cplx_t<R>* __restrict__ xw, int T, const int* __restrict__ n_live, int w0,
+                          double* __restrict__ xi) {
   __shared__ double red[6][256];
+  T = wave_centres(T, n_live, w0);
+  if (T == 0) return;
   const int b = blockIdx.x, tid = threadIdx.x;
   double v[6] = {0, 0, 0, 0, 0, 0};
   for (int c = tid; c < T; c += blockDim.x) {
@@ -352,14 +360,14 @@ __global__ void apply_corrections(const Layout L, const double* __restrict__ cor
 
 template <typename R, int NBT>
 cudaError_t launch_contract(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                            double* ups, cudaStream_t s) {
+                            const int* n_live, int w0, double* ups, cudaStream_t s) {
   const int nn = 2 * L.N + 1;
   const int threads = contract_threads(NBT);
   const size_t smem = (size_t)kChunk * (1 + 3 * NBT) * sizeof(cplx_t<R>);
   cudaError_t e = cudaFuncSetAttribute(contract_cuda_core<R, NBT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  contract_cuda_core<R, NBT><<<9 * nn * nn, threads, smem, s>>>(L, rec, xw, T, ups);
+  contract_cuda_core<R, NBT><<<9 * nn * nn, threads, smem, s>>>(L, rec, xw, T, n_live, w0, ups);
   ++g_launches;
   return cudaGetLastError();
 }
@@ -368,14 +376,14 @@ cudaError_t launch_contract(const Layout& L, const cplx_t<R>* rec, const cplx_t<
 
 template <typename R>
 cudaError_t contract_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                          double* ups, cudaStream_t s) {
+                          const int* n_live, int w0, double* ups, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
-  if (L.nb <= 4) return launch_contract<R, 4>(L, rec, xw, T, ups, s);
-  if (L.nb <= 8) return launch_contract<R, 8>(L, rec, xw, T, ups, s);
-  if (L.nb <= 12) return launch_contract<R, 12>(L, rec, xw, T, ups, s);
-  if (L.nb <= 16) return launch_contract<R, 16>(L, rec, xw, T, ups, s);
-  if (L.nb <= 24) return launch_contract<R, 24>(L, rec, xw, T, ups, s);
-  if (L.nb <= 32) return launch_contract<R, 32>(L, rec, xw, T, ups, s);
+  if (L.nb <= 4) return launch_contract<R, 4>(L, rec, xw, T, n_live, w0, ups, s);
+  if (L.nb <= 8) return launch_contract<R, 8>(L, rec, xw, T, n_live, w0, ups, s);
+  if (L.nb <= 12) return launch_contract<R, 12>(L, rec, xw, T, n_live, w0, ups, s);
+  if (L.nb <= 16) return launch_contract<R, 16>(L, rec, xw, T, n_live, w0, ups, s);
+  if (L.nb <= 24) return launch_contract<R, 24>(L, rec, xw, T, n_live, w0, ups, s);
+  if (L.nb <= 32) return launch_contract<R, 32>(L, rec, xw, T, n_live, w0, ups, s);
   return cudaErrorInvalidValue;
 }
 
@@ -386,7 +394,7 @@ size_t corrections_size(const Layout& L) {
 
 template <typename R>
 cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                             double* corr, double* xi_acc, cudaStream_t s) {
+                             const int* n_live, int w0, double* corr, double* xi_acc, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
   const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
   const int blocks = 9 * (2 * nn + ns + 1);
@@ -400,10 +408,10 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
                                (size_t)2 * threads * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(corrections_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, T, corr);
+  corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, T, n_live, w0, corr);
   ++g_launches;
   if (xi_acc) {
-    xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, T, xi_acc);
+    xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, T, n_live, w0, xi_acc);
     ++g_launches;
   }
   return cudaGetLastError();
@@ -419,10 +427,14 @@ cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, 
   return cudaGetLastError();
 }
 
-template cudaError_t contract_wave<float>(const Layout&, const float2*, const float2*, int, double*, cudaStream_t);
-template cudaError_t contract_wave<double>(const Layout&, const double2*, const double2*, int, double*, cudaStream_t);
-template cudaError_t corrections_wave<float>(const Layout&, const float2*, const float2*, int, double*, double*, cudaStream_t);
-template cudaError_t corrections_wave<double>(const Layout&, const double2*, const double2*, int, double*, double*, cudaStream_t);
+template cudaError_t contract_wave<float>(const Layout&, const float2*, const float2*, int, const int*, int, double*,
+                                          cudaStream_t);
+template cudaError_t contract_wave<double>(const Layout&, const double2*, const double2*, int, const int*, int, double*,
+                                           cudaStream_t);
+template cudaError_t corrections_wave<float>(const Layout&, const float2*, const float2*, int, const int*, int, double*,
+                                             double*, cudaStream_t);
+template cudaError_t corrections_wave<double>(const Layout&, const double2*, const double2*, int, const int*, int,
+                                              double*, double*, cudaStream_t);
 
 // kComp in the layout of ext4pcf_nth_order_factors at order 4: sign, centre code, then per
 // bin (array, conj, coefficient of n2, coefficient of n3, constant); A reads s = n2 + n3.

@@ -147,12 +147,15 @@ __device__ __forceinline__ void split_bf16(float re, float im, uint32_t& hi, uin
 
 struct TcArgs {
   Layout L;
-  int T;              // centres of the wave
+  int T;              // centres of the wave at most
+  const int* n_live;  // with w0: the wave's centres on the device (wave_centres)
+  int w0;
   double* red;        // reduced output [9][2N+3][2N+3][nb][npairs] (complex, FP64)
   int npairs;         // nb (nb + 1) / 2
   const int4* items;  // (type, s, row0, nrows | (n2 of row 0 of the s block + 64) << 8)
   int n_items;
   int row_g, row_w;   // first row of G and of W in the transposed wave array (x~B rows from 0)
+  const unsigned* rowmax;  // split-FP16 form: largest |component| of every staged row (float bits)
   int in_stages;      // depth of the staged-input ring
   int stage_rows;     // rows per staged stage and half (multiple of 8)
   long long timeout;
@@ -191,12 +194,17 @@ __device__ __forceinline__ float2 wave_value(const Layout& L, const float2* __re
 
 // 32 rows x 32 centres per block through shared memory: reads along each centre's record,
 // writes along the centres of each row (both coalesced)
+// Centres from the wave's count up to the next multiple of 32 are written as zeros (the last
+// stage of the contraction reads them); columns beyond are never read.
 __global__ void __launch_bounds__(256) transpose_wave_kernel(const Layout L, const float2* __restrict__ rec,
-                                                             const float2* __restrict__ xw, int T, int Tp,
+                                                             const float2* __restrict__ xw, int T,
+                                                             const int* __restrict__ n_live, int w0, int Tp,
                                                              int row_g, int row_w, int rows,
-                                                             float2* __restrict__ out) {
+                                                             float2* __restrict__ out, unsigned* __restrict__ rowmax) {
   __shared__ float2 tile[32][33];
   const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  T = wave_centres(T, n_live, w0);
+  if (c0 >= T) return;  // whole column tiles past the wave (uniform per block)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -210,9 +218,37 @@ __global__ void __launch_bounds__(256) transpose_wave_kernel(const Layout L, con
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int r = r0 + ty + 8 * k, c = c0 + tx;
-    if (r < rows && c < T) out[(size_t)r * Tp + c] = tile[tx][ty + 8 * k];
+    if (r < rows && c < Tp) out[(size_t)r * Tp + c] = tile[tx][ty + 8 * k];
+  }
+  // largest |component| of every row over the wave (non-negative floats order as integers)
+  if (rowmax && ty == 0 && r0 + tx < rows) {
+    float m = 0.f;
+    for (int c = 0; c < 32; ++c) m = fmaxf(m, fmaxf(fabsf(tile[c][tx].x), fabsf(tile[c][tx].y)));
+    if (m > 0.f) atomicMax(&rowmax[r0 + tx], __float_as_uint(m));
   }
 }
+
+// fp16 hi/lo split of a pair (re, im) packed as f16x2 (re in the low half); the values are
+// scaled into the fp16 range by the caller
+__device__ __forceinline__ void split_f16(float re, float im, uint32_t& hi, uint32_t& lo) {
+  uint32_t h;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(im), "f"(re));
+  float hr, hm;
+  asm("{\n .reg .b16 a, b;\n mov.b32 {a, b}, %2;\n cvt.f32.f16 %0, a;\n cvt.f32.f16 %1, b;\n}\n"
+      : "=f"(hr), "=f"(hm)
+      : "r"(h));
+  uint32_t l;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(im - hm), "f"(re - hr));
+  hi = h;
+  lo = l;
+}
+
+// Power-of-two scale of the split-FP16 form: 2^k with |value| * 2^k <= 2^14 for every value
+// whose magnitude is at most 2^e (k = 14 - e, limited to +-100; 2^k as a float)
+__device__ __forceinline__ int f16_scale_exp(int e) { return max(-100, min(100, 14 - e)); }
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+// exponent e with |x| <= 2^e for 0 <= x (x = 0 gives a large negative e)
+__device__ __forceinline__ int bound_exp(float x) { return x > 0.f ? ilogbf(x) + 1 : -200; }
 
 // Rows of the transposed array holding factor f for its variable in [va, vb]; `lo` is the
 // first multipole index (n for G, m = |n| for W).
@@ -306,6 +342,9 @@ template <> struct TcPrec<EXT4PCF_TF32> {  // A: fp32 (re, im) pairs; B: two ato
 template <> struct TcPrec<EXT4PCF_3XTF32> {  // A: hi | lo fp32 pairs; B: hi 2 atoms | lo 2 atoms
   static constexpr int kStages = 3, kStageCols = 128, kAtoms = 4;
 };
+template <> struct TcPrec<EXT4PCF_SPLIT_F16> {  // as BF16x3, fp16 halves of scaled values
+  static constexpr int kStages = 4, kStageCols = 64, kAtoms = 2;
+};
 
 // Warp roles: warps 0..15 form the A operand (Khatri-Rao rows, TMEM) and the B operand
 // (shared memory) of each stage; warp 16 issues the MMAs (one thread); warp 17 stages each
@@ -320,6 +359,9 @@ template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
 contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) {
   using P = TcPrec<PREC>;
+  // kind::f16 operands: bf16 or fp16 halves, one 32-bit word per centre (re, im)
+  constexpr bool k16 = PREC == EXT4PCF_SPLIT_BF16 || PREC == EXT4PCF_SPLIT_F16;
+  constexpr bool kScaled = PREC == EXT4PCF_SPLIT_F16;
   constexpr int kSt = P::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
@@ -371,7 +413,7 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const long long budget = args.timeout;
-  const int nstage = (args.T + kStageCentres - 1) / kStageCentres;
+  const int nstage = (wave_centres(args.T, args.n_live, args.w0) + kStageCentres - 1) / kStageCentres;
   const int nsub = (nstage + kPromote - 1) / kPromote;
   int err = 0;
   // bounded wait on an mbarrier phase; the first wait of the CTA that runs out of its budget
@@ -422,6 +464,52 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
         offB[q] = (uint32_t)h * half_bytes + stg_off(eB, c0 + q);
         offC[q] = (uint32_t)h * half_bytes + stg_off(eC, c0 + q);
       }
+      // this warp's column pairs v = (component slot, Th1) of the B operand (at most two, as
+      // nmu nb <= 32 for the supported shapes), with their staged row and conjugation, fixed
+      // for the item: kept in registers (no runtime-indexed access to the factor tables)
+      const int nv = nmu * nb;
+      int eAv[2] = {0, 0};
+      bool cjAv[2] = {false, false};
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int v = warp + j * kProducerWarps;
+        if (v < nv) {
+          const int b1 = v % nb;
+          if (v < nb) eAv[j] = g.sa0 + blk_index(g.ba0, kr.A[0], g.s, b1, nb, cjAv[j]);
+          else eAv[j] = g.sa1 + blk_index(g.ba1, kr.A[1], g.s, b1, nb, cjAv[j]);
+        }
+      }
+      const int mu0 = kr.mu[0], mu1 = kr.mu[1];
+      // shared-memory offsets of this lane's centre: the A value in the staged stage, and the
+      // words of the two B columns (re, im) in the B tile
+      uint32_t aoff[2], bre[2], bim[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int v = warp + j * kProducerWarps;
+        aoff[j] = (uint32_t)(lane >> 4) * half_bytes + stg_off(eAv[j], (lane & 15) >> 1) + (lane & 1) * 8;
+        const int kw = k16 ? lane : 2 * lane;  // K word of the centre
+        bre[j] = sw128_word_off(2 * v, kw, kMaxNpad);
+        bim[j] = sw128_word_off(2 * v + 1, kw, kMaxNpad);
+      }
+      // split-FP16 form: power-of-two scales of this row (x~B times C, bounded by twice the
+      // product of the two rows' largest components) and of the B columns this warp forms
+      int krow = 0, kcol[2] = {0, 0};
+      float scrow = 1.f, sccol[2] = {1.f, 1.f};
+      if constexpr (kScaled) {
+        const int xrow = g.bx.row0 + (eB - g.sx), crow = g.bc.row0 + (eC - g.sc);
+        krow = f16_scale_exp(bound_exp(__uint_as_float(args.rowmax[xrow])) +
+                             bound_exp(__uint_as_float(args.rowmax[crow])) + 1);
+        scrow = pow2f(krow);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int v = warp + j * kProducerWarps;
+          if (v < nv) {
+            const int arow = v < nb ? g.ba0.row0 + (eAv[j] - g.sa0) : g.ba1.row0 + (eAv[j] - g.sa1);
+            kcol[j] = f16_scale_exp(bound_exp(__uint_as_float(args.rowmax[arow])));
+            sccol[j] = pow2f(kcol[j]);
+          }
+        }
+      }
       float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
 #pragma unroll
       for (int j = 0; j < 16; ++j) accD[j] = 0.f;
@@ -448,36 +536,41 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
         unsigned char* bt = sm + aslot * stage_bytes;
         // B operand (shared memory, K-major, swizzled): the real embedding of A(Th1) for the
         // 32 centres of the stage; warp v forms column pair v = (g, b1), lane = centre
-        for (int v = warp; v < nmu * nb; v += kProducerWarps) {
-          const int ga = v / nb, b1 = v % nb;
-          bool cjA;
-          const int eA = (ga ? g.sa1 : g.sa0) + blk_index(ga ? g.ba1 : g.ba0, kr.A[ga], g.s, b1, nb, cjA);
-          float2 a = *reinterpret_cast<const float2*>(st + (lane >> 4) * half_bytes + stg_off(eA, (lane & 15) >> 1) +
-                                                      (lane & 1) * 8);
-          if (cjA) a.y = -a.y;
-          const int nre = 2 * v, nim = 2 * v + 1;
-          if (PREC == EXT4PCF_SPLIT_BF16) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          if (warp + j * kProducerWarps >= nv) break;
+          float2 a = *reinterpret_cast<const float2*>(st + aoff[j]);
+          if (cjAv[j]) a.y = -a.y;
+          if constexpr (kScaled) {
+            uint32_t rh, rl, ih, il;  // column re: (Ar, -Ai), column im: (Ai, Ar), f16x2 each
+            a.x *= sccol[j];
+            a.y *= sccol[j];
+            split_f16(a.x, -a.y, rh, rl);
+            split_f16(a.y, a.x, ih, il);
+            *reinterpret_cast<uint32_t*>(bt + bre[j]) = rh;
+            *reinterpret_cast<uint32_t*>(bt + tile_bytes + bre[j]) = rl;
+            *reinterpret_cast<uint32_t*>(bt + bim[j]) = ih;
+            *reinterpret_cast<uint32_t*>(bt + tile_bytes + bim[j]) = il;
+          } else if (PREC == EXT4PCF_SPLIT_BF16) {
             uint32_t rh, rl, ih, il;  // column re: (Ar, -Ai), column im: (Ai, Ar), bf16x2 each
             split_bf16(a.x, -a.y, rh, rl);
             split_bf16(a.y, a.x, ih, il);
-            *reinterpret_cast<uint32_t*>(bt + sw128_word_off(nre, lane, kMaxNpad)) = rh;
-            *reinterpret_cast<uint32_t*>(bt + tile_bytes + sw128_word_off(nre, lane, kMaxNpad)) = rl;
-            *reinterpret_cast<uint32_t*>(bt + sw128_word_off(nim, lane, kMaxNpad)) = ih;
-            *reinterpret_cast<uint32_t*>(bt + tile_bytes + sw128_word_off(nim, lane, kMaxNpad)) = il;
+            *reinterpret_cast<uint32_t*>(bt + bre[j]) = rh;
+            *reinterpret_cast<uint32_t*>(bt + tile_bytes + bre[j]) = rl;
+            *reinterpret_cast<uint32_t*>(bt + bim[j]) = ih;
+            *reinterpret_cast<uint32_t*>(bt + tile_bytes + bim[j]) = il;
           } else if (PREC == EXT4PCF_TF32) {
-            *reinterpret_cast<float2*>(bt + sw128_word_off(nre, 2 * lane, kMaxNpad)) = make_float2(a.x, -a.y);
-            *reinterpret_cast<float2*>(bt + sw128_word_off(nim, 2 * lane, kMaxNpad)) = make_float2(a.y, a.x);
+            *reinterpret_cast<float2*>(bt + bre[j]) = make_float2(a.x, -a.y);
+            *reinterpret_cast<float2*>(bt + bim[j]) = make_float2(a.y, a.x);
           } else {
             uint32_t xh, xl, yh, yl;
             split_tf32(a.x, xh, xl);
             split_tf32(a.y, yh, yl);
             const uint32_t sgn = 0x80000000u;
-            *reinterpret_cast<uint2*>(bt + sw128_word_off(nre, 2 * lane, kMaxNpad)) = make_uint2(xh, yh ^ sgn);
-            *reinterpret_cast<uint2*>(bt + sw128_word_off(nim, 2 * lane, kMaxNpad)) = make_uint2(yh, xh);
-            *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + sw128_word_off(nre, 2 * lane, kMaxNpad)) =
-                make_uint2(xl, yl ^ sgn);
-            *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + sw128_word_off(nim, 2 * lane, kMaxNpad)) =
-                make_uint2(yl, xl);
+            *reinterpret_cast<uint2*>(bt + bre[j]) = make_uint2(xh, yh ^ sgn);
+            *reinterpret_cast<uint2*>(bt + bim[j]) = make_uint2(yh, xh);
+            *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + bre[j]) = make_uint2(xl, yl ^ sgn);
+            *reinterpret_cast<uint2*>(bt + 2 * tile_bytes + bim[j]) = make_uint2(yl, xl);
           }
         }
         // A operand (TMEM): this row's Khatri-Rao values x~B * C for the warp's eight centres
@@ -492,7 +585,18 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
           cvv[2 * q + 1] = make_float2(tc.z, tc.w);
         }
         const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + aslot * P::kStageCols;
-        if (PREC == EXT4PCF_SPLIT_BF16) {
+        if constexpr (kScaled) {
+          uint32_t w[16];
+#pragma unroll
+          for (int j = 0; j < kQuarter; ++j) {
+            const float2 xb = xbv[j];
+            float2 cv = cvv[j];
+            cv.y *= sgnC;
+            split_f16((xb.x * cv.x - xb.y * cv.y) * scrow, (xb.x * cv.y + xb.y * cv.x) * scrow, w[j], w[8 + j]);
+          }
+          tmem_st8(acol + quarter * 8, w);
+          tmem_st8(acol + 32 + quarter * 8, w + 8);
+        } else if (PREC == EXT4PCF_SPLIT_BF16) {
           uint32_t w[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
@@ -552,11 +656,19 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
           const int n = quarter * 16 + j;
           if (n < ncols) {
             const int ga = n / (2 * nb), b1 = (n >> 1) % nb;
-            const int mu = kr.mu[ga];
+            const int mu = ga ? mu1 : mu0;
             const size_t o = ((((size_t)mu * nx + (n2 + N + 1)) * nx + (n3 + N + 1)) * nb + b1) * npairs + pr;
             double* p = args.red + 2 * o;
-            p[0] += (double)accD[j];
-            p[1] += (double)accD[j + 1];
+            double unscale = 1.0;
+            if constexpr (kScaled) {  // exact: both scales are powers of two
+              bool cj;
+              const int arow = ga ? g.ba1.row0 + blk_index(g.ba1, kr.A[1], g.s, b1, nb, cj)
+                                  : g.ba0.row0 + blk_index(g.ba0, kr.A[0], g.s, b1, nb, cj);
+              const int kc = f16_scale_exp(bound_exp(__uint_as_float(args.rowmax[arow])));
+              unscale = ldexp(1.0, -(krow + kc));
+            }
+            p[0] += (double)accD[j] * unscale;
+            p[1] += (double)accD[j + 1] * unscale;
           }
         }
       }
@@ -564,11 +676,13 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
   } else if (warp == kWarpMma) {
     // ---------------------------------------------------------------------- MMA issuer
     if (lane == 0) {
+      const uint64_t dbase = desc_sw128(saddr(sm));
       long long qa = 0, gs = 0;
       for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
         const KRType kr = kKR[args.items[it].x];
         const int npad = (2 * kr.nmu * nb + 15) / 16 * 16;
-        const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad) : idesc(2u, npad);
+        const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad)
+                            : PREC == EXT4PCF_SPLIT_F16 ? idesc(0u, npad) : idesc(2u, npad);
         for (int k = 0; k < nstage; ++k, ++qa) {
           const long long gg = gs + k / kPromote;
           const int buf = (int)(gg & 1);
@@ -581,11 +695,14 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
           tc_fence_after();
           const uint32_t d = tmem + buf * kDBuf;
           const uint32_t a0 = tmem + kDCols + slot * P::kStageCols;
-          const uint32_t b0 = saddr(sm + slot * stage_bytes);
-          if (PREC == EXT4PCF_SPLIT_BF16) {
+          // descriptor of the slot's B tile: the start-address field (bits 0-13, address / 16)
+          // of the first tile's descriptor plus the offset / 16 (no carry: shared addresses
+          // stay below 2^18)
+          const uint64_t db = dbase + (uint64_t)((slot * stage_bytes) >> 4);
+          if (k16) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {  // K = 16 bf16 = 8 centres per MMA
-              const uint64_t bh = desc_sw128(b0 + q * 32), bl = desc_sw128(b0 + tile_bytes + q * 32);
+            for (int q = 0; q < 4; ++q) {  // K = 16 halves = 8 centres per MMA
+              const uint64_t bh = db + (q * 32 >> 4), bl = db + ((tile_bytes + q * 32) >> 4);
               mma_f16(d, a0 + q * 8, bh, id, (!first || q > 0) ? 1u : 0u);
               mma_f16(d, a0 + q * 8, bl, id, 1u);
               mma_f16(d, a0 + 32 + q * 8, bh, id, 1u);
@@ -593,14 +710,14 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
           } else if (PREC == EXT4PCF_TF32) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {  // K = 8 fp32 = 4 centres per MMA
-              const uint64_t b = desc_sw128(b0 + (q >> 2) * tile_bytes + (q & 3) * 32);
+              const uint64_t b = db + (((q >> 2) * tile_bytes + (q & 3) * 32) >> 4);
               mma_tf32(d, a0 + q * 8, b, id, (!first || q > 0) ? 1u : 0u);
             }
           } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {  // hi*hi + hi*lo + lo*hi, K = 8 fp32 per MMA
               const uint32_t bo_ = (q >> 2) * tile_bytes + (q & 3) * 32;
-              const uint64_t bh = desc_sw128(b0 + bo_), bl = desc_sw128(b0 + 2 * tile_bytes + bo_);
+              const uint64_t bh = db + (bo_ >> 4), bl = db + ((2 * tile_bytes + bo_) >> 4);
               mma_tf32(d, a0 + q * 8, bh, id, (!first || q > 0) ? 1u : 0u);
               mma_tf32(d, a0 + q * 8, bl, id, 1u);
               mma_tf32(d, a0 + 64 + q * 8, bh, id, 1u);
@@ -676,7 +793,7 @@ int stage_rows_for(int nb, int N) {
 }
 
 size_t tc_fixed_smem(int prec) {
-  const bool x3 = prec == EXT4PCF_3XTF32;
+  const bool x3 = prec == EXT4PCF_3XTF32;  // the others: 4 stages of 2 atoms
   const int st = x3 ? TcPrec<EXT4PCF_3XTF32>::kStages : 4;
   const int atoms = x3 ? TcPrec<EXT4PCF_3XTF32>::kAtoms : 2;
   return (size_t)st * atoms * kMaxNpad * 128 + 1024 + 512;
@@ -706,7 +823,9 @@ cudaError_t launch_tc(const TcArgs& a, const CUtensorMap& tm, size_t smem, int s
 }  // namespace
 
 bool tc_supported(const Layout& L, int precision) {
-  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32 && precision != EXT4PCF_3XTF32) return false;
+  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32 && precision != EXT4PCF_3XTF32 &&
+      precision != EXT4PCF_SPLIT_F16)
+    return false;
   return L.nb >= 1 && 4 * L.nb <= kMaxNpad && tc_in_stages(L.nb, L.N, precision) >= 2;
 }
 
@@ -740,6 +859,8 @@ int tc_wave_pitch(int T) { return (T + 31) / 32 * 32; }
 size_t contract_tc_xb_bytes(const Layout& L, int T) {
   return (size_t)tc_wave_rows(L) * tc_wave_pitch(T) * sizeof(float2);
 }
+
+size_t contract_tc_rowmax_bytes(const Layout& L) { return (size_t)tc_wave_rows(L) * sizeof(unsigned); }
 
 size_t tc_reduced_doubles(const Layout& L) {
   const size_t nx = 2 * L.N + 3;
@@ -817,15 +938,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }
 }  // namespace
 
-cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, double* red,
-                             int precision, const int4* items, int n_items, float2* wave, int* status,
-                             long long timeout, cudaStream_t s) {
+cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, const int* n_live,
+                             int w0, double* red, int precision, const int4* items, int n_items, float2* wave,
+                             unsigned* rowmax, int* status, long long timeout, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
   const int rows = tc_wave_rows(L), pitch = tc_wave_pitch(T);
   const int row_g = kXBTypes * (2 * L.N + 3) * L.nb, row_w = row_g + L.nG * L.nb;
+  const bool scaled = precision == EXT4PCF_SPLIT_F16;
+  if (scaled) {
+    cudaError_t e = cudaMemsetAsync(rowmax, 0, (size_t)rows * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+  }
   {
     dim3 grid((rows + 31) / 32, (T + 31) / 32);
-    transpose_wave_kernel<<<grid, 256, 0, s>>>(L, rec, xw, T, pitch, row_g, row_w, rows, wave);
+    transpose_wave_kernel<<<grid, 256, 0, s>>>(L, rec, xw, T, n_live, w0, pitch, row_g, row_w, rows, wave,
+                                               scaled ? rowmax : nullptr);
     ++g_launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -843,10 +970,11 @@ cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* x
           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   TcArgs a;
-  a.L = L; a.T = T; a.red = red;
+  a.L = L; a.T = T; a.n_live = n_live; a.w0 = w0; a.red = red;
   a.npairs = L.nb * (L.nb + 1) / 2;
   a.items = items; a.n_items = n_items;
   a.row_g = row_g; a.row_w = row_w;
+  a.rowmax = rowmax;
   a.in_stages = tc_in_stages(L.nb, L.N, precision);
   a.stage_rows = stage_rows_for(L.nb, L.N);
   a.timeout = timeout; a.status = status;
@@ -857,6 +985,7 @@ cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* x
   const size_t smem = tc_smem_bytes(L.nb, L.N, precision);
   cudaError_t e;
   if (precision == EXT4PCF_SPLIT_BF16) e = launch_tc<EXT4PCF_SPLIT_BF16>(a, tm, smem, sms, s);
+  else if (precision == EXT4PCF_SPLIT_F16) e = launch_tc<EXT4PCF_SPLIT_F16>(a, tm, smem, sms, s);
   else if (precision == EXT4PCF_TF32) e = launch_tc<EXT4PCF_TF32>(a, tm, smem, sms, s);
   else e = launch_tc<EXT4PCF_3XTF32>(a, tm, smem, sms, s);
   ++g_launches;

@@ -291,23 +291,34 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   R* trs = reinterpret_cast<R*>(misc + 8);
   signed char* cbin = reinterpret_cast<signed char*>(trs + (kTrSplit ? nb * args.nblk * 10 : 0));  // bin of each candidate
 
+  // the cell grid (computed on the device for the measure path) and the wave's centres
+  double gx0 = cat.x0, gy0 = cat.y0, cell = cat.cell;
+  int gncx = cat.ncx, gncy = cat.ncy;
+  if (cat.geom) {
+    gx0 = cat.geom->x0; gy0 = cat.geom->y0; cell = cat.geom->cell;
+    gncx = cat.geom->ncx; gncy = cat.geom->ncy;
+  }
+  const int T = args.n_live ? min(args.T, *args.n_live - args.w0) : args.T;
   for (int b = tid; b <= nb; b += kThreads) {
-    e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b]; win[b] = args.win[b];
+    e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b];
+    // rounding window of the float bin decision: |dx| carries ~2 ulp of max(cell, r)
+    const double e = sqrt(args.bins.e2[b]);
+    const double err = 4.0 * 1.2e-7 * (cell + e);
+    win[b] = (float)(2.0 * e * err + err * err);
   }
   for (int k = tid; k < kWarps * 64; k += kThreads) wcnt[k] = 0;
   __syncthreads();
   const double rmax = args.bins.rmax * (1.0 + 1e-9) + 1e-12;
-  const double cell = cat.cell;
 
-  for (int c = blockIdx.x; c < args.T; c += gridDim.x) {
+  for (int c = blockIdx.x; c < T; c += gridDim.x) {
     const int pi = args.centres[c];
     const double pxi = cat.px[pi], pyi = cat.py[pi];
     float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (sizeof(R) == 4) Pi = cat.p4[pi];
     if (tid == 0) {
-      const double xc = pxi - cat.x0, yc = pyi - cat.y0;
+      const double xc = pxi - gx0, yc = pyi - gy0;
       int cy0 = (int)floor((yc - rmax) / cell), cy1 = (int)floor((yc + rmax) / cell);
-      cy0 = max(cy0, 0); cy1 = min(cy1, cat.ncy - 1);
+      cy0 = max(cy0, 0); cy1 = min(cy1, gncy - 1);
       int nr = 0, tot = 0;
       for (int cy = cy0; cy <= cy1 && nr < kMaxRows; ++cy) {
         const double lo = cy * cell, hi = lo + cell;
@@ -315,10 +326,10 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
         if (gap > rmax) continue;
         const double hw = sqrt(fmax(0.0, rmax * rmax - gap * gap));
         int cx0 = (int)floor((xc - hw) / cell), cx1 = (int)floor((xc + hw) / cell);
-        cx0 = max(cx0, 0); cx1 = min(cx1, cat.ncx - 1);
+        cx0 = max(cx0, 0); cx1 = min(cx1, gncx - 1);
         if (cx0 > cx1) continue;
-        const int a = cat.cell_start[cy * cat.ncx + cx0];
-        const int b = cat.cell_start[cy * cat.ncx + cx1 + 1];
+        const int a = cat.cell_start[cy * gncx + cx0];
+        const int b = cat.cell_start[cy * gncx + cx1 + 1];
         if (b <= a) continue;
         rstart[nr] = a; rpre[nr] = tot; tot += b - a; ++nr;
       }
@@ -520,19 +531,14 @@ template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 
 template <typename R>
 cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
-                        const int* centres, int T, cplx_t<R>* rec, cplx_t<R>* xw,
+                        const int* centres, int T, const int* n_live, int w0, cplx_t<R>* rec, cplx_t<R>* xw,
                         unsigned long long* pair_count, int sm_count, cudaStream_t s) {
   if (T <= 0) return cudaSuccess;
   constexpr int MB = kMB<R>;
   constexpr int MINB = kMinBlocks<R>;
   GatherArgs a;
   a.cat = cat; a.bins = bins; a.L = L; a.centres = centres; a.T = T; a.pair_count = pair_count;
-  // rounding window of the float bin decision: |dx| carries ~2 ulp of max(cell, r)
-  for (int b = 0; b <= bins.nb; ++b) {
-    const double e = sqrt(bins.e2[b]);
-    const double err = 4.0 * 1.2e-7 * (cat.cell + e);
-    a.win[b] = (float)(2.0 * e * err + err * err);
-  }
+  a.n_live = n_live; a.w0 = w0;
   const int npow = L.max_pow + 1;
   int nblk = (npow + MB - 1) / MB;
   nblk = (nblk + kWarps - 1) / kWarps * kWarps;
@@ -560,10 +566,10 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
 }
 
 template cudaError_t gather_wave<float>(const SortedCat&, const Bins&, const Layout&, const int*,
-                                        int, float2*, float2*, unsigned long long*, int,
+                                        int, const int*, int, float2*, float2*, unsigned long long*, int,
                                         cudaStream_t);
 template cudaError_t gather_wave<double>(const SortedCat&, const Bins&, const Layout&, const int*,
-                                         int, double2*, double2*, unsigned long long*, int,
+                                         int, const int*, int, double2*, double2*, unsigned long long*, int,
                                          cudaStream_t);
 
 }  // namespace ext4pcf

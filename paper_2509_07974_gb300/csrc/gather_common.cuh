@@ -102,10 +102,11 @@ template <> struct Pair<float> {
 struct GatherArgs {
   SortedCat cat;
   Bins bins;
-  float win[65];
   Layout L;
-  const int* centres;
-  int T;
+  const int* centres;  // the wave's first centre (sorted positions)
+  int T;               // centres of the wave at most
+  const int* n_live;   // device: centres of the catalogue (nullptr: T is exact)
+  int w0;              // the wave's first index in the catalogue's centre list
   int cap;
   int mb;    // powers per warp block (<= MB)
   int nblk;  // power blocks

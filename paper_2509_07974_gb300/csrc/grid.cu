@@ -49,6 +49,50 @@ __global__ void bbox_final(const double* __restrict__ part, int np, double* __re
   for (int k = 0; k < 4; ++k) out[k] = v[k];
 }
 
+// ------------------------------------------------------------------------ device grid
+// cell side: about an eighth of the largest separation, at most ~4000 cells per axis, and
+// with 12 significant bits so that (cell index) * cell is exact in float
+__global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, GridGeom* __restrict__ g) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  GridGeom r;
+  const bool finite = isfinite(bb[0]) && isfinite(bb[1]) && isfinite(bb[2]) && isfinite(bb[3]);
+  r.bad = finite ? 0 : 1;
+  const double x0 = finite ? bb[0] : 0.0, y0 = finite ? bb[1] : 0.0;
+  const double wx = finite ? bb[2] - bb[0] : 0.0, wy = finite ? bb[3] - bb[1] : 0.0;
+  const double extent = fmax(wx, wy);
+  double c = rmax / 8.0;
+  if (extent / 4000.0 > c) c = extent / 4000.0;
+  int ex;
+  double m = frexp(c, &ex);          // c = m 2^ex, m in [0.5, 1)
+  m = floor(m * 4096.0) / 4096.0;    // 12 significant bits
+  c = ldexp(m, ex);
+  r.x0 = x0;
+  r.y0 = y0;
+  r.cell = c;
+  r.inv_cell = 1.0 / c;
+  r.cellf = (float)c;
+  r.ncx = min((int)floor(wx / c) + 1, kMaxCellsPerAxis);
+  r.ncy = min((int)floor(wy / c) + 1, kMaxCellsPerAxis);
+  *g = r;
+}
+
+// a position that is not finite (NaN, which the bounding box's fmin/fmax skip, or +-inf)
+// sets bit 1 of *status; its key is clamped into the grid like any other
+__global__ void make_keys_dev(const double* __restrict__ pos, int n, const GridGeom* __restrict__ g,
+                              int* __restrict__ keys, int* __restrict__ idx, int* __restrict__ status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const GridGeom G = *g;
+  const double x = pos[2 * i], y = pos[2 * i + 1];
+  if (!isfinite(x) || !isfinite(y)) atomicOr(status, 2);
+  int cx = (int)floor((x - G.x0) * G.inv_cell);
+  int cy = (int)floor((y - G.y0) * G.inv_cell);
+  cx = min(max(cx, 0), G.ncx - 1);
+  cy = min(max(cy, 0), G.ncy - 1);
+  keys[i] = cy * G.ncx + cx;
+  idx[i] = i;
+}
+
 // ------------------------------------------------------------------------ keys
 __global__ void make_keys(const double* __restrict__ pos, int n, double x0, double y0,
                           double inv_cell, int ncx, int ncy, int* __restrict__ keys,
@@ -182,6 +226,16 @@ __global__ void cell_bounds(const int* __restrict__ keys, int n, int ncells, int
   for (int c = lo + 1; c <= hi; ++c) start[c] = p;
 }
 
+__global__ void cell_bounds_dev(const int* __restrict__ keys, int n, const GridGeom* __restrict__ g,
+                                int* __restrict__ start) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > n) return;
+  const int ncells = g->ncx * g->ncy;
+  int lo = (p == 0) ? -1 : keys[p - 1];
+  int hi = (p == n) ? ncells : keys[p];
+  for (int c = lo + 1; c <= hi; ++c) start[c] = p;
+}
+
 __global__ void fill_start_empty(int* start, int ncells) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c <= ncells) start[c] = 0;
@@ -190,7 +244,8 @@ __global__ void fill_start_empty(int* start, int ncells) {
 // ------------------------------------------------------------------------ sorted arrays
 __global__ void build_sorted(const double* __restrict__ pos, const double* __restrict__ shear,
                              const double* __restrict__ wts, const int* __restrict__ perm,
-                             const int* __restrict__ keys, int n, int ncx, double x0, double y0,
+                             const int* __restrict__ keys, int n, const GridGeom* __restrict__ geom,
+                             int ncx, double x0, double y0,
                              double cell, float cellf, bool want_f32, double* __restrict__ px,
                              double* __restrict__ py, double* __restrict__ xr,
                              double* __restrict__ xi, double* __restrict__ w,
@@ -202,6 +257,9 @@ __global__ void build_sorted(const double* __restrict__ pos, const double* __res
   double gr = ww * shear[2 * i], gi = ww * shear[2 * i + 1];
   px[p] = x; py[p] = y; xr[p] = gr; xi[p] = gi; w[p] = ww;
   if (want_f32) {
+    if (geom) {
+      ncx = geom->ncx; x0 = geom->x0; y0 = geom->y0; cell = geom->cell; cellf = geom->cellf;
+    }
     int key = keys[p];
     int cx = key % ncx, cy = key / ncx;
     // cx*cell and cy*cell are exact in float (cell has few significant bits)
@@ -230,7 +288,7 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
                       double x0, double y0, double cell, int ncx, int ncy, bool want_f32,
                       GridBuffers& gb, SortedCat& out, cudaStream_t s) {
   const int ncells = ncx * ncy;
-  out.n = n; out.ncx = ncx; out.ncy = ncy; out.x0 = x0; out.y0 = y0;
+  out.n = n; out.geom = nullptr; out.ncx = ncx; out.ncy = ncy; out.x0 = x0; out.y0 = y0;
   out.cell = cell; out.cellf = (float)cell;
   out.cell_start = gb.cell_start;
   out.perm = gb.perm;
@@ -261,9 +319,48 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
   }
   out.perm = vin;
   cell_bounds<<<(n + 1 + 255) / 256, 256, 0, s>>>(kin, n, ncells, gb.cell_start);
-  build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, ncx, x0, y0, cell,
+  build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, nullptr, ncx, x0, y0, cell,
                                                (float)cell, want_f32, gb.px, gb.py, gb.xr, gb.xi,
                                                gb.w, gb.p4, gb.s4);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n,
+                             const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
+                             GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s) {
+  out.n = n;
+  out.geom = d_geom;
+  out.ncx = out.ncy = 0;
+  out.x0 = out.y0 = out.cell = 0.0;
+  out.cellf = 0.f;
+  out.cell_start = gb.cell_start;
+  out.perm = gb.perm;
+  out.px = gb.px; out.py = gb.py; out.xr = gb.xr; out.xi = gb.xi; out.w = gb.w;
+  out.p4 = gb.p4; out.s4 = gb.s4;
+  if (n == 0) return cudaSuccess;
+  grid_geom_kernel<<<1, 32, 0, s>>>(d_bbox, rmax, d_geom);
+  make_keys_dev<<<(n + 255) / 256, 256, 0, s>>>(pos, n, d_geom, gb.keys, gb.perm, status);
+  g_launches += 2;
+  // keys below kMaxCellsPerAxis^2 < 2^24: three 8-bit digits
+  const int ntiles = (n + kTile - 1) / kTile;
+  int* kin = gb.keys; int* kout = gb.keys_alt;
+  int* vin = gb.perm; int* vout = gb.perm_alt;
+  unsigned* hist = gb.hist;
+  unsigned* tmp = gb.hist + (size_t)256 * ntiles;
+  for (int shift = 0; shift < 24; shift += 8) {
+    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
+    cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
+    g_launches += 2;
+    int* t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+  }
+  out.perm = vin;
+  cell_bounds_dev<<<(n + 1 + 255) / 256, 256, 0, s>>>(kin, n, d_geom, gb.cell_start);
+  build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, d_geom, 0, 0.0, 0.0, 1.0, 1.f,
+                                               want_f32, gb.px, gb.py, gb.xr, gb.xi, gb.w, gb.p4, gb.s4);
   g_launches += 2;
   return cudaGetLastError();
 }

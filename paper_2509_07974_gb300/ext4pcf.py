@@ -3,7 +3,7 @@
 The functions ``ext4pcf_create``, ``ext4pcf_destroy``, ``ext4pcf_measure``,
 ``ext4pcf_to_real_space``, ``ext4pcf_to_map4``, ``ext4pcf_to_real_space_noalloc``,
 ``ext4pcf_map_direct``, ``ext4pcf_measure3``, ``ext4pcf_nth_order_components``, ``ext4pcf_nth_order_factors``,
-``ext4pcf_contraction_tables`` and ``ext4pcf_last_error`` mirror the C ABI one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
+``ext4pcf_contraction_tables``, ``ext4pcf_synchronize`` and ``ext4pcf_last_error`` mirror the C ABI one to one; pointer arguments accept torch tensors (device or host), numpy arrays, raw
 integer addresses or None.  ``Estimator`` wraps them for torch users: it allocates outputs
 and passes the current CUDA stream.  Every computation happens in the CUDA library; there
 is no fallback, and loading fails loudly if the library has not been built.
@@ -23,7 +23,7 @@ EXT4PCF_E_CUDA = -3
 EXT4PCF_E_TIMEOUT = -4
 EXT4PCF_E_UNSUPPORTED = -5
 
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16x3": 4}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16x3": 4, "f16x3": 5}
 
 
 class Config(ctypes.Structure):
@@ -37,7 +37,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int64), ("centres", ctypes.c_int64), ("waves", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("ms_grid", ctypes.c_double), ("ms_gather", ctypes.c_double),
                 ("ms_contract", ctypes.c_double), ("ms_correct", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("wave_centres", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_contraction_tables.argtypes = [I, P, I]
     for f in ("ext4pcf_nth_order_components", "ext4pcf_nth_order_factors", "ext4pcf_contraction_tables"):
         getattr(lib, f).restype = I
+    lib.ext4pcf_synchronize.argtypes = [P]
+    lib.ext4pcf_synchronize.restype = I
     lib.ext4pcf_last_error.argtypes = [P]
     lib.ext4pcf_last_error.restype = ctypes.c_char_p
     for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_to_real_space",
@@ -110,6 +112,12 @@ def ext4pcf_create(config: Config) -> int:
 
 def ext4pcf_destroy(ctx: int) -> int:
     return load().ext4pcf_destroy(ctx)
+
+
+def ext4pcf_synchronize(ctx: int) -> int:
+    """Wait for the context's enqueued work; raises on a recorded failure (timeout, non-finite
+    positions)."""
+    return _check(ctx, load().ext4pcf_synchronize(ctx))
 
 
 def ext4pcf_last_error(ctx: int) -> str:
@@ -231,7 +239,7 @@ class Estimator:
     ``as_complex`` gives a complex128 view)."""
 
     def __init__(self, device: int = 0, precision: str = "fp64", stream=None,
-                 wave_centres: int = 0):
+                 wave_centres: int = 0, autotune: bool = False, workspace_bytes: int = 0):
         import torch
         self.torch = torch
         self.device = device
@@ -239,8 +247,8 @@ class Estimator:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         cfg = Config(device=device, stream=stream.cuda_stream, precision=PRECISION[precision],
-                     autotune=0, workspace_bytes=0, timeout_cycles=0, deterministic=1,
-                     wave_centres=wave_centres)
+                     autotune=1 if autotune else 0, workspace_bytes=int(workspace_bytes), timeout_cycles=0,
+                     deterministic=1, wave_centres=wave_centres)
         self.ctx = ext4pcf_create(cfg)
 
     def close(self):

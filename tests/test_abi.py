@@ -47,7 +47,7 @@ def test_struct_layouts_match_header():
     from paper_2509_07974_gb300 import ext4pcf
     # int, void*, int, int, int64, int64, int, int  (x86-64 / aarch64 LP64 alignment)
     assert ctypes.sizeof(ext4pcf.Config) == 48
-    assert ctypes.sizeof(ext4pcf.Stats) == 9 * 8
+    assert ctypes.sizeof(ext4pcf.Stats) == 10 * 8
 
 
 def test_create_without_gpu_is_an_error_code(lib):
