@@ -426,7 +426,7 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     const size_t cbytes = f64 ? sizeof(double2) : sizeof(float2);
     auto wave_bytes = [&](int t) -> size_t {
       size_t b = (size_t)t * L.rec * cbytes + (size_t)t * 2 * cbytes;
-      if (tc) b += contract_tc_xb_bytes(L, t);
+      if (tc) b += contract_tc_xb_bytes(L, t, prec);
       return b;
     };
     const auto key = std::make_tuple(prec, n_max, n_bins);
@@ -459,8 +459,8 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     if (Tmax < T) Tmax = T;
     ENSURE(ctx->rec, (size_t)Tmax * L.rec * cbytes);
     if (tc) {
-      ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, Tmax));
-      ENSURE(ctx->tc_rowmax, contract_tc_rowmax_bytes(L));
+      ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, Tmax, prec));
+      if (prec == EXT4PCF_SPLIT_F16) ENSURE(ctx->tc_rowmax, contract_h16_rowmax_bytes(L));
     }
     ENSURE(ctx->xw, (size_t)Tmax * 2 * cbytes);
     std::vector<float> trial_ms;

@@ -165,16 +165,24 @@ size_t corrections_size(const Layout& L);  // doubles
 
 // contract_tc.cu (tensor cores).  The wave is contracted into the reduced array of the
 // Theta2 <-> Theta3 symmetry (tc_reduced_doubles doubles, zeroed per catalogue); tc_expand adds
-// every ordered triple at |n| <= N from it into the output.
+// every ordered triple at |n| <= N from it into the output.  wave: the transposed wave array
+// (contract_tc_xb_bytes); rowmax: the split-FP16 form's row maxima (contract_h16_rowmax_bytes).
 bool tc_supported(const Layout& L, int precision);
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T,
                              const int* n_live, int w0, double* red, int precision, const int4* items,
-                             int n_items, float2* xb, unsigned* rowmax, int* status, long long timeout,
+                             int n_items, float2* wave, unsigned* rowmax, int* status, long long timeout,
                              cudaStream_t s);
-size_t contract_tc_xb_bytes(const Layout& L, int T);
-size_t contract_tc_rowmax_bytes(const Layout& L);  // per-row maxima of the split-FP16 form
+size_t contract_tc_xb_bytes(const Layout& L, int T, int precision);
 size_t tc_reduced_doubles(const Layout& L);
 bool tc_build_items(const Layout& L, std::vector<int4>& items);
 cudaError_t tc_expand(const Layout& L, const double* red, double* ups, cudaStream_t s);
+
+// contract_h16.cu: the split-FP16 form (called through contract_wave_tc)
+bool h16_supported(const Layout& L);
+size_t contract_h16_wave_bytes(const Layout& L, int T);
+size_t contract_h16_rowmax_bytes(const Layout& L);
+cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* xw, int T, const int* n_live,
+                              int w0, double* red, const int4* items, int n_items, float2* wave, unsigned* rowmax,
+                              int* status, long long timeout, cudaStream_t s);
 
 }  // namespace ext4pcf

@@ -23,6 +23,8 @@
 // Precision: BF16x3 splits every operand into bf16 hi + lo and accumulates
 // hi*hi + hi*lo + lo*hi (kind::f16); 3xTF32 does the same with tf32 hi + lo (kind::tf32,
 // ~22 mantissa bits per operand); TF32 uses one kind::tf32 pass.
+// The split-FP16 form has a kernel of its own (contract_h16.cu) with the same work items and
+// reduced output.
 // Every wait is bounded by a clock budget; on expiry the kernel records an error code, runs
 // to its end, waits for its own MMAs and copies and frees its TMEM.
 //
@@ -41,6 +43,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "kr_table.cuh"
 #include "tc_ptx.cuh"
 
 namespace ext4pcf {
@@ -54,85 +57,6 @@ constexpr int kThreads = kProducers + 64;  // + the MMA issuer warp and the TMA 
 constexpr uint32_t kTmemCols = 512;
 constexpr int kDCols = 128;          // D region: two 64-column buffers
 constexpr int kMaxNpad = 64;         // B columns: 2 * #mu * nb padded to 16 (nb <= 16)
-
-struct KF {
-  signed char arr, sgn, off, conj;  // arr 0: G, 1: W; index n = sgn * var + off
-};
-struct KRType {
-  signed char xconj;  // 0: x, 1: x^*, 2: w
-  KF B, C;            // row factors B(Th2; n2), C(Th3; n3)
-  signed char nmu;
-  signed char mu[2];
-  KF A[2];            // column factors A(Th1; s)
-};
-
-// Khatri-Rao row types and the components that use them
-#define EXT4PCF_KR_TABLE                                                                                  \
-  {                                                                                                     \
-    {0, {0, -1, -2, 0}, {0, -1, -3, 0}, 2, {0, 2}, {{0, 1, -3, 0}, {0, -1, -1, 1}}},                    \
-    {0, {0, 1, -2, 1}, {0, -1, -3, 0}, 1, {3, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},                       \
-    {0, {0, -1, -2, 0}, {0, 1, -1, 1}, 1, {4, 0}, {{0, 1, -3, 0}, {0, 0, 0, 0}}},                       \
-    {1, {0, -1, -2, 0}, {0, -1, -1, 0}, 2, {1, 5}, {{0, 1, -1, 0}, {0, -1, -3, 1}}},                    \
-    {1, {0, 1, -2, 1}, {0, -1, -1, 0}, 1, {6, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},                       \
-    {1, {0, -1, -2, 0}, {0, 1, -3, 1}, 1, {7, 0}, {{0, 1, -1, 0}, {0, 0, 0, 0}}},                       \
-    {2, {1, -1, 0, 0}, {1, -1, 0, 0}, 1, {8, 0}, {{1, 1, 0, 0}, {0, 0, 0, 0}}},                         \
-  }
-__constant__ KRType kKR[7] = EXT4PCF_KR_TABLE;
-// host copy of the same initializer (inspection through ext4pcf_contraction_tables)
-const KRType kKRHost[7] = EXT4PCF_KR_TABLE;
-constexpr int kKRTypes = 7;
-
-bool same_kf(KF a, KF b) { return a.arr == b.arr && a.sgn == b.sgn && a.off == b.off && a.conj == b.conj; }
-
-// Partner mu' and offset o of every component under the exchange of Theta2 and Theta3, from
-// the factor table: the centre factor and the column factor A(s) (s = n2 + n3 is kept) must be
-// the same, and the row factors must trade places, B'(n3 + o) = C(n3) and C'(n2 - o) = B(n2).
-// Returns false if a component has no partner.
-bool derive_swap_map(signed char mup[9], signed char off[9]) {
-  for (int mu = 0; mu < 9; ++mu) {
-    int t = -1, g = 0;
-    for (int k = 0; k < kKRTypes && t < 0; ++k)
-      for (int j = 0; j < kKRHost[k].nmu; ++j)
-        if (kKRHost[k].mu[j] == mu) { t = k; g = j; }
-    if (t < 0) return false;
-    const KRType& a = kKRHost[t];
-    bool found = false;
-    for (int k = 0; k < kKRTypes && !found; ++k)
-      for (int j = 0; j < kKRHost[k].nmu && !found; ++j) {
-        const KRType& b = kKRHost[k];
-        if (b.xconj != a.xconj || !same_kf(b.A[j], a.A[g])) continue;
-        for (int o = -1; o <= 1 && !found; ++o) {
-          KF bB = b.B, bC = b.C;  // B'(n3 + o) = C(n3): sgn' = sgn_C, off' + sgn' o = off_C
-          if (bB.arr != a.C.arr || bB.conj != a.C.conj || bB.sgn != a.C.sgn || bB.off + bB.sgn * o != a.C.off) continue;
-          if (bC.arr != a.B.arr || bC.conj != a.B.conj || bC.sgn != a.B.sgn || bC.off - bC.sgn * o != a.B.off) continue;
-          mup[mu] = b.mu[j];
-          off[mu] = (signed char)o;
-          found = true;
-        }
-      }
-    if (!found) return false;
-  }
-  return true;
-}
-
-// offset o shared by the components of row type t (the rows of a type serve all its components)
-int type_offset(int t, const signed char off[9]) {
-  const int o = off[kKRHost[t].mu[0]];
-  for (int j = 1; j < kKRHost[t].nmu; ++j)
-    if (off[kKRHost[t].mu[j]] != o) return 99;
-  return o;
-}
-
-// bin pair p -> (b2, b3), b2 <= b3, pairs in row-major order of (b2, b3)
-__device__ __forceinline__ void pair_of(int p, int nb, int& b2, int& b3) {
-  int b = 0, first = 0;
-  while (p >= first + (nb - b)) {
-    first += nb - b;
-    ++b;
-  }
-  b2 = b;
-  b3 = b + (p - first);
-}
 
 // bf16 hi/lo split of a pair (re, im) packed as bf16x2 (re in the low half)
 __device__ __forceinline__ void split_bf16(float re, float im, uint32_t& hi, uint32_t& lo) {
@@ -155,7 +79,6 @@ struct TcArgs {
   const int4* items;  // (type, s, row0, nrows | (n2 of row 0 of the s block + 64) << 8)
   int n_items;
   int row_g, row_w;   // first row of G and of W in the transposed wave array (x~B rows from 0)
-  const unsigned* rowmax;  // split-FP16 form: largest |component| of every staged row (float bits)
   int in_stages;      // depth of the staged-input ring
   int stage_rows;     // rows per staged stage and half (multiple of 8)
   long long timeout;
@@ -168,8 +91,6 @@ struct TcArgs {
 //   rows [row_g, row_w)   G_n(bin), n in [-2N-3, 2N-1]
 //   rows [row_w, rows)    W_m(bin), m in [0, 2N]
 // x~ B: 0: x G[-n2-2]   1: x G[n2-2]^*   2: x^* G[-n2-2]   3: x^* G[n2-2]^*   4: w W[-n2] (|n2| <= N)
-constexpr int kXBTypes = 5;
-__constant__ signed char kXBOfType[7] = {0, 1, 0, 2, 3, 2, 4};
 
 __device__ __forceinline__ float2 wave_value(const Layout& L, const float2* __restrict__ rc, float2 x, float w,
                                              int r, int row_g, int row_w) {
@@ -200,7 +121,7 @@ __global__ void __launch_bounds__(256) transpose_wave_kernel(const Layout L, con
                                                              const float2* __restrict__ xw, int T,
                                                              const int* __restrict__ n_live, int w0, int Tp,
                                                              int row_g, int row_w, int rows,
-                                                             float2* __restrict__ out, unsigned* __restrict__ rowmax) {
+                                                             float2* __restrict__ out) {
   __shared__ float2 tile[32][33];
   const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   T = wave_centres(T, n_live, w0);
@@ -220,35 +141,7 @@ __global__ void __launch_bounds__(256) transpose_wave_kernel(const Layout L, con
     const int r = r0 + ty + 8 * k, c = c0 + tx;
     if (r < rows && c < Tp) out[(size_t)r * Tp + c] = tile[tx][ty + 8 * k];
   }
-  // largest |component| of every row over the wave (non-negative floats order as integers)
-  if (rowmax && ty == 0 && r0 + tx < rows) {
-    float m = 0.f;
-    for (int c = 0; c < 32; ++c) m = fmaxf(m, fmaxf(fabsf(tile[c][tx].x), fabsf(tile[c][tx].y)));
-    if (m > 0.f) atomicMax(&rowmax[r0 + tx], __float_as_uint(m));
-  }
 }
-
-// fp16 hi/lo split of a pair (re, im) packed as f16x2 (re in the low half); the values are
-// scaled into the fp16 range by the caller
-__device__ __forceinline__ void split_f16(float re, float im, uint32_t& hi, uint32_t& lo) {
-  uint32_t h;
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(im), "f"(re));
-  float hr, hm;
-  asm("{\n .reg .b16 a, b;\n mov.b32 {a, b}, %2;\n cvt.f32.f16 %0, a;\n cvt.f32.f16 %1, b;\n}\n"
-      : "=f"(hr), "=f"(hm)
-      : "r"(h));
-  uint32_t l;
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(im - hm), "f"(re - hr));
-  hi = h;
-  lo = l;
-}
-
-// Power-of-two scale of the split-FP16 form: 2^k with |value| * 2^k <= 2^14 for every value
-// whose magnitude is at most 2^e (k = 14 - e, limited to +-100; 2^k as a float)
-__device__ __forceinline__ int f16_scale_exp(int e) { return max(-100, min(100, 14 - e)); }
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
-// exponent e with |x| <= 2^e for 0 <= x (x = 0 gives a large negative e)
-__device__ __forceinline__ int bound_exp(float x) { return x > 0.f ? ilogbf(x) + 1 : -200; }
 
 // Rows of the transposed array holding factor f for its variable in [va, vb]; `lo` is the
 // first multipole index (n for G, m = |n| for W).
@@ -342,9 +235,6 @@ template <> struct TcPrec<EXT4PCF_TF32> {  // A: fp32 (re, im) pairs; B: two ato
 template <> struct TcPrec<EXT4PCF_3XTF32> {  // A: hi | lo fp32 pairs; B: hi 2 atoms | lo 2 atoms
   static constexpr int kStages = 3, kStageCols = 128, kAtoms = 4;
 };
-template <> struct TcPrec<EXT4PCF_SPLIT_F16> {  // as BF16x3, fp16 halves of scaled values
-  static constexpr int kStages = 4, kStageCols = 64, kAtoms = 2;
-};
 
 // Warp roles: warps 0..15 form the A operand (Khatri-Rao rows, TMEM) and the B operand
 // (shared memory) of each stage; warp 16 issues the MMAs (one thread); warp 17 stages each
@@ -359,9 +249,8 @@ template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
 contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) {
   using P = TcPrec<PREC>;
-  // kind::f16 operands: bf16 or fp16 halves, one 32-bit word per centre (re, im)
-  constexpr bool k16 = PREC == EXT4PCF_SPLIT_BF16 || PREC == EXT4PCF_SPLIT_F16;
-  constexpr bool kScaled = PREC == EXT4PCF_SPLIT_F16;
+  // kind::f16 operands: bf16 halves, one 32-bit word per centre (re, im)
+  constexpr bool k16 = PREC == EXT4PCF_SPLIT_BF16;
   constexpr int kSt = P::kStages;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
@@ -491,25 +380,6 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
         bre[j] = sw128_word_off(2 * v, kw, kMaxNpad);
         bim[j] = sw128_word_off(2 * v + 1, kw, kMaxNpad);
       }
-      // split-FP16 form: power-of-two scales of this row (x~B times C, bounded by twice the
-      // product of the two rows' largest components) and of the B columns this warp forms
-      int krow = 0, kcol[2] = {0, 0};
-      float scrow = 1.f, sccol[2] = {1.f, 1.f};
-      if constexpr (kScaled) {
-        const int xrow = g.bx.row0 + (eB - g.sx), crow = g.bc.row0 + (eC - g.sc);
-        krow = f16_scale_exp(bound_exp(__uint_as_float(args.rowmax[xrow])) +
-                             bound_exp(__uint_as_float(args.rowmax[crow])) + 1);
-        scrow = pow2f(krow);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int v = warp + j * kProducerWarps;
-          if (v < nv) {
-            const int arow = v < nb ? g.ba0.row0 + (eAv[j] - g.sa0) : g.ba1.row0 + (eAv[j] - g.sa1);
-            kcol[j] = f16_scale_exp(bound_exp(__uint_as_float(args.rowmax[arow])));
-            sccol[j] = pow2f(kcol[j]);
-          }
-        }
-      }
       float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
 #pragma unroll
       for (int j = 0; j < 16; ++j) accD[j] = 0.f;
@@ -541,17 +411,7 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
           if (warp + j * kProducerWarps >= nv) break;
           float2 a = *reinterpret_cast<const float2*>(st + aoff[j]);
           if (cjAv[j]) a.y = -a.y;
-          if constexpr (kScaled) {
-            uint32_t rh, rl, ih, il;  // column re: (Ar, -Ai), column im: (Ai, Ar), f16x2 each
-            a.x *= sccol[j];
-            a.y *= sccol[j];
-            split_f16(a.x, -a.y, rh, rl);
-            split_f16(a.y, a.x, ih, il);
-            *reinterpret_cast<uint32_t*>(bt + bre[j]) = rh;
-            *reinterpret_cast<uint32_t*>(bt + tile_bytes + bre[j]) = rl;
-            *reinterpret_cast<uint32_t*>(bt + bim[j]) = ih;
-            *reinterpret_cast<uint32_t*>(bt + tile_bytes + bim[j]) = il;
-          } else if (PREC == EXT4PCF_SPLIT_BF16) {
+          if (PREC == EXT4PCF_SPLIT_BF16) {
             uint32_t rh, rl, ih, il;  // column re: (Ar, -Ai), column im: (Ai, Ar), bf16x2 each
             split_bf16(a.x, -a.y, rh, rl);
             split_bf16(a.y, a.x, ih, il);
@@ -585,18 +445,7 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
           cvv[2 * q + 1] = make_float2(tc.z, tc.w);
         }
         const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kDCols + aslot * P::kStageCols;
-        if constexpr (kScaled) {
-          uint32_t w[16];
-#pragma unroll
-          for (int j = 0; j < kQuarter; ++j) {
-            const float2 xb = xbv[j];
-            float2 cv = cvv[j];
-            cv.y *= sgnC;
-            split_f16((xb.x * cv.x - xb.y * cv.y) * scrow, (xb.x * cv.y + xb.y * cv.x) * scrow, w[j], w[8 + j]);
-          }
-          tmem_st8(acol + quarter * 8, w);
-          tmem_st8(acol + 32 + quarter * 8, w + 8);
-        } else if (PREC == EXT4PCF_SPLIT_BF16) {
+        if (PREC == EXT4PCF_SPLIT_BF16) {
           uint32_t w[16];
 #pragma unroll
           for (int j = 0; j < kQuarter; ++j) {
@@ -659,16 +508,8 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
             const int mu = ga ? mu1 : mu0;
             const size_t o = ((((size_t)mu * nx + (n2 + N + 1)) * nx + (n3 + N + 1)) * nb + b1) * npairs + pr;
             double* p = args.red + 2 * o;
-            double unscale = 1.0;
-            if constexpr (kScaled) {  // exact: both scales are powers of two
-              bool cj;
-              const int arow = ga ? g.ba1.row0 + blk_index(g.ba1, kr.A[1], g.s, b1, nb, cj)
-                                  : g.ba0.row0 + blk_index(g.ba0, kr.A[0], g.s, b1, nb, cj);
-              const int kc = f16_scale_exp(bound_exp(__uint_as_float(args.rowmax[arow])));
-              unscale = ldexp(1.0, -(krow + kc));
-            }
-            p[0] += (double)accD[j] * unscale;
-            p[1] += (double)accD[j + 1] * unscale;
+            p[0] += (double)accD[j];
+            p[1] += (double)accD[j + 1];
           }
         }
       }
@@ -681,8 +522,7 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
       for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
         const KRType kr = kKR[args.items[it].x];
         const int npad = (2 * kr.nmu * nb + 15) / 16 * 16;
-        const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad)
-                            : PREC == EXT4PCF_SPLIT_F16 ? idesc(0u, npad) : idesc(2u, npad);
+        const uint32_t id = PREC == EXT4PCF_SPLIT_BF16 ? idesc(1u, npad) : idesc(2u, npad);
         for (int k = 0; k < nstage; ++k, ++qa) {
           const long long gg = gs + k / kPromote;
           const int buf = (int)(gg & 1);
@@ -823,9 +663,8 @@ cudaError_t launch_tc(const TcArgs& a, const CUtensorMap& tm, size_t smem, int s
 }  // namespace
 
 bool tc_supported(const Layout& L, int precision) {
-  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32 && precision != EXT4PCF_3XTF32 &&
-      precision != EXT4PCF_SPLIT_F16)
-    return false;
+  if (precision == EXT4PCF_SPLIT_F16) return h16_supported(L);
+  if (precision != EXT4PCF_SPLIT_BF16 && precision != EXT4PCF_TF32 && precision != EXT4PCF_3XTF32) return false;
   return L.nb >= 1 && 4 * L.nb <= kMaxNpad && tc_in_stages(L.nb, L.N, precision) >= 2;
 }
 
@@ -856,11 +695,11 @@ bool tc_build_items(const Layout& L, std::vector<int4>& items) {
 int tc_wave_rows(const Layout& L) { return (kXBTypes * (2 * L.N + 3) + L.nG + L.nW) * L.nb; }
 int tc_wave_pitch(int T) { return (T + 31) / 32 * 32; }
 
-size_t contract_tc_xb_bytes(const Layout& L, int T) {
+size_t contract_tc_xb_bytes(const Layout& L, int T, int precision) {
+  if (precision == EXT4PCF_SPLIT_F16) return contract_h16_wave_bytes(L, T);
   return (size_t)tc_wave_rows(L) * tc_wave_pitch(T) * sizeof(float2);
 }
 
-size_t contract_tc_rowmax_bytes(const Layout& L) { return (size_t)tc_wave_rows(L) * sizeof(unsigned); }
 
 size_t tc_reduced_doubles(const Layout& L) {
   const size_t nx = 2 * L.N + 3;
@@ -938,43 +777,49 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 }
 }  // namespace
 
+// 2D tensor map of a wave array of 8-byte elements: x elements per row (row_bytes apart), `rows`
+// rows, boxes of 16 x 8 elements with the 128-byte swizzle
+cudaError_t encode_wave_tmap(CUtensorMap* tm, const void* base, uint64_t x, uint64_t rows, uint64_t row_bytes) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)x, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+  const cuuint32_t box[2] = {16, 8};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, const int* n_live,
                              int w0, double* red, int precision, const int4* items, int n_items, float2* wave,
                              unsigned* rowmax, int* status, long long timeout, cudaStream_t s) {
+  if (precision == EXT4PCF_SPLIT_F16)
+    return contract_wave_h16(L, rec, xw, T, n_live, w0, red, items, n_items, wave, rowmax, status, timeout, s);
   if (T <= 0) return cudaSuccess;
   const int rows = tc_wave_rows(L), pitch = tc_wave_pitch(T);
   const int row_g = kXBTypes * (2 * L.N + 3) * L.nb, row_w = row_g + L.nG * L.nb;
-  const bool scaled = precision == EXT4PCF_SPLIT_F16;
-  if (scaled) {
-    cudaError_t e = cudaMemsetAsync(rowmax, 0, (size_t)rows * sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-  }
   {
     dim3 grid((rows + 31) / 32, (T + 31) / 32);
-    transpose_wave_kernel<<<grid, 256, 0, s>>>(L, rec, xw, T, n_live, w0, pitch, row_g, row_w, rows, wave,
-                                               scaled ? rowmax : nullptr);
+    transpose_wave_kernel<<<grid, 256, 0, s>>>(L, rec, xw, T, n_live, w0, pitch, row_g, row_w, rows, wave);
     ++g_launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
-  if (!enc) return cudaErrorNotSupported;
   // 2D view: x = centre (T of them, pitch elements per row), y = row; boxes of 16 centres
   // (128 bytes, the swizzle span) by 8 rows; centres past T read as zero
   CUtensorMap tm;
-  const cuuint64_t dims[2] = {(cuuint64_t)T, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float2)};
-  const cuuint32_t box[2] = {16, (cuuint32_t)kBoxRows};
-  const cuuint32_t estr[2] = {1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, wave, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaErrorInvalidValue;
+  {
+    cudaError_t e = encode_wave_tmap(&tm, wave, (uint64_t)T, (uint64_t)rows, (uint64_t)pitch * sizeof(float2));
+    if (e != cudaSuccess) return e;
+  }
   TcArgs a;
   a.L = L; a.T = T; a.n_live = n_live; a.w0 = w0; a.red = red;
   a.npairs = L.nb * (L.nb + 1) / 2;
   a.items = items; a.n_items = n_items;
   a.row_g = row_g; a.row_w = row_w;
-  a.rowmax = rowmax;
   a.in_stages = tc_in_stages(L.nb, L.N, precision);
   a.stage_rows = stage_rows_for(L.nb, L.N);
   a.timeout = timeout; a.status = status;
@@ -985,7 +830,6 @@ cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* x
   const size_t smem = tc_smem_bytes(L.nb, L.N, precision);
   cudaError_t e;
   if (precision == EXT4PCF_SPLIT_BF16) e = launch_tc<EXT4PCF_SPLIT_BF16>(a, tm, smem, sms, s);
-  else if (precision == EXT4PCF_SPLIT_F16) e = launch_tc<EXT4PCF_SPLIT_F16>(a, tm, smem, sms, s);
   else if (precision == EXT4PCF_TF32) e = launch_tc<EXT4PCF_TF32>(a, tm, smem, sms, s);
   else e = launch_tc<EXT4PCF_3XTF32>(a, tm, smem, sms, s);
   ++g_launches;

@@ -2,6 +2,9 @@
 // tensor-memory loads/stores, shared-memory matrix descriptors, the MMA issue and commit,
 // and the hi/lo operand splits.
 #pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace ext4pcf {
@@ -140,4 +143,9 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
 }
 
 }  // namespace
+
+// contract_tc.cu: 2D tensor map of a wave array of 8-byte elements (x per row, `rows` rows,
+// row_bytes apart), boxes of 16 x 8 elements with the 128-byte swizzle
+cudaError_t encode_wave_tmap(CUtensorMap* tm, const void* base, uint64_t x, uint64_t rows, uint64_t row_bytes);
+
 }  // namespace ext4pcf
