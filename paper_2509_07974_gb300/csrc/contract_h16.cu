@@ -12,8 +12,15 @@
 //    range, with no per-value scaling in the kernel; the epilogue takes out the exact factor
 //    2^-(k_B + k_C + k_A).
 //  * Planar staging.  Per 16 centres a row holds their 16 real parts, then their 16 imaginary
-//    parts (128 bytes, one TMA box row), so that two centres' real (or imaginary) parts form
-//    one 64-bit register pair and the complex products run on the packed f32x2 pipe.
+//    parts (128 bytes), so that two centres' real (or imaginary) parts form one 64-bit register
+//    pair and the complex products run on the packed f32x2 pipe.
+//  * Stage-major wave array.  The array is laid out [stage of 64 centres][row][512 bytes], the
+//    16-byte chunks of every 128-byte quarter XOR-permuted by the row index mod 8 (the 128-byte
+//    swizzle, applied by the transpose).  The rows a work item needs for one stage (its x~B,
+//    C and A blocks) are then four contiguous ranges, fetched with four plain bulk copies
+//    (cp.async.bulk) instead of one tensor box per 8 rows and 16 centres: the copy engine's
+//    per-request cost, not bandwidth, bounded the boxed staging.  Eight lanes reading eight
+//    consecutive rows at the same logical chunk hit eight different bank groups.
 //  * K order.  In every group of 8 centres (one MMA, K = 16 halves) K = 0..7 holds the real
 //    and K = 8..15 the imaginary parts of the row values; the column operand holds (A_r, -A_i)
 //    for the real and (A_i, A_r) for the imaginary output at the same K.
@@ -41,7 +48,6 @@ namespace ext4pcf {
 namespace {
 
 constexpr int kHCentres = 64;                        // centres per stage
-constexpr int kHCols = kHCentres / 16;               // TMA box columns (16 centres) per stage
 constexpr int kHProducerWarps = 16;
 constexpr int kHThreads = kHProducerWarps * 32 + 64; // + the MMA issuer and the TMA loader warp
 constexpr int kHWarpMma = kHProducerWarps, kHWarpLoad = kHProducerWarps + 1;
@@ -125,14 +131,15 @@ __global__ void __launch_bounds__(256) hwave_rowmax_kernel(const Layout L, const
   }
 }
 
-// The transposed, scaled, planar wave array: row r, centre c at r * pitch2 + (c / 16) * 32 +
-// (c % 16) (real part) and + 16 (imaginary part), pitch2 = 2 * pitch floats.  Centres from the
-// wave's count to the next multiple of 64 are written as zeros (the last stage reads them).
+// The transposed, scaled, planar wave array, stage-major: centre c of row r sits in stage
+// c / 64 at float (c / 64 * rows + r) * 128 + q * 32 + ((k ^ (r % 8)) * 4) + c % 4, with
+// q = (c % 64) / 16 the quarter and k = (c % 16) / 4 (real part) or 4 + (c % 16) / 4
+// (imaginary part) the logical 16-byte chunk.  Centres from the wave's count to the next
+// multiple of 64 are written as zeros (the last stage reads them).
 __global__ void __launch_bounds__(256) hwave_transpose_kernel(const Layout L, const float2* __restrict__ rec,
                                                               const float2* __restrict__ xw, int T,
-                                                              const int* __restrict__ n_live, int w0, int pitch2,
-                                                              int row_g, int row_w, int rows,
-                                                              const unsigned* __restrict__ rowmax,
+                                                              const int* __restrict__ n_live, int w0, int row_g,
+                                                              int row_w, int rows, const unsigned* __restrict__ rowmax,
                                                               float* __restrict__ out) {
   __shared__ float2 tile[32][33];
   const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
@@ -155,9 +162,10 @@ __global__ void __launch_bounds__(256) hwave_transpose_kernel(const Layout L, co
     if (r < rows) {
       const float sc = h_pow2f(h_scale_exp(rowmax[r]));
       const float2 v = tile[tx][ty + 8 * k];
-      float* o = out + (size_t)r * pitch2 + (c >> 4) * 32 + (c & 15);
-      o[0] = v.x * sc;
-      o[16] = v.y * sc;
+      const int q = (c & 63) >> 4, kre = (c & 15) >> 2, sw = r & 7;
+      float* o = out + ((size_t)(c >> 6) * rows + r) * 128 + q * 32 + (c & 3);
+      o[(kre ^ sw) * 4] = v.x * sc;
+      o[((4 + kre) ^ sw) * 4] = v.y * sc;
     }
   }
 }
@@ -173,8 +181,10 @@ struct HArgs {
   int n_items;
   int row_g, row_w;   // first G row and first W row of the wave array
   const unsigned* rowmax;  // largest |component| per row (float bits): the row scales
+  const float* wave;  // the stage-major wave array
+  int rows;           // its rows
   int in_stages;      // staged-input ring depth
-  int stage_rows;     // rows per staged stage (multiple of 8)
+  int stage_rows;     // rows per staged stage
   int npad_max;       // rows of a B tile: 2 * 2 * nb rounded up to 16
   long long timeout;
   int* status;
@@ -200,13 +210,12 @@ __device__ __forceinline__ int hblk_index(const HBlk& k, KF f, int v, int b, int
 }
 
 // Geometry of one work item: the staged blocks (x~B rows, C rows, A rows) and their first
-// rows in a staged stage (each block starts at a multiple of 8 rows: one TMA box)
+// rows in a staged stage (packed one after the other)
 struct HGeo {
   int s, row0, nrows, n2a, t2a, t2b;
   HBlk bx, bc, ba0, ba1;
   int sx, sc, sa0, sa1;
 };
-__device__ __forceinline__ int hround8(int v) { return (v + 7) & ~7; }
 __device__ __forceinline__ HGeo hgeo(const HArgs& a, int4 item, const KRType& kr) {
   const int nb = a.L.nb, N = a.L.N, nx = 2 * N + 3;
   HGeo g;
@@ -223,9 +232,9 @@ __device__ __forceinline__ HGeo hgeo(const HArgs& a, int4 item, const KRType& kr
   g.ba0 = hblk(a, kr.A[0], g.s, g.s);
   g.ba1 = kr.nmu > 1 ? hblk(a, kr.A[1], g.s, g.s) : HBlk{0, 0, 0};
   g.sx = 0;
-  g.sc = hround8(g.bx.len);
-  g.sa0 = g.sc + hround8(g.bc.len);
-  g.sa1 = g.sa0 + hround8(g.ba0.len);
+  g.sc = g.bx.len;
+  g.sa0 = g.sc + g.bc.len;
+  g.sa1 = g.sa0 + g.ba0.len;
   return g;
 }
 
@@ -274,31 +283,31 @@ __device__ __forceinline__ void sts_32(uint32_t addr, uint32_t v) {
 
 // The Khatri-Rao values of one row for 8 centres (group h of the thread's 16): x~B at PB, C at
 // PC (shared addresses of the rows in the staged stage, swizzle term folded in: chunk c is at
-// P ^ (c << 4)); CJ: C enters conjugated.  Writes hi / lo words 8h .. 8h+7: four pairs of real
-// parts, then four pairs of imaginary parts.
+// P ^ (c << 4)); CJ: C enters conjugated.  Writes hi / lo words 0..7: four pairs of real parts,
+// then four pairs of imaginary parts.  One 16-byte chunk (four centres) at a time.
 template <bool CJ>
 __device__ __forceinline__ void kr_group(uint32_t PB, uint32_t PC, int h, uint32_t* hi, uint32_t* lo) {
-  unsigned long long xr[4], xi[4], cr[4], ci[4];
-  lds_2x64(PB ^ ((2 * h) << 4), xr[0], xr[1]);
-  lds_2x64(PB ^ ((2 * h + 1) << 4), xr[2], xr[3]);
-  lds_2x64(PB ^ ((4 + 2 * h) << 4), xi[0], xi[1]);
-  lds_2x64(PB ^ ((5 + 2 * h) << 4), xi[2], xi[3]);
-  lds_2x64(PC ^ ((2 * h) << 4), cr[0], cr[1]);
-  lds_2x64(PC ^ ((2 * h + 1) << 4), cr[2], cr[3]);
-  lds_2x64(PC ^ ((4 + 2 * h) << 4), ci[0], ci[1]);
-  lds_2x64(PC ^ ((5 + 2 * h) << 4), ci[2], ci[3]);
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    unsigned long long re, im;
-    if (CJ) {  // x~B conj(C)
-      re = f2fma(xi[p], ci[p], f2mul(xr[p], cr[p]));
-      im = f2sub(f2mul(xi[p], cr[p]), f2mul(xr[p], ci[p]));
-    } else {
-      re = f2sub(f2mul(xr[p], cr[p]), f2mul(xi[p], ci[p]));
-      im = f2fma(xr[p], ci[p], f2mul(xi[p], cr[p]));
+  for (int c = 0; c < 2; ++c) {
+    const uint32_t re_off = (uint32_t)(2 * h + c) << 4, im_off = (uint32_t)(4 + 2 * h + c) << 4;
+    unsigned long long xr[2], xi[2], cr[2], ci[2];
+    lds_2x64(PB ^ re_off, xr[0], xr[1]);
+    lds_2x64(PB ^ im_off, xi[0], xi[1]);
+    lds_2x64(PC ^ re_off, cr[0], cr[1]);
+    lds_2x64(PC ^ im_off, ci[0], ci[1]);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      unsigned long long re, im;
+      if (CJ) {  // x~B conj(C)
+        re = f2fma(xi[p], ci[p], f2mul(xr[p], cr[p]));
+        im = f2sub(f2mul(xi[p], cr[p]), f2mul(xr[p], ci[p]));
+      } else {
+        re = f2sub(f2mul(xr[p], cr[p]), f2mul(xi[p], ci[p]));
+        im = f2fma(xr[p], ci[p], f2mul(xi[p], cr[p]));
+      }
+      split_h2(re, hi[2 * c + p], lo[2 * c + p]);
+      split_h2(im, hi[4 + 2 * c + p], lo[4 + 2 * c + p]);
     }
-    split_h2(re, hi[8 * h + p], lo[8 * h + p]);
-    split_h2(im, hi[8 * h + 4 + p], lo[8 * h + 4 + p]);
   }
 }
 
@@ -310,7 +319,7 @@ __device__ __forceinline__ void kr_group(uint32_t PB, uint32_t PC, int h, uint32
 //   A and B       ab_full [16 producer warps] / ab_empty [1, tcgen05.commit]
 //   partial sums  dfull [1, tcgen05.commit] / dempty [16 producer warps]
 __global__ void __launch_bounds__(kHThreads, 1)
-contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) {
+contract_h16_kernel(const HArgs args) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const Layout L = args.L;
@@ -318,8 +327,7 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t atom_bytes = (uint32_t)args.npad_max * 128u;  // one 128-byte-wide K-atom of a B tile
   const uint32_t bslot_bytes = 4u * atom_bytes;                  // hi tile (2 atoms) | lo tile (2 atoms)
-  const uint32_t col_bytes = (uint32_t)args.stage_rows * 128u;   // one box column of a staged stage
-  const uint32_t in_bytes = kHCols * col_bytes;
+  const uint32_t in_bytes = (uint32_t)args.stage_rows * 512u;    // one staged stage: rows of 512 bytes
   const int S_in = args.in_stages;
   unsigned char* in_base = sm + kHSlots * bslot_bytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(in_base + (size_t)S_in * in_bytes);
@@ -356,7 +364,6 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kHWarpLoad && lane == 0) tma_prefetch_desc(&tmap);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -405,30 +412,36 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
       const int eB = g.sx + (n2 - g.t2a) * nb + b2;
       const int eC = g.sc + hblk_index(g.bc, kr.C, n3, b3, nb);
       const bool cjC = kr.C.conj != 0;
-      // this row's x~B and C rows in box column qq of a staged stage, swizzle term folded in
-      const uint32_t xB0 = qq * col_bytes + (uint32_t)eB * 128u + ((uint32_t)(eB & 7) << 4);
-      const uint32_t xC0 = qq * col_bytes + (uint32_t)eC * 128u + ((uint32_t)(eC & 7) << 4);
+      // this row's x~B and C rows, quarter qq, in a staged stage, with the swizzle term of their
+      // rows in the wave array folded in (chunk c at P ^ (c << 4))
+      const int rB = g.bx.row0 + (eB - g.sx), rC = g.bc.row0 + (eC - g.sc);
+      const uint32_t xB0 = (uint32_t)eB * 512u + qq * 128u + ((uint32_t)(rB & 7) << 4);
+      const uint32_t xC0 = (uint32_t)eC * 512u + qq * 128u + ((uint32_t)(rC & 7) << 4);
       // the B columns this warp forms: column pairs v = warp, warp + 16 (component slot v / nb,
       // Th1 = v % nb); lane = centres 2 lane, 2 lane + 1 of the stage
-      uint32_t aoff[2][2], boff[2][4], msk[2];
+      // shared offsets: aoff = the lane's two real parts of A (the imaginary parts: chunk + 4,
+      // i.e. ^ 64); boff[o] = the real-part K word of output o (0: real, 1: imaginary) in the
+      // hi tile (the imaginary-part K word: the next chunk, i.e. ^ 16)
+      uint32_t aoff[2], boff[2][2], msk[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int v = warp + j * kHProducerWarps;
-        int eA = 0;
+        int eA = 0, rA = 0;
         bool cj = false;
         if (v < nv) {
           const int b1 = v % nb;
           if (v < nb) {
             eA = g.sa0 + hblk_index(g.ba0, kr.A[0], g.s, b1, nb);
+            rA = g.ba0.row0 + (eA - g.sa0);
             cj = kr.A[0].conj != 0;
           } else {
             eA = g.sa1 + hblk_index(g.ba1, kr.A[1], g.s, b1, nb);
+            rA = g.ba1.row0 + (eA - g.sa1);
             cj = kr.A[1].conj != 0;
           }
         }
-        const uint32_t rowA = (uint32_t)(lane >> 3) * col_bytes + (uint32_t)eA * 128u + (lane & 1) * 8;
-        aoff[j][0] = rowA + ((uint32_t)(((lane & 7) >> 1) ^ (eA & 7)) << 4);
-        aoff[j][1] = rowA + ((uint32_t)((4 + ((lane & 7) >> 1)) ^ (eA & 7)) << 4);
+        aoff[j] = (uint32_t)eA * 512u + (uint32_t)(lane >> 3) * 128u + (lane & 1) * 8 +
+                  ((uint32_t)(((lane & 7) >> 1) ^ (rA & 7)) << 4);
         // real output: K_re <- A_r, K_im <- -A_i (conj A: +A_i); imaginary output: K_re <- A_i
         // (conj: -A_i), K_im <- A_r
         msk[j] = cj ? 0u : 0x80008000u;
@@ -438,30 +451,45 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
 #pragma unroll
         for (int o = 0; o < 2; ++o) {
           const int n = 2 * v + o;
-          const uint32_t rowb = atom + (uint32_t)(n >> 3) * 1024u + (uint32_t)(n & 7) * 128u + within;
-          boff[j][2 * o] = rowb + ((uint32_t)(ch ^ (n & 7)) << 4);
-          boff[j][2 * o + 1] = rowb + ((uint32_t)((ch + 1) ^ (n & 7)) << 4);
+          boff[j][o] = atom + (uint32_t)(n >> 3) * 1024u + (uint32_t)(n & 7) * 128u + within +
+                       ((uint32_t)(ch ^ (n & 7)) << 4);
         }
       }
       float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
 #pragma unroll
       for (int j = 0; j < 16; ++j) accD[j] = 0.f;
       const bool has_cols = qq * 16 < npad;
-      auto promote = [&](long long gg) {  // read partial sum gg from its D buffer
+      // Software pipeline over the stages (k = this stage):
+      //  * the partial sum of stage k - 2 is read out of TMEM (tcgen05.ld issued mid-stage,
+      //    waited for at its end), then its D buffer is released;
+      //  * the rows of stage k - 1 were stored into TMEM at the end of the previous iteration;
+      //    their completion is awaited (and the MMA warp signalled) only after the first half
+      //    of this stage's rows is formed, so the store latency is hidden behind that work.
+      // The MMAs of stage k - 1 thus start one iteration late, which the three A/B slots absorb.
+      auto promote_issue = [&](long long gg, uint32_t* v) {
         const int buf = (int)(gg & 1);
         wait(&dfull[buf], (uint32_t)((gg >> 1) & 1));
         tc_fence_after();
+        if (has_cols) tmem_ld16(tmem + ((uint32_t)(grp * 32) << 16) + buf * 64 + qq * 16, v);
+      };
+      auto promote_finish = [&](long long gg, const uint32_t* v) {
         if (has_cols) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(grp * 32) << 16) + buf * 64 + qq * 16, v);
           tmem_wait_ld();
 #pragma unroll
           for (int j = 0; j < 16; ++j) accD[j] += __uint_as_float(v[j]);
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&dempty[buf]);
+        if (lane == 0) mbar_arrive(&dempty[(int)(gg & 1)]);
       };
+      auto publish = [&](int slot) {  // the rows (TMEM) and columns (shared) of a slot are complete
+        tmem_wait_st();
+        fence_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ab_full[slot]);
+      };
+      int prev_slot = 0;
       for (int k = 0; k < nstage; ++k) {
         wait(&in_full[islot], iph);
         wait(&ab_empty[aslot], aph ^ 1u);
@@ -473,49 +501,58 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
         for (int j = 0; j < 2; ++j) {
           if (warp + j * kHProducerWarps >= nv) break;
           uint32_t arh, arl, aih, ail;
-          split_h2(lds_64(st + aoff[j][0]), arh, arl);
-          split_h2(lds_64(st + aoff[j][1]), aih, ail);
+          split_h2(lds_64(st + aoff[j]), arh, arl);
+          split_h2(lds_64(st + (aoff[j] ^ 64u)), aih, ail);
           const uint32_t m1 = msk[j], m2 = msk[j] ^ 0x80008000u;
-          sts_32(bt + boff[j][0], arh);
-          sts_32(bt + boff[j][1], aih ^ m1);
-          sts_32(bt + boff[j][2], aih ^ m2);
-          sts_32(bt + boff[j][3], arh);
-          const uint32_t lt = bt + 2 * atom_bytes;
-          sts_32(lt + boff[j][0], arl);
-          sts_32(lt + boff[j][1], ail ^ m1);
-          sts_32(lt + boff[j][2], ail ^ m2);
-          sts_32(lt + boff[j][3], arl);
+          const uint32_t r0 = bt + boff[j][0], r1 = bt + boff[j][1], lt = 2 * atom_bytes;
+          sts_32(r0, arh);
+          sts_32(r0 ^ 16u, aih ^ m1);
+          sts_32(r1, aih ^ m2);
+          sts_32(r1 ^ 16u, arh);
+          sts_32(r0 + lt, arl);
+          sts_32((r0 ^ 16u) + lt, ail ^ m1);
+          sts_32(r1 + lt, ail ^ m2);
+          sts_32((r1 ^ 16u) + lt, arl);
         }
-        // A operand (TMEM): this row's Khatri-Rao values for the warp's 16 centres
-        uint32_t hi[16], lo[16];
+        // A operand (TMEM): this row's Khatri-Rao values for the warp's 16 centres, in two
+        // groups of 8; the previous stage is published between them
         const uint32_t PB = st + xB0, PC = st + xC0;
-        if (cjC) {
-          kr_group<true>(PB, PC, 0, hi, lo);
-          kr_group<true>(PB, PC, 1, hi, lo);
-        } else {
-          kr_group<false>(PB, PC, 0, hi, lo);
-          kr_group<false>(PB, PC, 1, hi, lo);
+        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kHDCols + aslot * kHACols + qq * 16;
+        {
+          uint32_t hi[8], lo[8];
+          if (cjC) kr_group<true>(PB, PC, 0, hi, lo);
+          else kr_group<false>(PB, PC, 0, hi, lo);
+          if (k >= 1) publish(prev_slot);
+          tmem_st8(acol, hi);
+          tmem_st8(acol + 64, lo);
         }
-        // every value this warp loaded from the staged stage has been used: it can be refilled
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&in_empty[islot]);
-        const uint32_t acol = tmem + ((uint32_t)(grp * 32) << 16) + kHDCols + aslot * kHACols;
-        tmem_st16(acol + qq * 16, hi);
-        tmem_st16(acol + 64 + qq * 16, lo);
-        tmem_wait_st();
-        fence_async_smem();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ab_full[aslot]);
+        uint32_t pv[16];
+        if (k >= 2) promote_issue(gs + k - 2, pv);
+        {
+          uint32_t hi[8], lo[8];
+          if (cjC) kr_group<true>(PB, PC, 1, hi, lo);
+          else kr_group<false>(PB, PC, 1, hi, lo);
+          // every value this warp loaded from the staged stage has been used: it can be refilled
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&in_empty[islot]);
+          tmem_st8(acol + 8, hi);
+          tmem_st8(acol + 64 + 8, lo);
+        }
+        if (k >= 2) promote_finish(gs + k - 2, pv);
+        prev_slot = aslot;
         if (++islot == S_in) { islot = 0; iph ^= 1u; }
         if (++aslot == kHSlots) { aslot = 0; aph ^= 1u; }
-        // the previous stage's partial sum is read while this stage's MMAs run
-        if (k >= 1) promote(gs + k - 1);
       }
-      if (nstage > 0) promote(gs + nstage - 1);
+      // drain the pipeline: the last stage's rows, then the last two partial sums
+      if (nstage >= 1) publish(prev_slot);
+      for (long long gg = gs + (nstage >= 2 ? nstage - 2 : 0); gg < gs + nstage; ++gg) {
+        uint32_t pv[16];
+        promote_issue(gg, pv);
+        promote_finish(gg, pv);
+      }
       gs += nstage;
       // ---------------------------------------------------------------- epilogue
-      if (row_ok && has_cols) {
+      if (row_ok && has_cols && nstage > 0) {  // (a wave past the end adds nothing)
         const int pr = rr % npairs, nx = 2 * N + 3;
         const int kx = h_scale_exp(args.rowmax[g.bx.row0 + (eB - g.sx)]);
         const int kc = h_scale_exp(args.rowmax[g.bc.row0 + (eC - g.sc)]);
@@ -577,7 +614,9 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
     }
     __syncwarp();
   } else if (warp == kHWarpLoad) {
-    // ---------------------------------------------------------------------- TMA loader
+    // ---------------------------------------------------------------------- bulk-copy loader
+    // One thread: per stage the four blocks of the item, each a contiguous range of the
+    // stage-major wave array, copied with one cp.async.bulk each.
     if (lane == 0) {
       int islot = 0;
       uint32_t iph = 0;
@@ -588,25 +627,26 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
         const HGeo g = hgeo(args, args.items[it], kr);
         const HBlk blk[4] = {g.bx, g.bc, g.ba0, g.ba1};
         const int srow[4] = {g.sx, g.sc, g.sa0, g.sa1};
-        if (g.sa1 + hround8(g.ba1.len) > args.stage_rows) {  // never for the supported shapes
+        bool ok = g.sa1 + g.ba1.len <= args.stage_rows;
+        for (int b = 0; b < 4; ++b)
+          ok = ok && (blk[b].len == 0 || (blk[b].row0 >= 0 && blk[b].row0 + blk[b].len <= args.rows));
+        if (!ok) {  // never for the supported shapes
           *abort_flag = 1;
           err = 1;
         }
-        uint32_t boxes = 0;
-        for (int b = 0; b < 4; ++b) boxes += (uint32_t)((blk[b].len + 7) / 8);
-        const uint32_t bytes = boxes * kHCols * 1024u;
+        const uint32_t bytes = (uint32_t)(g.sa1 + g.ba1.len) * 512u;
         for (int k = 0; k < nstage; ++k) {
           wait(&in_empty[islot], iph ^ 1u);
           if (!*abort_flag) {  // nothing more is copied once the CTA gives up
             last[islot] = (int)iph;
             mbar_expect_tx(&in_full[islot], bytes);
             unsigned char* st = in_base + (size_t)islot * in_bytes;
-            for (int b = 0; b < 4; ++b)
-              for (int r = 0; r < blk[b].len; r += 8)
+            const float* src = args.wave + (size_t)k * args.rows * 128;
 #pragma unroll
-                for (int c = 0; c < kHCols; ++c)
-                  tma_load_2d(st + c * col_bytes + (srow[b] + r) * 128, &tmap, k * kHCentres + c * 16,
-                              blk[b].row0 + r, &in_full[islot]);
+            for (int b = 0; b < 4; ++b)
+              if (blk[b].len > 0)
+                bulk_load(st + srow[b] * 512, src + (size_t)blk[b].row0 * 128, (uint32_t)blk[b].len * 512u,
+                          &in_full[islot]);
           }
           if (++islot == S_in) { islot = 0; iph ^= 1u; }
         }
@@ -627,25 +667,23 @@ contract_h16_kernel(const HArgs args, const __grid_constant__ CUtensorMap tmap) 
 }
 
 // rows per staged stage: the x~B and C blocks of at most the tile's n2 values (128 rows =
-// 128 / pairs values of n2, +2 for misalignment, at most 2N + 3) and two A blocks, each
-// rounded up to whole TMA boxes
+// 128 / pairs values of n2, +2 for misalignment, at most 2N + 3) and two A blocks
 int h_stage_rows(int nb, int N) {
   int rows = 128 / (nb * (nb + 1) / 2) + 2;
   if (rows > 2 * N + 3) rows = 2 * N + 3;
-  auto r8 = [](int v) { return (v + 7) & ~7; };
-  return 2 * r8(rows * nb) + 2 * r8(nb);
+  return 2 * rows * nb + 2 * nb;
 }
 int h_npad_max(int nb) { return (4 * nb + 15) / 16 * 16; }
 size_t h_fixed_smem(int nb) { return (size_t)kHSlots * 4 * h_npad_max(nb) * 128 + 1024 + 512; }
 int h_in_stages(int nb, int N) {
-  const size_t per = (size_t)h_stage_rows(nb, N) * 128 * kHCols;
+  const size_t per = (size_t)h_stage_rows(nb, N) * 512;
   const size_t room = 227 * 1024 - h_fixed_smem(nb);
   int k = (int)(room / per);
   if (k > kHMaxIn) k = kHMaxIn;
   return k >= 2 ? k : 0;
 }
 size_t h_smem_bytes(int nb, int N) {
-  return h_fixed_smem(nb) + (size_t)h_in_stages(nb, N) * h_stage_rows(nb, N) * 128 * kHCols;
+  return h_fixed_smem(nb) + (size_t)h_in_stages(nb, N) * h_stage_rows(nb, N) * 512;
 }
 
 }  // namespace
@@ -672,15 +710,9 @@ cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* 
   hwave_rowmax_kernel<<<dim3((rows + 31) / 32, (T + 127) / 128), 256, 0, s>>>(L, rec, xw, T, n_live, w0, row_g,
                                                                             row_w, rows, rowmax);
   hwave_transpose_kernel<<<dim3((rows + 31) / 32, pitch / 32), 256, 0, s>>>(
-      L, rec, xw, T, n_live, w0, 2 * pitch, row_g, row_w, rows, rowmax, reinterpret_cast<float*>(wave));
+      L, rec, xw, T, n_live, w0, row_g, row_w, rows, rowmax, reinterpret_cast<float*>(wave));
   g_launches += 2;
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // 2D view in 8-byte elements: x = 16-centre chunks' halves (pitch per row), y = row; boxes
-  // of 16 elements (128 bytes, the swizzle span: 16 centres' real, then imaginary parts) by 8
-  // rows.  Every stage reads below the padded count, so no box leaves the array along x.
-  CUtensorMap tm;
-  e = encode_wave_tmap(&tm, wave, (uint64_t)pitch, (uint64_t)rows, (uint64_t)pitch * sizeof(float2));
   if (e != cudaSuccess) return e;
   HArgs a;
   a.L = L; a.T = T; a.n_live = n_live; a.w0 = w0; a.red = red;
@@ -688,6 +720,8 @@ cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* 
   a.items = items; a.n_items = n_items;
   a.row_g = row_g; a.row_w = row_w;
   a.rowmax = rowmax;
+  a.wave = reinterpret_cast<const float*>(wave);
+  a.rows = rows;
   a.in_stages = h_in_stages(L.nb, L.N);
   a.stage_rows = h_stage_rows(L.nb, L.N);
   a.npad_max = h_npad_max(L.nb);
@@ -699,7 +733,7 @@ cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* 
   const size_t smem = h_smem_bytes(L.nb, L.N);
   e = cudaFuncSetAttribute(contract_h16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  contract_h16_kernel<<<sms, kHThreads, smem, s>>>(a, tm);
+  contract_h16_kernel<<<sms, kHThreads, smem, s>>>(a);
   ++g_launches;
   return cudaGetLastError();
 }

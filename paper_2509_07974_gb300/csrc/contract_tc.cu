@@ -498,7 +498,7 @@ contract_tc_kernel(const TcArgs args, const __grid_constant__ CUtensorMap tmap) 
       for (long long gg = gs0 + read_in_loop; gg < gs0 + nsub; ++gg) promote(gg);
       gs = gs0 + nsub;
       // ---------------------------------------------------------------- epilogue
-      if (row_ok) {
+      if (row_ok && nstage > 0) {  // (a wave past the end adds nothing)
         const int pr = rr % npairs, nx = 2 * N + 3;
 #pragma unroll
         for (int j = 0; j < 16; j += 2) {
