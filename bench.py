@@ -479,9 +479,10 @@ def run_ours(args):
                                   if tc_form else "complex multiply-adds of all ordered bin triples"}
     # DRAM bytes (read + write) of one full-size launch of the default configuration, from the
     # committed ncu summaries (null when the kernel source changed since the capture)
-    if args.precision == "3xtf32" and args.n_gal is None and args.centres is None:
+    if args.n_gal is None and args.centres is None:
         roof_g["traffic"] = measured_traffic("gather_kernel")
-        roof_c["traffic"] = measured_traffic("contract_tc_kernel")
+        roof_c["traffic"] = measured_traffic("contract_h16_kernel" if args.precision == "f16x3"
+                                             else "contract_tc_kernel" if tc_form else "contract_kernel")
         roof_g["traffic_unit"] = roof_c["traffic_unit"] = "bytes per launch (DRAM read + write, ncu)"
     roof_main, roof_other = (roof_c, roof_g) if c_ms >= g_ms else (roof_g, roof_c)
 
@@ -560,7 +561,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="3xtf32", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3", "f16x3"])
+    ap.add_argument("--precision", default="f16x3", choices=["fp64", "fp32", "tf32", "3xtf32", "bf16x3", "f16x3"])
     ap.add_argument("--oracle-centres", type=int, default=2000)
     ap.add_argument("--fp64-centres", type=int, default=4096)
     ap.add_argument("--no-baselines", action="store_true")

@@ -68,9 +68,10 @@ typedef enum {
   EXT4PCF_3XTF32 = 3,    /* as TF32 with hi/lo split operands, three passes */
   EXT4PCF_SPLIT_BF16 = 4,/* tensor-core contraction (kind::f16, bf16 hi/lo, three passes) */
   EXT4PCF_SPLIT_F16 = 5  /* kind::f16 with fp16 hi/lo (22 bits per operand, as 3XTF32), three
-                            passes at twice the tf32 rate; every staged row and column is
-                            scaled by a power of two so that its largest value over the wave
-                            maps to 2^14 (fp16 range), and the scale is undone exactly */
+                            passes at twice the tf32 rate; every row of the wave's multipoles
+                            is scaled by a power of two so that its largest component over the
+                            wave lies in [2^6, 2^7) (products stay below 2^15, inside the fp16
+                            range), and the scales are undone exactly in FP64 */
 } ext4pcf_precision;
 
 typedef struct {
