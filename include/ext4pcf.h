@@ -95,7 +95,7 @@ typedef struct {
   int64_t waves;   /* contraction waves launched */
   int64_t launches; /* kernels launched by the call */
   double ms_grid, ms_gather, ms_contract, ms_correct, ms_total; /* CUDA-event times */
-  int64_t wave_centres; /* wave size of the call's last catalogue (after any autotuning) */
+  int64_t wave_centres; /* wave size of the call after any autotuning (at most its largest wave) */
 } ext4pcf_stats;
 
 /* Create a context on cfg->device.  Fails with EXT4PCF_E_UNSUPPORTED unless the device is
@@ -140,6 +140,27 @@ EXT4PCF_API int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const
                     const double* weights, int64_t n_gal, const double* radial_bins,
                     int n_bins, int n_max, const int64_t* cat_offsets, int n_cat,
                     const uint8_t* centre_mask, double* upsilon, double* xi_acc,
+                    ext4pcf_stats* stats);
+
+/* Batched form of ext4pcf_measure: many catalogues (mocks, or the overlapping patches of one
+ * survey) in one call, each catalogue's result added into an output slot.
+ *   out_slot    host, int [n_cat] or NULL: catalogue k accumulates into slot out_slot[k]
+ *               (0 <= out_slot[k] < n_out); NULL means slot k (n_out = n_cat, as
+ *               ext4pcf_measure).  Patches of one survey share slot 0: with a centre mask
+ *               marking each patch's core, every galaxy is a centre exactly once and its
+ *               neighbours come from the patch's core and margin.
+ *   upsilon     [n_out][...] and xi_acc [n_out][n_bins][3][2], otherwise as ext4pcf_measure.
+ * The grids of all catalogues are built first, then the centres are processed in waves.  In
+ * the SPLIT_F16 form a wave packs the centres of several catalogues (runs starting at
+ * multiples of 64 records) whenever their numbers are known on the host (no mask, or a host
+ * mask), so that every kernel launch covers many small catalogues; the other forms, and
+ * catalogues with a device-resident mask, take one catalogue per wave.  Every output is
+ * written by one thread block per kernel in a fixed order (no atomics): results are bitwise
+ * reproducible for a given configuration and wave size. */
+EXT4PCF_API int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                    const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
+                    int n_max, const int64_t* cat_offsets, int n_cat, const int* out_slot,
+                    int n_out, const uint8_t* centre_mask, double* upsilon, double* xi_acc,
                     ext4pcf_stats* stats);
 
 /* Multipoles -> real space (paper Eq. Multipole2RealConversion, FP64).  The angular

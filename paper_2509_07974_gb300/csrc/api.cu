@@ -51,16 +51,17 @@ __global__ void mask_flags(const uint8_t* __restrict__ mask, const int* __restri
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) flag[p] = mask ? (mask[perm[p]] != 0) : 1u;
 }
+// centre list: concatenated sorted positions c0 + p of the catalogue's centres
 __global__ void mask_compact(const unsigned* __restrict__ flag_scan, const uint8_t* __restrict__ mask,
-                             const int* __restrict__ perm, int n, int* __restrict__ centres,
+                             const int* __restrict__ perm, int n, int c0, int* __restrict__ centres,
                              int* __restrict__ count) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n && (!mask || mask[perm[p]] != 0)) centres[flag_scan[p]] = p;
+  if (p < n && (!mask || mask[perm[p]] != 0)) centres[flag_scan[p]] = c0 + p;
   if (p == n - 1) *count = (int)flag_scan[p] + ((!mask || mask[perm[p]] != 0) ? 1 : 0);
 }
-__global__ void iota(int* a, int n) {
+__global__ void iota(int* a, int n, int c0) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) a[p] = p;
+  if (p < n) a[p] = c0 + p;
 }
 // status bits: 1 a bounded device-side wait ran out, 2 non-finite positions
 int status_code(int st) {
@@ -237,10 +238,10 @@ int ext4pcf_synchronize(ext4pcf_ctx* ctx) {
   return r != EXT4PCF_OK ? r : rc;
 }
 
-int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* shears,
-                    const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
-                    int n_max, const int64_t* cat_offsets, int n_cat, const uint8_t* centre_mask,
-                    double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
+int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                          const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
+                          int n_max, const int64_t* cat_offsets, int n_cat, const int* out_slot, int n_out,
+                          const uint8_t* centre_mask, double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
   if (!ctx) return EXT4PCF_E_INVALID_ARG;
   ctx->err.clear();
   if (std::getenv("EXT4PCF_FAULT") && std::strcmp(std::getenv("EXT4PCF_FAULT"), "arg") == 0)
@@ -262,6 +263,13 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       if (cat_offsets[k + 1] < cat_offsets[k]) return fail(ctx, EXT4PCF_E_INVALID_ARG, "cat_offsets decrease");
   } else {
     n_cat = 1;
+  }
+  if (out_slot) {
+    if (n_out < 1) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_out < 1");
+    for (int k = 0; k < n_cat; ++k)
+      if (out_slot[k] < 0 || out_slot[k] >= n_out) return fail(ctx, EXT4PCF_E_INVALID_ARG, "out_slot out of range");
+  } else {
+    n_out = n_cat;
   }
   const int prec = ctx->cfg.precision;
   if (prec >= EXT4PCF_TF32 && !tc_supported(Layout::make(n_max, n_bins), prec))
@@ -304,14 +312,14 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     d_mask = (const uint8_t*)ctx->in_mask.p;
   }
   if (host_ups) {
-    ENSURE(ctx->io_ups, ups_bytes * n_cat);
-    CK(cudaMemcpyAsync(ctx->io_ups.p, upsilon, ups_bytes * n_cat, cudaMemcpyHostToDevice, s));
+    ENSURE(ctx->io_ups, ups_bytes * n_out);
+    CK(cudaMemcpyAsync(ctx->io_ups.p, upsilon, ups_bytes * n_out, cudaMemcpyHostToDevice, s));
     d_ups = (double*)ctx->io_ups.p;
   }
   const size_t xi_bytes = (size_t)n_bins * 6 * 8;
   if (host_xi) {
-    ENSURE(ctx->io_xi, xi_bytes * n_cat);
-    CK(cudaMemcpyAsync(ctx->io_xi.p, xi_acc, xi_bytes * n_cat, cudaMemcpyHostToDevice, s));
+    ENSURE(ctx->io_xi, xi_bytes * n_out);
+    CK(cudaMemcpyAsync(ctx->io_xi.p, xi_acc, xi_bytes * n_out, cudaMemcpyHostToDevice, s));
     d_xi = (double*)ctx->io_xi.p;
   }
 
@@ -348,6 +356,9 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   CK(cudaMemsetAsync(ctx->counter.p, 0, 8, s));
   const bool tc = prec == EXT4PCF_TF32 || prec == EXT4PCF_SPLIT_BF16 || prec == EXT4PCF_3XTF32 ||
                   prec == EXT4PCF_SPLIT_F16;
+  // waves that pack the centres of several catalogues: the split-FP16 contraction, the gather
+  // and the correction sums take segments; the other contraction forms one catalogue a wave
+  const bool multi = prec == EXT4PCF_SPLIT_F16;
   if (tc) {
     if (ctx->tc_N != n_max || ctx->tc_nb != n_bins) {
       std::vector<int4> items;
@@ -360,182 +371,271 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
     }
   }
   const long long timeout = ctx->cfg.timeout_cycles > 0 ? ctx->cfg.timeout_cycles : 20000000000LL;
+
+  // ---- per catalogue: first galaxy, galaxy count and (when known on the host) centre count
+  std::vector<int64_t> c0v(n_cat + 1, 0);
+  for (int k = 0; k < n_cat; ++k) c0v[k + 1] = cat_offsets ? cat_offsets[k + 1] : n_gal;
+  std::vector<int64_t> ncent(n_cat, -1);  // -1: counted on the device (a device-resident mask)
+  const bool host_mask = centre_mask && !is_device_ptr(centre_mask);
+  for (int k = 0; k < n_cat; ++k) {
+    const int64_t nk = c0v[k + 1] - c0v[k];
+    if (!centre_mask) {
+      ncent[k] = nk;
+    } else if (host_mask) {
+      int64_t c = 0;
+      for (int64_t i = c0v[k]; i < c0v[k + 1]; ++i) c += centre_mask[i] != 0;
+      ncent[k] = c;
+    }
+  }
+  int64_t nk_max = 0, cells_total = 0;
+  std::vector<int64_t> cell_off(n_cat + 1, 0);
+  for (int k = 0; k < n_cat; ++k) {
+    const int64_t nk = c0v[k + 1] - c0v[k];
+    nk_max = std::max(nk_max, nk);
+    cell_off[k + 1] = cell_off[k] + (nk > 0 ? (int64_t)grid_cells_cap(nk) : 0);
+  }
+  cells_total = cell_off[n_cat];
+
+  // ---- grids of all catalogues (device geometry, no host round trip), into the concatenated
+  // sorted arrays; centre lists hold concatenated positions
   ENSURE(ctx->ncen, (size_t)(n_cat + 1) * sizeof(int));
   ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
-  ENSURE(ctx->geom, sizeof(GridGeom));
-  ENSURE(ctx->cell_start, ((size_t)kMaxCellsPerAxis * kMaxCellsPerAxis + 1) * 4);
+  ENSURE(ctx->geom, (size_t)std::max(n_cat, 1) * sizeof(GridGeom));
+  ENSURE(ctx->cell_start, (size_t)std::max<int64_t>(cells_total, 1) * 4);
   if (centre_mask) CK(cudaMemsetAsync(ctx->ncen.p, 0, (size_t)(n_cat + 1) * sizeof(int), s));
-
-  for (int k = 0; k < n_cat; ++k) {
-    const int64_t c0 = cat_offsets ? cat_offsets[k] : 0;
-    const int nk = (int)((cat_offsets ? cat_offsets[k + 1] : n_gal) - c0);
-    double* ups_k = d_ups + 2 * ups_elems * (size_t)k;
-    double* xi_k = d_xi ? d_xi + (size_t)n_bins * 6 * k : nullptr;
-    if (nk == 0) continue;
-    const double* pos_k = d_pos + 2 * c0;
-    const double* sh_k = d_sh + 2 * c0;
-    const double* w_k = d_w + c0;
-    const uint8_t* mask_k = d_mask ? d_mask + c0 : nullptr;
-    if (timing) t_grid0 = tmark();
-    // ---- grid, chosen on the device from the bounding box (no host round trip)
-    CK(grid_bbox(pos_k, nk, (double*)ctx->bbox.p, s));
-    const int ntiles = (nk + 2047) / 2048;
-    ENSURE(ctx->keys, (size_t)nk * 4); ENSURE(ctx->keys_alt, (size_t)nk * 4);
-    ENSURE(ctx->perm, (size_t)nk * 4); ENSURE(ctx->perm_alt, (size_t)nk * 4);
+  {
+    const int ntiles = (int)((nk_max + 2047) / 2048);
+    ENSURE(ctx->keys, (size_t)nk_max * 4); ENSURE(ctx->keys_alt, (size_t)nk_max * 4);
+    ENSURE(ctx->perm, (size_t)nk_max * 4); ENSURE(ctx->perm_alt, (size_t)nk_max * 4);
     ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
-    ENSURE(ctx->px, (size_t)nk * 8); ENSURE(ctx->py, (size_t)nk * 8);
-    ENSURE(ctx->xr, (size_t)nk * 8); ENSURE(ctx->xi, (size_t)nk * 8); ENSURE(ctx->w, (size_t)nk * 8);
-    if (!f64) { ENSURE(ctx->p4, (size_t)nk * 16); ENSURE(ctx->s4, (size_t)nk * 16); }
+    ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
+    ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
+    if (!f64) { ENSURE(ctx->p4, n * 16); ENSURE(ctx->s4, n * 16); }
+    ENSURE(ctx->centres, n * 4);
+    if (centre_mask) ENSURE(ctx->flags, ((size_t)nk_max + (size_t)nk_max / 1000 + 4096) * 4);
+  }
+  SortedCat cat{};
+  cat.n = (int)n;
+  cat.px = (const double*)ctx->px.p; cat.py = (const double*)ctx->py.p;
+  cat.xr = (const double*)ctx->xr.p; cat.xi = (const double*)ctx->xi.p; cat.w = (const double*)ctx->w.p;
+  cat.p4 = (const float4*)ctx->p4.p; cat.s4 = (const float4*)ctx->s4.p;
+  GridGeom* geoms = (GridGeom*)ctx->geom.p;
+  int* cells = (int*)ctx->cell_start.p;
+  int* clist = (int*)ctx->centres.p;
+  int* ncen_d = (int*)ctx->ncen.p;
+  if (timing) t_grid0 = tmark();
+  for (int k = 0; k < n_cat; ++k) {
+    const int64_t c0 = c0v[k];
+    const int nk = (int)(c0v[k + 1] - c0);
+    if (nk == 0) continue;
+    const uint8_t* mask_k = d_mask ? d_mask + c0 : nullptr;
+    CK(grid_bbox(d_pos + 2 * c0, nk, (double*)ctx->bbox.p, s));
     GridBuffers gb;
     gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
     gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
-    gb.cell_start = (int*)ctx->cell_start.p; gb.cell_cap = ctx->cell_start.bytes / 4;
+    gb.cell_start = cells + cell_off[k]; gb.cell_cap = (size_t)(cell_off[k + 1] - cell_off[k]);
     gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
-    gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
-    gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
-    gb.p4 = (float4*)ctx->p4.p; gb.s4 = (float4*)ctx->s4.p; gb.bbox = (double*)ctx->bbox.p;
-    SortedCat cat;
-    CK(grid_sort_device(pos_k, sh_k, w_k, nk, (const double*)ctx->bbox.p, bins.rmax, (GridGeom*)ctx->geom.p, !f64,
-                        gb, cat, (int*)ctx->status.p, s));
-    // ---- centre list (sorted positions of the centres); with a mask their number stays on
-    // the device (n_live) and the waves cover every galaxy, those past it doing nothing
-    ENSURE(ctx->centres, (size_t)nk * 4);
-    const int* n_live = nullptr;
+    gb.px = (double*)ctx->px.p + c0; gb.py = (double*)ctx->py.p + c0;
+    gb.xr = (double*)ctx->xr.p + c0; gb.xi = (double*)ctx->xi.p + c0; gb.w = (double*)ctx->w.p + c0;
+    gb.p4 = f64 ? nullptr : (float4*)ctx->p4.p + c0; gb.s4 = f64 ? nullptr : (float4*)ctx->s4.p + c0;
+    gb.bbox = (double*)ctx->bbox.p;
+    SortedCat sk;
+    CK(grid_sort_device(d_pos + 2 * c0, d_sh + 2 * c0, d_w + c0, nk, (int)c0, (const double*)ctx->bbox.p,
+                        bins.rmax, geoms + k, !f64, gb, sk, (int*)ctx->status.p, s));
+    // centre list (concatenated sorted positions of the centres); with a mask the count goes
+    // to ncen[k] on the device
     if (mask_k) {
-      ENSURE(ctx->flags, ((size_t)nk + (size_t)nk / 1000 + 4096) * 4);
       unsigned* flag = (unsigned*)ctx->flags.p;
-      mask_flags<<<(nk + 255) / 256, 256, 0, s>>>(mask_k, cat.perm, nk, flag);
+      mask_flags<<<(nk + 255) / 256, 256, 0, s>>>(mask_k, sk.perm, nk, flag);
       g_launches += 2;  // flags + compaction
       unsigned* tmp = (unsigned*)ctx->hist.p;  // reuse as scan scratch
       CK(scan_exclusive(flag, (size_t)nk, tmp, s));
-      mask_compact<<<(nk + 255) / 256, 256, 0, s>>>(flag, mask_k, cat.perm, nk, (int*)ctx->centres.p,
-                                                   (int*)ctx->ncen.p + k);
+      mask_compact<<<(nk + 255) / 256, 256, 0, s>>>(flag, mask_k, sk.perm, nk, (int)c0, clist + c0, ncen_d + k);
       CK(cudaGetLastError());
-      n_live = (const int*)ctx->ncen.p + k;
     } else {
-      iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
+      iota<<<(nk + 255) / 256, 256, 0, s>>>(clist + c0, nk, (int)c0);
       ++g_launches;
       CK(cudaGetLastError());
-      tot_centres += nk;
     }
-    const int n_cen = nk;  // waves cover at most this many centres
-    if (timing) marks.push_back({0, t_grid0, tmark()});
-    int t_w0 = -1, t_w1 = -1, t_w2 = -1;
-    // ---- waves: size from the configuration, else the autotuner's choice for this shape, else
-    // the default; capped so that the per-wave scratch fits ext4pcf_config.workspace_bytes
-    const size_t cbytes = f64 ? sizeof(double2) : sizeof(float2);
-    auto wave_bytes = [&](int t) -> size_t {
-      size_t b = (size_t)t * L.rec * cbytes + (size_t)t * 2 * cbytes;
-      if (tc) b += contract_tc_xb_bytes(L, t, prec);
-      return b;
-    };
-    const auto key = std::make_tuple(prec, n_max, n_bins);
-    const auto tit = ctx->tuned.find(key);
-    int T = ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres
-            : tit != ctx->tuned.end()  ? tit->second
-                                       : (f64 ? 4096 : 8192);
-    const size_t cap = ctx->cfg.workspace_bytes > 0 ? (size_t)ctx->cfg.workspace_bytes : (size_t)-1;
-    while (T > 32 && wave_bytes(T) > cap) T /= 2;
-    if (wave_bytes(T) > cap) return fail(ctx, EXT4PCF_E_OOM, "workspace_bytes too small for a wave of 32 centres");
-    // autotuning (first call of a shape, no centre mask, enough centres): the first waves take
-    // the candidate sizes in turn -- real waves of the result, so no work is repeated -- and
-    // are timed; the fastest per centre is kept for this shape.  These waves synchronise.
-    std::vector<int> trial;
-    if (ctx->cfg.autotune && ctx->cfg.wave_centres <= 0 && tit == ctx->tuned.end() && !mask_k) {
-      const int cand[4] = {2048, 4096, 8192, 16384};
-      int need = 0;
-      for (int c : cand)
-        if (wave_bytes(c) <= cap) {
-          trial.push_back(c);
-          need += c;
-        }
-      if (trial.empty() || need > n_cen) trial.clear();
-    }
-    int Tmax = T;
-    for (int c : trial) Tmax = std::max(Tmax, c);
-    if (Tmax > n_cen) Tmax = n_cen;
-    if (T > n_cen) T = n_cen;
-    if (T < 1) T = 1;
-    if (Tmax < T) Tmax = T;
-    ENSURE(ctx->rec, (size_t)Tmax * L.rec * cbytes);
-    if (tc) {
-      ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, Tmax, prec));
-      if (prec == EXT4PCF_SPLIT_F16) ENSURE(ctx->tc_rowmax, contract_h16_rowmax_bytes(L));
-    }
-    ENSURE(ctx->xw, (size_t)Tmax * 2 * cbytes);
-    std::vector<float> trial_ms;
-    const size_t corr_doubles = corrections_size(L);
-    ENSURE(ctx->corr, corr_doubles * 8);
-    CK(cudaMemsetAsync(ctx->corr.p, 0, corr_doubles * 8, s));
-    if (tc) {
-      const size_t red_bytes = tc_reduced_doubles(L) * 8;
-      ENSURE(ctx->tc_red, red_bytes);
-      CK(cudaMemsetAsync(ctx->tc_red.p, 0, red_bytes, s));
-    }
-    size_t wave_i = 0;
-    for (int w0 = 0; w0 < n_cen;) {
-      const bool tuning = wave_i < trial.size();
-      const int Tw = std::min(tuning ? trial[wave_i] : T, n_cen - w0);
-      const int* cl = (const int*)ctx->centres.p + w0;
-      if (tuning) CK(cudaEventRecord(ctx->ev[1], s));
-      if (timing) t_w0 = tmark();
-      if (f64) {
-        CK(gather_wave<double>(cat, bins, L, cl, Tw, n_live, w0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
-                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
-      } else {
-        CK(gather_wave<float>(cat, bins, L, cl, Tw, n_live, w0, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
-                              (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
-      }
-      if (timing) t_w1 = tmark();
-      if (f64) {
-        CK(contract_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, n_live, w0, ups_k, s));
-      } else if (prec == EXT4PCF_FP32) {
-        CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, n_live, w0, ups_k, s));
-      } else {
-        CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, n_live, w0,
-                            (double*)ctx->tc_red.p, prec, (const int4*)ctx->tc_items.p,
-                            (int)(ctx->tc_items_bytes / sizeof(int4)), (float2*)ctx->tc_xb.p,
-                            (unsigned*)ctx->tc_rowmax.p, (int*)ctx->status.p, timeout, s));
-      }
-      if (timing) t_w2 = tmark();
-      if (f64) {
-        CK(corrections_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, n_live, w0,
-                                    (double*)ctx->corr.p, xi_k, s));
-      } else {
-        CK(corrections_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, n_live, w0,
-                                   (double*)ctx->corr.p, xi_k, s));
-      }
-      if (timing) {
-        const int t_w3 = tmark();
-        marks.push_back({1, t_w0, t_w1});
-        marks.push_back({2, t_w1, t_w2});
-        marks.push_back({3, t_w2, t_w3});
-      }
-      if (tuning) {
-        float ms = 0.f;
-        CK(cudaEventRecord(ctx->ev[2], s));
-        CK(cudaEventSynchronize(ctx->ev[2]));
-        CK(cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]));
-        trial_ms.push_back(ms / (float)Tw);
-        if (trial_ms.size() == trial.size()) {
-          size_t best = 0;
-          for (size_t i = 1; i < trial.size(); ++i)
-            if (trial_ms[i] < trial_ms[best]) best = i;
-          T = trial[best];
-          ctx->tuned[key] = T;
-        }
-      }
-      w0 += Tw;
-      ++wave_i;
-      ++tot_waves;
-    }
-    ctx->last_wave = T;
-    if (tc) CK(tc_expand(L, (const double*)ctx->tc_red.p, ups_k, s));
-    CK(corrections_apply(L, (const double*)ctx->corr.p, ups_k, s));
-
   }
-  if (host_ups) CK(cudaMemcpyAsync(upsilon, d_ups, ups_bytes * n_cat, cudaMemcpyDeviceToHost, s));
-  if (host_xi) CK(cudaMemcpyAsync(xi_acc, d_xi, xi_bytes * n_cat, cudaMemcpyDeviceToHost, s));
+  if (timing) marks.push_back({0, t_grid0, tmark()});
+  for (int k = 0; k < n_cat; ++k)
+    if (ncent[k] >= 0) tot_centres += ncent[k];
+
+  // ---- waves.  Size from the configuration, else the autotuner's choice for this shape, else
+  // the default; capped so that the per-wave scratch fits ext4pcf_config.workspace_bytes
+  const size_t cbytes = f64 ? sizeof(double2) : sizeof(float2);
+  auto wave_bytes = [&](int t) -> size_t {
+    size_t b = (size_t)t * L.rec * cbytes + (size_t)t * 2 * cbytes;
+    if (tc) b += contract_tc_xb_bytes(L, t, prec);
+    return b;
+  };
+  const auto key = std::make_tuple(prec, n_max, n_bins);
+  const auto tit = ctx->tuned.find(key);
+  int T = ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres
+          : tit != ctx->tuned.end()  ? tit->second
+                                     : (f64 ? 4096 : 8192);
+  const size_t cap = ctx->cfg.workspace_bytes > 0 ? (size_t)ctx->cfg.workspace_bytes : (size_t)-1;
+  while (T > 32 && wave_bytes(T) > cap) T /= 2;
+  if (wave_bytes(T) > cap) return fail(ctx, EXT4PCF_E_OOM, "workspace_bytes too small for a wave of 32 centres");
+  // records a wave can need: every centre list padded to a multiple of 64
+  int64_t list_total = 0, known_total = 0;
+  bool all_known = true;
+  for (int k = 0; k < n_cat; ++k) {
+    const int64_t len = ncent[k] >= 0 ? ncent[k] : c0v[k + 1] - c0v[k];
+    list_total += (len + 63) / 64 * 64;
+    if (ncent[k] < 0) all_known = false;
+    else known_total += ncent[k];
+  }
+  // autotuning (first call of a shape, centre counts known on the host, enough centres): the
+  // first waves take the candidate sizes in turn -- real waves of the result, so no work is
+  // repeated -- and are timed; the fastest per centre is kept for this shape.  These waves
+  // synchronise.
+  std::vector<int> trial;
+  if (ctx->cfg.autotune && ctx->cfg.wave_centres <= 0 && tit == ctx->tuned.end() && all_known) {
+    const int cand[4] = {2048, 4096, 8192, 16384};
+    int64_t need = 0;
+    for (int c : cand)
+      if (wave_bytes(c) <= cap) {
+        trial.push_back(c);
+        need += c;
+      }
+    if (trial.empty() || need > known_total) trial.clear();
+  }
+  int Tmax = T;
+  for (int c : trial) Tmax = std::max(Tmax, c);
+  if ((int64_t)Tmax > list_total) Tmax = (int)std::max<int64_t>(list_total, 1);
+  if ((int64_t)T > list_total) T = (int)std::max<int64_t>(list_total, 1);
+  if (Tmax < T) Tmax = T;
+  ENSURE(ctx->rec, (size_t)Tmax * L.rec * cbytes);
+  if (tc) {
+    ENSURE(ctx->tc_xb, contract_tc_xb_bytes(L, Tmax, prec));
+    if (prec == EXT4PCF_SPLIT_F16) ENSURE(ctx->tc_rowmax, contract_h16_rowmax_bytes(L));
+  }
+  ENSURE(ctx->xw, (size_t)Tmax * 2 * cbytes);
+  std::vector<float> trial_ms;
+  const size_t corr_doubles = corrections_size(L);
+  ENSURE(ctx->corr, corr_doubles * 8 * n_out);
+  CK(cudaMemsetAsync(ctx->corr.p, 0, corr_doubles * 8 * n_out, s));
+  const size_t red_doubles = tc ? tc_reduced_doubles(L) : 0;
+  if (tc) {
+    ENSURE(ctx->tc_red, red_doubles * 8 * n_out);
+    CK(cudaMemsetAsync(ctx->tc_red.p, 0, red_doubles * 8 * n_out, s));
+  }
+  // Wave planner: the catalogues' centre lists in order.  With `multi`, a wave packs runs of
+  // several lists whose lengths are known on the host, each starting at a multiple of 64
+  // records; otherwise (or for a list counted on the device) a wave is one run of one list.
+  int pk = 0;
+  int64_t pw0 = 0;
+  auto slot_of = [&](int k) { return out_slot ? out_slot[k] : k; };
+  auto next_plan = [&](int Tg, WavePlan& P) -> bool {
+    P.nseg = 0;
+    P.total = 0;
+    int fill = 0;
+    while (pk < n_cat) {
+      const int64_t cnt = ncent[pk];
+      const int64_t len = cnt >= 0 ? cnt : c0v[pk + 1] - c0v[pk];
+      if (pw0 >= len) {
+        ++pk;
+        pw0 = 0;
+        continue;
+      }
+      const bool single = !multi || cnt < 0;
+      if (single && P.nseg > 0) break;
+      const int space = Tg - fill;
+      if (space <= 0) break;
+      const int take = (int)std::min<int64_t>(len - pw0, space);
+      WaveSeg& g = P.seg[P.nseg++];
+      g.centres = clist + c0v[pk];
+      g.n_live = cnt >= 0 ? nullptr : ncen_d + pk;
+      g.geom = geoms + pk;
+      g.cell_start = cells + cell_off[pk];
+      g.w0 = (int)pw0;
+      g.t = take;
+      g.off = fill;
+      g.slot = slot_of(pk);
+      P.total = fill + take;
+      pw0 += take;
+      fill = (fill + take + 63) / 64 * 64;
+      if (single || fill >= Tg || P.nseg == kMaxSegs) break;
+    }
+    return P.nseg > 0;
+  };
+  int t_w0 = -1, t_w1 = -1, t_w2 = -1;
+  int largest_wave = 0;
+  size_t wave_i = 0;
+  WavePlan P;
+  double* red_base = (double*)ctx->tc_red.p;
+  double* corr_base = (double*)ctx->corr.p;
+  for (;;) {
+    const bool tuning = wave_i < trial.size();
+    if (!next_plan(tuning ? trial[wave_i] : T, P)) break;
+    const WaveSeg& g0 = P.seg[0];  // the one segment of a one-catalogue wave
+    largest_wave = std::max(largest_wave, P.total);
+    if (tuning) CK(cudaEventRecord(ctx->ev[1], s));
+    if (timing) t_w0 = tmark();
+    if (f64) {
+      CK(gather_wave<double>(cat, bins, L, P, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+                             (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+    } else {
+      CK(gather_wave<float>(cat, bins, L, P, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+                            (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+    }
+    if (timing) t_w1 = tmark();
+    if (f64) {
+      CK(contract_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, g0.t, g0.n_live, g0.w0,
+                               d_ups + 2 * ups_elems * (size_t)g0.slot, s));
+    } else if (prec == EXT4PCF_FP32) {
+      CK(contract_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, g0.t, g0.n_live, g0.w0,
+                              d_ups + 2 * ups_elems * (size_t)g0.slot, s));
+    } else if (prec == EXT4PCF_SPLIT_F16) {
+      CK(contract_wave_h16(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, P, red_base,
+                           (const int4*)ctx->tc_items.p, (int)(ctx->tc_items_bytes / sizeof(int4)),
+                           (float2*)ctx->tc_xb.p, (unsigned*)ctx->tc_rowmax.p, (int*)ctx->status.p, timeout, s));
+    } else {
+      CK(contract_wave_tc(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, g0.t, g0.n_live, g0.w0,
+                          red_base + red_doubles * (size_t)g0.slot, prec, (const int4*)ctx->tc_items.p,
+                          (int)(ctx->tc_items_bytes / sizeof(int4)), (float2*)ctx->tc_xb.p,
+                          (unsigned*)ctx->tc_rowmax.p, (int*)ctx->status.p, timeout, s));
+    }
+    if (timing) t_w2 = tmark();
+    if (f64) {
+      CK(corrections_wave<double>(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, P, corr_base, d_xi, s));
+    } else {
+      CK(corrections_wave<float>(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, P, corr_base, d_xi, s));
+    }
+    if (timing) {
+      const int t_w3 = tmark();
+      marks.push_back({1, t_w0, t_w1});
+      marks.push_back({2, t_w1, t_w2});
+      marks.push_back({3, t_w2, t_w3});
+    }
+    if (tuning) {
+      float ms = 0.f;
+      CK(cudaEventRecord(ctx->ev[2], s));
+      CK(cudaEventSynchronize(ctx->ev[2]));
+      CK(cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]));
+      trial_ms.push_back(ms / (float)std::max(1, P.total));
+      if (trial_ms.size() == trial.size()) {
+        size_t best = 0;
+        for (size_t i = 1; i < trial.size(); ++i)
+          if (trial_ms[i] < trial_ms[best]) best = i;
+        T = trial[best];
+        ctx->tuned[key] = T;
+      }
+    }
+    ++wave_i;
+    ++tot_waves;
+  }
+  ctx->last_wave = std::min(T, largest_wave);  // the wave size in use (trial waves aside)
+  // ---- per output slot: every ordered triple from the reduced array, then the corrections
+  for (int o = 0; o < n_out; ++o) {
+    double* ups_o = d_ups + 2 * ups_elems * (size_t)o;
+    if (tc) CK(tc_expand(L, red_base + red_doubles * (size_t)o, ups_o, s));
+    CK(corrections_apply(L, corr_base + corr_doubles * (size_t)o, ups_o, s));
+  }
+  if (host_ups) CK(cudaMemcpyAsync(upsilon, d_ups, ups_bytes * n_out, cudaMemcpyDeviceToHost, s));
+  if (host_xi) CK(cudaMemcpyAsync(xi_acc, d_xi, xi_bytes * n_out, cudaMemcpyDeviceToHost, s));
   // a call that synchronises anyway (host outputs or statistics) reports the status word;
   // a device-only call returns after enqueueing and leaves it to ext4pcf_synchronize
   if (host_ups || host_xi || timing) {
@@ -558,11 +658,12 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
       else if (m.kind == 2) ms_contract += t;
       else ms_correct += t;
     }
-    if (centre_mask) {
+    if (centre_mask && !host_mask) {  // counts that only the device knows
       std::vector<int> nc(n_cat);
       CK(cudaMemcpyAsync(nc.data(), ctx->ncen.p, (size_t)n_cat * sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      for (int k = 0; k < n_cat; ++k) tot_centres += nc[k];
+      for (int k = 0; k < n_cat; ++k)
+        if (ncent[k] < 0) tot_centres += nc[k];
     }
     stats->pairs = (int64_t)pairs;
     stats->centres = tot_centres;
@@ -577,6 +678,14 @@ int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* she
   }
   CK(cudaGetLastError());
   return EXT4PCF_OK;
+}
+
+int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                    const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
+                    int n_max, const int64_t* cat_offsets, int n_cat, const uint8_t* centre_mask,
+                    double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
+  return ext4pcf_measure_batch(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, cat_offsets,
+                               n_cat, nullptr, 0, centre_mask, upsilon, xi_acc, stats);
 }
 
 int ext4pcf_to_real_space(ext4pcf_ctx* ctx, const double* upsilon, int n_bins, int n_max, int n_phi,
@@ -698,7 +807,7 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   const int ntiles = (nk + 2047) / 2048;
   ENSURE(ctx->keys, n * 4); ENSURE(ctx->keys_alt, n * 4);
   ENSURE(ctx->perm, n * 4); ENSURE(ctx->perm_alt, n * 4);
-  ENSURE(ctx->cell_start, ((size_t)kMaxCellsPerAxis * kMaxCellsPerAxis + 1) * 4);
+  ENSURE(ctx->cell_start, grid_cells_cap(nk) * 4);
   ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
   ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
   ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
@@ -711,11 +820,11 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
   gb.p4 = nullptr; gb.s4 = nullptr; gb.bbox = (double*)ctx->bbox.p;
   SortedCat cat;
-  CK(grid_sort_device(positions, shears, weights, nk, (const double*)ctx->bbox.p, bins.rmax, (GridGeom*)ctx->geom.p,
-                      false, gb, cat, (int*)ctx->status.p, s));
+  CK(grid_sort_device(positions, shears, weights, nk, 0, (const double*)ctx->bbox.p, bins.rmax,
+                      (GridGeom*)ctx->geom.p, false, gb, cat, (int*)ctx->status.p, s));
   // ---- every galaxy a centre; waves of FP64 records, contracted with the order-3 tables
   ENSURE(ctx->centres, n * 4);
-  iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk);
+  iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk, 0);
   ++g_launches;
   CK(cudaGetLastError());
   const int T = std::min(ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres : 4096, nk);
@@ -723,8 +832,12 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   ENSURE(ctx->xw, (size_t)T * 2 * sizeof(double2));
   for (int w0 = 0; w0 < nk; w0 += T) {
     const int Tw = std::min(T, nk - w0);
-    const int* cl = (const int*)ctx->centres.p + w0;
-    CK(gather_wave<double>(cat, bins, L, cl, Tw, nullptr, w0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+    WavePlan P;
+    P.nseg = 1;
+    P.total = Tw;
+    P.seg[0] = WaveSeg{(const int*)ctx->centres.p, nullptr, (const GridGeom*)ctx->geom.p, (const int*)ctx->cell_start.p,
+                       w0, Tw, 0, 0};
+    CK(gather_wave<double>(cat, bins, L, P, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                            (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
     CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3, s));
   }

@@ -114,6 +114,37 @@ __device__ __forceinline__ int wave_centres(int T, const int* n_live, int w0) {
   return left < T ? (left > 0 ? left : 0) : T;
 }
 
+// A wave of the measure path: runs ("segments") of the centre lists of one or more catalogues,
+// each at an offset of the wave's records that is a multiple of 64.  Centre lists and cell
+// lists hold positions in the concatenated sorted arrays of all catalogues.
+constexpr int kMaxSegs = 64;
+struct WaveSeg {
+  const int* centres;     // the catalogue's centre list
+  const int* n_live;      // its length on the device (nullptr: t is exact)
+  const GridGeom* geom;   // the catalogue's grid
+  const int* cell_start;  // its cell list
+  int w0;                 // first list index of the segment
+  int t;                  // centres of the segment at most
+  int off;                // first record of the segment in the wave
+  int slot;               // output slot the segment accumulates into
+};
+struct WavePlan {
+  int nseg;
+  int total;  // records of the wave: the last segment's off + t
+  WaveSeg seg[kMaxSegs];
+};
+// live centres of a segment (device)
+__device__ __forceinline__ int seg_live(const WaveSeg& g) { return wave_centres(g.t, g.n_live, g.w0); }
+// segment holding record c, or -1 (records between segments are padding); *j = index in it
+__device__ __forceinline__ int seg_of(const WavePlan& p, int c, int* j) {
+  for (int s = p.nseg - 1; s >= 0; --s)
+    if (c >= p.seg[s].off) {
+      *j = c - p.seg[s].off;
+      return *j < p.seg[s].t ? s : -1;
+    }
+  return -1;
+}
+
 struct Bins {
   int nb;
   double e2[65];   // squared edges (double)
@@ -140,26 +171,33 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
                       double x0, double y0, double cell, int ncx, int ncy, bool want_f32,
                       GridBuffers& gb, SortedCat& out, cudaStream_t s);
 // the measure path: the grid chosen on the device from the bounding box d_bbox (written by
-// grid_bbox) for separations up to rmax, then the sort; cell_start must hold
-// kMaxCellsPerAxis^2 + 1 entries; positions that are not finite set bit 1 of *status
-cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n,
+// grid_bbox) for separations up to rmax, then the sort.  The sorted arrays of gb point at this
+// catalogue's place in the concatenated arrays, whose first galaxy is c0; the cell list holds
+// concatenated positions and needs grid_cells_cap(n) entries; positions that are not finite
+// set bit 1 of *status
+cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n, int c0,
                              const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
                              GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s);
+// entries of a cell list of the measure path for n galaxies (the device grid keeps at most
+// ~4n cells)
+inline size_t grid_cells_cap(int64_t n) { return (size_t)(4 * n + 2); }
 
-// gather.cu: per-centre multipole records for centres[c0 .. c0+T) (sorted positions).
-// n_live, w0: see wave_centres
+// gather.cu: per-centre multipole records of a wave (records of padding centres are left
+// untouched); cat holds the concatenated sorted arrays (its grid fields unused)
 template <typename R>
-cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
-                        const int* centres, int T, const int* n_live, int w0, cplx_t<R>* rec, cplx_t<R>* xw,
-                        unsigned long long* pair_count, int sm_count, cudaStream_t s);
+cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L, const WavePlan& plan,
+                        cplx_t<R>* rec, cplx_t<R>* xw, unsigned long long* pair_count, int sm_count,
+                        cudaStream_t s);
 
 // contract.cu
 template <typename R>
 cudaError_t contract_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
                           const int* n_live, int w0, double* ups, cudaStream_t s);
+// correction sums of every segment into its slot: corr + slot * corrections_size(L), and
+// (xi_acc non-null) xi_acc + slot * 6 nb
 template <typename R>
-cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                             const int* n_live, int w0, double* corr, double* xi_acc, cudaStream_t s);
+cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, const WavePlan& plan,
+                             double* corr, double* xi_acc, cudaStream_t s);
 cudaError_t corrections_apply(const Layout& L, const double* corr, double* ups, cudaStream_t s);
 size_t corrections_size(const Layout& L);  // doubles
 
@@ -177,12 +215,13 @@ size_t tc_reduced_doubles(const Layout& L);
 bool tc_build_items(const Layout& L, std::vector<int4>& items);
 cudaError_t tc_expand(const Layout& L, const double* red, double* ups, cudaStream_t s);
 
-// contract_h16.cu: the split-FP16 form (called through contract_wave_tc)
+// contract_h16.cu: the split-FP16 form
 bool h16_supported(const Layout& L);
 size_t contract_h16_wave_bytes(const Layout& L, int T);
 size_t contract_h16_rowmax_bytes(const Layout& L);
-cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* xw, int T, const int* n_live,
-                              int w0, double* red, const int4* items, int n_items, float2* wave, unsigned* rowmax,
+// (plan: every segment's sums go to red + slot * tc_reduced_doubles(L))
+cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* xw, const WavePlan& plan,
+                              double* red, const int4* items, int n_items, float2* wave, unsigned* rowmax,
                               int* status, long long timeout, cudaStream_t s);
 
 }  // namespace ext4pcf

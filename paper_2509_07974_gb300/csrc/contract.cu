@@ -177,13 +177,11 @@ contract_cuda_core(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx
 // Correction sums over the wave: block (mu, kind, index); thread (2x2 tile of (ba, bb), slice
 // of the centres), or, for the triple term, threads over the centres.
 template <typename R>
-__global__ void __launch_bounds__(256, 8) corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
-                                   const cplx_t<R>* __restrict__ xw, int T, const int* __restrict__ n_live,
-                                   int w0, double* __restrict__ corr) {
+__device__ __forceinline__ void corrections_block(const Layout& L, const cplx_t<R>* __restrict__ rec,
+                                                  const cplx_t<R>* __restrict__ xw, int T,
+                                                  double* __restrict__ corr, unsigned char* smem_raw) {
   using Cx = cplx_t<R>;
-  T = wave_centres(T, n_live, w0);
   if (T == 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = L.N, nb = L.nb, nn = 2 * N + 1, ns = 4 * N + 1;
   const int per_mu = 2 * nn + ns;  // index rows of the three double-counting kinds
   const int mu = blockIdx.x / (per_mu + 1);
@@ -309,11 +307,9 @@ __global__ void __launch_bounds__(256, 8) corrections_kernel(const Layout L, con
 
 // xi accumulators per bin: (sum conj(x) G_0, sum x G_-4, sum w W_0), FP64, fixed order.
 template <typename R>
-__global__ void xi_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
-                          const cplx_t<R>* __restrict__ xw, int T, const int* __restrict__ n_live, int w0,
-                          double* __restrict__ xi) {
-  __shared__ double red[6][256];
-  T = wave_centres(T, n_live, w0);
+__device__ __forceinline__ void xi_block(const Layout& L, const cplx_t<R>* __restrict__ rec,
+                                         const cplx_t<R>* __restrict__ xw, int T, double* __restrict__ xi,
+                                         double (*red)[256]) {
   if (T == 0) return;
   const int b = blockIdx.x, tid = threadIdx.x;
   double v[6] = {0, 0, 0, 0, 0, 0};
@@ -335,6 +331,35 @@ __global__ void xi_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
     __syncthreads();
   }
   if (tid < 6) xi[6 * b + tid] += red[tid][0];
+  __syncthreads();
+}
+
+// Correction sums over a wave: block (mu, kind, index); each block takes the wave's segments
+// in order and adds each one's sums into its slot (one writer per output: no atomics, fixed
+// order)
+template <typename R>
+__global__ void __launch_bounds__(256, 8) corrections_kernel(const Layout L, const cplx_t<R>* __restrict__ rec,
+                                                            const cplx_t<R>* __restrict__ xw, const WavePlan plan,
+                                                            double* __restrict__ corr, size_t corr_stride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int si = 0; si < plan.nseg; ++si) {
+    const WaveSeg& g = plan.seg[si];
+    corrections_block<R>(L, rec + (size_t)g.off * L.rec, xw + 2 * (size_t)g.off, seg_live(g),
+                         corr + (size_t)g.slot * corr_stride, smem_raw);
+    __syncthreads();
+  }
+}
+
+// xi accumulators of a wave: block = radial bin, segments in order into their slots
+template <typename R>
+__global__ void xi_kernel(const Layout L, const cplx_t<R>* __restrict__ rec, const cplx_t<R>* __restrict__ xw,
+                          const WavePlan plan, double* __restrict__ xi) {
+  __shared__ double red[6][256];
+  for (int si = 0; si < plan.nseg; ++si) {
+    const WaveSeg& g = plan.seg[si];
+    xi_block<R>(L, rec + (size_t)g.off * L.rec, xw + 2 * (size_t)g.off, seg_live(g),
+                xi + (size_t)g.slot * 6 * L.nb, red);
+  }
 }
 
 __global__ void apply_corrections(const Layout L, const double* __restrict__ corr, double* __restrict__ ups) {
@@ -393,9 +418,9 @@ size_t corrections_size(const Layout& L) {
 }
 
 template <typename R>
-cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, int T,
-                             const int* n_live, int w0, double* corr, double* xi_acc, cudaStream_t s) {
-  if (T <= 0) return cudaSuccess;
+cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t<R>* xw, const WavePlan& plan,
+                             double* corr, double* xi_acc, cudaStream_t s) {
+  if (plan.total <= 0 || plan.nseg <= 0) return cudaSuccess;
   const int nn = 2 * L.N + 1, ns = 4 * L.N + 1;
   const int blocks = 9 * (2 * nn + ns + 1);
   // 192 threads (10 resident blocks per SM) let the 9 x (2(2N+1) + 4N+2) blocks of a wave
@@ -408,10 +433,10 @@ cudaError_t corrections_wave(const Layout& L, const cplx_t<R>* rec, const cplx_t
                                (size_t)2 * threads * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(corrections_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, T, n_live, w0, corr);
+  corrections_kernel<R><<<blocks, threads, smem, s>>>(L, rec, xw, plan, corr, corrections_size(L));
   ++g_launches;
   if (xi_acc) {
-    xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, T, n_live, w0, xi_acc);
+    xi_kernel<R><<<L.nb, 256, 0, s>>>(L, rec, xw, plan, xi_acc);
     ++g_launches;
   }
   return cudaGetLastError();
@@ -431,9 +456,9 @@ template cudaError_t contract_wave<float>(const Layout&, const float2*, const fl
                                           cudaStream_t);
 template cudaError_t contract_wave<double>(const Layout&, const double2*, const double2*, int, const int*, int, double*,
                                            cudaStream_t);
-template cudaError_t corrections_wave<float>(const Layout&, const float2*, const float2*, int, const int*, int, double*,
+template cudaError_t corrections_wave<float>(const Layout&, const float2*, const float2*, const WavePlan&, double*,
                                              double*, cudaStream_t);
-template cudaError_t corrections_wave<double>(const Layout&, const double2*, const double2*, int, const int*, int,
+template cudaError_t corrections_wave<double>(const Layout&, const double2*, const double2*, const WavePlan&,
                                               double*, double*, cudaStream_t);
 
 // kComp in the layout of ext4pcf_nth_order_factors at order 4: sign, centre code, then per

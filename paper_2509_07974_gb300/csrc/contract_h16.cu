@@ -103,20 +103,22 @@ __device__ __forceinline__ float2 hwave_value(const Layout& L, const float2* __r
 }
 
 // largest |component| of every row over the wave's centres: 32 rows x 128 centres per block
+// (records of the wave's live centres only: padding records are never read)
 __global__ void __launch_bounds__(256) hwave_rowmax_kernel(const Layout L, const float2* __restrict__ rec,
-                                                           const float2* __restrict__ xw, int T,
-                                                           const int* __restrict__ n_live, int w0, int row_g,
-                                                           int row_w, int rows, unsigned* __restrict__ rowmax) {
+                                                           const float2* __restrict__ xw, const WavePlan plan,
+                                                           int row_g, int row_w, int rows,
+                                                           unsigned* __restrict__ rowmax) {
   __shared__ float part[8][33];
   const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 128;
-  T = wave_centres(T, n_live, w0);
-  if (c0 >= T) return;
+  if (c0 >= plan.total) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, r = r0 + tx;
   float m = 0.f;
   if (r < rows) {
     for (int k = 0; k < 16; ++k) {
       const int c = c0 + ty + 8 * k;
-      if (c < T) {
+      int j = 0;
+      const int si = c < plan.total ? seg_of(plan, c, &j) : -1;
+      if (si >= 0 && j < seg_live(plan.seg[si])) {
         const float2 v = hwave_value(L, rec + (size_t)c * L.rec, xw[2 * (size_t)c], xw[2 * (size_t)c + 1].x, r,
                                      row_g, row_w);
         m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
@@ -131,27 +133,29 @@ __global__ void __launch_bounds__(256) hwave_rowmax_kernel(const Layout L, const
   }
 }
 
-// The transposed, scaled, planar wave array, stage-major: centre c of row r sits in stage
+// The transposed, scaled, planar wave array, stage-major: record c of row r sits in stage
 // c / 64 at float (c / 64 * rows + r) * 128 + q * 32 + ((k ^ (r % 8)) * 4) + c % 4, with
 // q = (c % 64) / 16 the quarter and k = (c % 16) / 4 (real part) or 4 + (c % 16) / 4
-// (imaginary part) the logical 16-byte chunk.  Centres from the wave's count to the next
-// multiple of 64 are written as zeros (the last stage reads them).
+// (imaginary part) the logical 16-byte chunk.
+// Padding records (between segments, past a segment's live centres, past the wave up to a
+// multiple of 64) are written as zeros.
 __global__ void __launch_bounds__(256) hwave_transpose_kernel(const Layout L, const float2* __restrict__ rec,
-                                                              const float2* __restrict__ xw, int T,
-                                                              const int* __restrict__ n_live, int w0, int row_g,
-                                                              int row_w, int rows, const unsigned* __restrict__ rowmax,
+                                                              const float2* __restrict__ xw, const WavePlan plan,
+                                                              int row_g, int row_w, int rows,
+                                                              const unsigned* __restrict__ rowmax,
                                                               float* __restrict__ out) {
   __shared__ float2 tile[32][33];
   const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-  T = wave_centres(T, n_live, w0);
-  const int Tp = (T + kHCentres - 1) / kHCentres * kHCentres;
+  const int Tp = (plan.total + kHCentres - 1) / kHCentres * kHCentres;
   if (c0 >= Tp) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int c = c0 + ty + 8 * k, r = r0 + tx;
     float2 v = make_float2(0.f, 0.f);
-    if (c < T && r < rows)
+    int j = 0;
+    const int si = c < plan.total ? seg_of(plan, c, &j) : -1;
+    if (si >= 0 && j < seg_live(plan.seg[si]) && r < rows)
       v = hwave_value(L, rec + (size_t)c * L.rec, xw[2 * (size_t)c], xw[2 * (size_t)c + 1].x, r, row_g, row_w);
     tile[ty + 8 * k][tx] = v;
   }
@@ -172,10 +176,9 @@ __global__ void __launch_bounds__(256) hwave_transpose_kernel(const Layout L, co
 
 struct HArgs {
   Layout L;
-  int T;              // centres of the wave at most
-  const int* n_live;  // with w0: the wave's centres on the device (wave_centres)
-  int w0;
-  double* red;        // reduced output [9][2N+3][2N+3][nb][npairs] (complex, FP64)
+  WavePlan plan;      // the wave's segments (a segment starts at a stage boundary)
+  double* red;        // reduced outputs [slot][9][2N+3][2N+3][nb][npairs] (complex, FP64)
+  size_t red_stride;  // doubles per slot
   int npairs;
   const int4* items;  // (type, s, row0, nrows | (n2 of row 0 of the s block + 64) << 8)
   int n_items;
@@ -319,7 +322,7 @@ __device__ __forceinline__ void kr_group(uint32_t PB, uint32_t PC, int h, uint32
 //   A and B       ab_full [16 producer warps] / ab_empty [1, tcgen05.commit]
 //   partial sums  dfull [1, tcgen05.commit] / dempty [16 producer warps]
 __global__ void __launch_bounds__(kHThreads, 1)
-contract_h16_kernel(const HArgs args) {
+contract_h16_kernel(const __grid_constant__ HArgs args) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023);
   const Layout L = args.L;
@@ -369,7 +372,6 @@ contract_h16_kernel(const HArgs args) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const long long budget = args.timeout;
-  const int nstage = (wave_centres(args.T, args.n_live, args.w0) + kHCentres - 1) / kHCentres;
   int err = 0;
   // bounded wait on an mbarrier phase; the first wait of the CTA that runs out of its budget
   // raises the abort flag, after which every wait gives up at once
@@ -456,8 +458,6 @@ contract_h16_kernel(const HArgs args) {
         }
       }
       float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
-#pragma unroll
-      for (int j = 0; j < 16; ++j) accD[j] = 0.f;
       const bool has_cols = qq * 16 < npad;
       // Software pipeline over the stages (k = this stage):
       //  * the partial sum of stage k - 2 is read out of TMEM (tcgen05.ld issued mid-stage,
@@ -489,6 +489,12 @@ contract_h16_kernel(const HArgs args) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&ab_full[slot]);
       };
+      // the wave's segments in order; each one's sums go to its slot
+      for (int si = 0; si < args.plan.nseg; ++si) {
+      const WaveSeg& sgm = args.plan.seg[si];
+      const int nstage = (seg_live(sgm) + kHCentres - 1) / kHCentres;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) accD[j] = 0.f;
       int prev_slot = 0;
       for (int k = 0; k < nstage; ++k) {
         wait(&in_full[islot], iph);
@@ -552,7 +558,7 @@ contract_h16_kernel(const HArgs args) {
       }
       gs += nstage;
       // ---------------------------------------------------------------- epilogue
-      if (row_ok && has_cols && nstage > 0) {  // (a wave past the end adds nothing)
+      if (row_ok && has_cols && nstage > 0) {  // (an empty segment adds nothing)
         const int pr = rr % npairs, nx = 2 * N + 3;
         const int kx = h_scale_exp(args.rowmax[g.bx.row0 + (eB - g.sx)]);
         const int kc = h_scale_exp(args.rowmax[g.bc.row0 + (eC - g.sc)]);
@@ -566,12 +572,13 @@ contract_h16_kernel(const HArgs args) {
                                 : g.ba0.row0 + hblk_index(g.ba0, kr.A[0], g.s, b1, nb);
             const double unscale = h_pow2d(-(kx + kc + h_scale_exp(args.rowmax[arow])));
             const size_t o = ((((size_t)mu * nx + (n2 + N + 1)) * nx + (n3 + N + 1)) * nb + b1) * npairs + pr;
-            double* p = args.red + 2 * o;
+            double* p = args.red + (size_t)sgm.slot * args.red_stride + 2 * o;
             p[0] += (double)accD[j] * unscale;
             p[1] += (double)accD[j + 1] * unscale;
           }
         }
       }
+      }  // segments
     }
   } else if (warp == kHWarpMma) {
     // ---------------------------------------------------------------------- MMA issuer
@@ -584,6 +591,8 @@ contract_h16_kernel(const HArgs args) {
         const KRType kr = kKR[args.items[it].x];
         const int npad = (2 * kr.nmu * nb + 15) / 16 * 16;
         const uint32_t id = idesc(0u, npad);  // fp16 A and B, FP32 D
+        for (int si = 0; si < args.plan.nseg; ++si) {
+        const int nstage = (seg_live(args.plan.seg[si]) + kHCentres - 1) / kHCentres;
         for (int k = 0; k < nstage; ++k, ++gs) {
           const int buf = (int)(gs & 1);
           if (gs >= 2) wait(&dempty[buf], (uint32_t)(((gs >> 1) - 1) & 1));
@@ -606,6 +615,7 @@ contract_h16_kernel(const HArgs args) {
           mma_commit(&dfull[buf]);
           if (++aslot == kHSlots) { aslot = 0; aph ^= 1u; }
         }
+        }  // segments
       }
       // every MMA of this CTA has completed before the TMEM is released (also when a wait
       // above gave up); an MMA always finishes, so this bound is generous
@@ -635,13 +645,16 @@ contract_h16_kernel(const HArgs args) {
           err = 1;
         }
         const uint32_t bytes = (uint32_t)(g.sa1 + g.ba1.len) * 512u;
+        for (int si = 0; si < args.plan.nseg; ++si) {
+        const WaveSeg& sgm = args.plan.seg[si];
+        const int nstage = (seg_live(sgm) + kHCentres - 1) / kHCentres, kst0 = sgm.off / kHCentres;
         for (int k = 0; k < nstage; ++k) {
           wait(&in_empty[islot], iph ^ 1u);
           if (!*abort_flag) {  // nothing more is copied once the CTA gives up
             last[islot] = (int)iph;
             mbar_expect_tx(&in_full[islot], bytes);
             unsigned char* st = in_base + (size_t)islot * in_bytes;
-            const float* src = args.wave + (size_t)k * args.rows * 128;
+            const float* src = args.wave + (size_t)(kst0 + k) * args.rows * 128;
 #pragma unroll
             for (int b = 0; b < 4; ++b)
               if (blk[b].len > 0)
@@ -650,6 +663,7 @@ contract_h16_kernel(const HArgs args) {
           }
           if (++islot == S_in) { islot = 0; iph ^= 1u; }
         }
+        }  // segments
       }
       // every copy has landed before the shared memory is given up: the phases of a slot
       // complete in order, so its last issued phase covers the earlier ones
@@ -699,23 +713,25 @@ size_t contract_h16_wave_bytes(const Layout& L, int T) {
 }
 size_t contract_h16_rowmax_bytes(const Layout& L) { return (size_t)h16_wave_rows(L) * sizeof(unsigned); }
 
-cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* xw, int T, const int* n_live,
-                              int w0, double* red, const int4* items, int n_items, float2* wave, unsigned* rowmax,
+cudaError_t contract_wave_h16(const Layout& L, const float2* rec, const float2* xw, const WavePlan& plan,
+                              double* red, const int4* items, int n_items, float2* wave, unsigned* rowmax,
                               int* status, long long timeout, cudaStream_t s) {
-  if (T <= 0) return cudaSuccess;
-  const int rows = h16_wave_rows(L), pitch = h16_wave_pitch(T);
+  if (plan.total <= 0 || plan.nseg <= 0) return cudaSuccess;
+  for (int i = 0; i < plan.nseg; ++i)  // segments start at stage boundaries
+    if (plan.seg[i].off % kHCentres != 0) return cudaErrorInvalidValue;
+  const int rows = h16_wave_rows(L), pitch = h16_wave_pitch(plan.total);
   const int row_g = kXBTypes * (2 * L.N + 3) * L.nb, row_w = row_g + L.nG * L.nb;
   cudaError_t e = cudaMemsetAsync(rowmax, 0, (size_t)rows * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  hwave_rowmax_kernel<<<dim3((rows + 31) / 32, (T + 127) / 128), 256, 0, s>>>(L, rec, xw, T, n_live, w0, row_g,
-                                                                            row_w, rows, rowmax);
+  hwave_rowmax_kernel<<<dim3((rows + 31) / 32, (plan.total + 127) / 128), 256, 0, s>>>(L, rec, xw, plan, row_g,
+                                                                                     row_w, rows, rowmax);
   hwave_transpose_kernel<<<dim3((rows + 31) / 32, pitch / 32), 256, 0, s>>>(
-      L, rec, xw, T, n_live, w0, row_g, row_w, rows, rowmax, reinterpret_cast<float*>(wave));
+      L, rec, xw, plan, row_g, row_w, rows, rowmax, reinterpret_cast<float*>(wave));
   g_launches += 2;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   HArgs a;
-  a.L = L; a.T = T; a.n_live = n_live; a.w0 = w0; a.red = red;
+  a.L = L; a.plan = plan; a.red = red; a.red_stride = tc_reduced_doubles(L);
   a.npairs = L.nb * (L.nb + 1) / 2;
   a.items = items; a.n_items = n_items;
   a.row_g = row_g; a.row_w = row_w;

@@ -796,8 +796,6 @@ cudaError_t encode_wave_tmap(CUtensorMap* tm, const void* base, uint64_t x, uint
 cudaError_t contract_wave_tc(const Layout& L, const float2* rec, const float2* xw, int T, const int* n_live,
                              int w0, double* red, int precision, const int4* items, int n_items, float2* wave,
                              unsigned* rowmax, int* status, long long timeout, cudaStream_t s) {
-  if (precision == EXT4PCF_SPLIT_F16)
-    return contract_wave_h16(L, rec, xw, T, n_live, w0, red, items, n_items, wave, rowmax, status, timeout, s);
   if (T <= 0) return cudaSuccess;
   const int rows = tc_wave_rows(L), pitch = tc_wave_pitch(T);
   const int row_g = kXBTypes * (2 * L.N + 3) * L.nb, row_w = row_g + L.nG * L.nb;

@@ -291,27 +291,33 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   R* trs = reinterpret_cast<R*>(misc + 8);
   signed char* cbin = reinterpret_cast<signed char*>(trs + (kTrSplit ? nb * args.nblk * 10 : 0));  // bin of each candidate
 
-  // the cell grid (computed on the device for the measure path) and the wave's centres
-  double gx0 = cat.x0, gy0 = cat.y0, cell = cat.cell;
-  int gncx = cat.ncx, gncy = cat.ncy;
-  if (cat.geom) {
-    gx0 = cat.geom->x0; gy0 = cat.geom->y0; cell = cat.geom->cell;
-    gncx = cat.geom->ncx; gncy = cat.geom->ncy;
-  }
-  const int T = args.n_live ? min(args.T, *args.n_live - args.w0) : args.T;
   for (int b = tid; b <= nb; b += kThreads) {
     e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b];
-    // rounding window of the float bin decision: |dx| carries ~2 ulp of max(cell, r)
-    const double e = sqrt(args.bins.e2[b]);
-    const double err = 4.0 * 1.2e-7 * (cell + e);
-    win[b] = (float)(2.0 * e * err + err * err);
   }
   for (int k = tid; k < kWarps * 64; k += kThreads) wcnt[k] = 0;
-  __syncthreads();
   const double rmax = args.bins.rmax * (1.0 + 1e-9) + 1e-12;
+  double cell_w = -1.0;  // cell side the rounding windows were computed for
 
-  for (int c = blockIdx.x; c < T; c += gridDim.x) {
-    const int pi = args.centres[c];
+  for (int c = blockIdx.x; c < args.plan.total; c += gridDim.x) {
+    // the record's segment: its catalogue's grid and centre (padding records are skipped)
+    int j = 0;
+    const int si = seg_of(args.plan, c, &j);
+    if (si < 0 || j >= seg_live(args.plan.seg[si])) continue;  // uniform over the block
+    const WaveSeg& sg = args.plan.seg[si];
+    const GridGeom gm = *sg.geom;
+    const double gx0 = gm.x0, gy0 = gm.y0, cell = gm.cell;
+    const int gncx = gm.ncx, gncy = gm.ncy;
+    if (cell != cell_w) {
+      __syncthreads();
+      for (int b = tid; b <= nb; b += kThreads) {
+        // rounding window of the float bin decision: |dx| carries ~2 ulp of max(cell, r)
+        const double e = sqrt(args.bins.e2[b]);
+        const double err = 4.0 * 1.2e-7 * (cell + e);
+        win[b] = (float)(2.0 * e * err + err * err);
+      }
+      cell_w = cell;
+    }
+    const int pi = sg.centres[sg.w0 + j];
     const double pxi = cat.px[pi], pyi = cat.py[pi];
     float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (sizeof(R) == 4) Pi = cat.p4[pi];
@@ -328,8 +334,8 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
         int cx0 = (int)floor((xc - hw) / cell), cx1 = (int)floor((xc + hw) / cell);
         cx0 = max(cx0, 0); cx1 = min(cx1, gncx - 1);
         if (cx0 > cx1) continue;
-        const int a = cat.cell_start[cy * gncx + cx0];
-        const int b = cat.cell_start[cy * gncx + cx1 + 1];
+        const int a = sg.cell_start[cy * gncx + cx0];
+        const int b = sg.cell_start[cy * gncx + cx1 + 1];
         if (b <= a) continue;
         rstart[nr] = a; rpre[nr] = tot; tot += b - a; ++nr;
       }
@@ -530,15 +536,14 @@ template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 }  // namespace
 
 template <typename R>
-cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
-                        const int* centres, int T, const int* n_live, int w0, cplx_t<R>* rec, cplx_t<R>* xw,
-                        unsigned long long* pair_count, int sm_count, cudaStream_t s) {
-  if (T <= 0) return cudaSuccess;
+cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L, const WavePlan& plan,
+                        cplx_t<R>* rec, cplx_t<R>* xw, unsigned long long* pair_count, int sm_count,
+                        cudaStream_t s) {
+  if (plan.total <= 0) return cudaSuccess;
   constexpr int MB = kMB<R>;
   constexpr int MINB = kMinBlocks<R>;
   GatherArgs a;
-  a.cat = cat; a.bins = bins; a.L = L; a.centres = centres; a.T = T; a.pair_count = pair_count;
-  a.n_live = n_live; a.w0 = w0;
+  a.cat = cat; a.bins = bins; a.L = L; a.plan = plan; a.pair_count = pair_count;
   const int npow = L.max_pow + 1;
   int nblk = (npow + MB - 1) / MB;
   nblk = (nblk + kWarps - 1) / kWarps * kWarps;
@@ -558,18 +563,16 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   cudaError_t e = cudaFuncSetAttribute(gather_kernel<R, MB, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int grid = T;
+  int grid = plan.total;
   gather_kernel<R, MB, MINB><<<grid, kThreads, smem, s>>>(a, rec, xw);
   ++g_launches;
   (void)sm_count;
   return cudaGetLastError();
 }
 
-template cudaError_t gather_wave<float>(const SortedCat&, const Bins&, const Layout&, const int*,
-                                        int, const int*, int, float2*, float2*, unsigned long long*, int,
-                                        cudaStream_t);
-template cudaError_t gather_wave<double>(const SortedCat&, const Bins&, const Layout&, const int*,
-                                         int, const int*, int, double2*, double2*, unsigned long long*, int,
-                                         cudaStream_t);
+template cudaError_t gather_wave<float>(const SortedCat&, const Bins&, const Layout&, const WavePlan&,
+                                        float2*, float2*, unsigned long long*, int, cudaStream_t);
+template cudaError_t gather_wave<double>(const SortedCat&, const Bins&, const Layout&, const WavePlan&,
+                                         double2*, double2*, unsigned long long*, int, cudaStream_t);
 
 }  // namespace ext4pcf

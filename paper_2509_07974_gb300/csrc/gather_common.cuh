@@ -103,10 +103,7 @@ struct GatherArgs {
   SortedCat cat;
   Bins bins;
   Layout L;
-  const int* centres;  // the wave's first centre (sorted positions)
-  int T;               // centres of the wave at most
-  const int* n_live;   // device: centres of the catalogue (nullptr: T is exact)
-  int w0;              // the wave's first index in the catalogue's centre list
+  WavePlan plan;       // the wave's segments (centre lists, grids, record offsets)
   int cap;
   int mb;    // powers per warp block (<= MB)
   int nblk;  // power blocks

@@ -50,9 +50,10 @@ __global__ void bbox_final(const double* __restrict__ part, int np, double* __re
 }
 
 // ------------------------------------------------------------------------ device grid
-// cell side: about an eighth of the largest separation, at most ~4000 cells per axis, and
-// with 12 significant bits so that (cell index) * cell is exact in float
-__global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, GridGeom* __restrict__ g) {
+// cell side: about an eighth of the largest separation, at most ~4000 cells per axis and
+// about sqrt(n) per axis (so that the cells number at most 4n: grid_cells_cap), and with 12
+// significant bits so that (cell index) * cell is exact in float
+__global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, int n, GridGeom* __restrict__ g) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   GridGeom r;
   const bool finite = isfinite(bb[0]) && isfinite(bb[1]) && isfinite(bb[2]) && isfinite(bb[3]);
@@ -62,6 +63,10 @@ __global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, Gri
   const double extent = fmax(wx, wy);
   double c = rmax / 8.0;
   if (extent / 4000.0 > c) c = extent / 4000.0;
+  // 1.01: the rounding to 12 bits below lowers c by less than 2^-12, so floor(extent / c)
+  // stays below sqrt(n) and (sqrt(n) + 1)^2 <= 4n cells
+  const double cn = 1.01 * extent / sqrt((double)(n > 0 ? n : 1));
+  if (cn > c) c = cn;
   int ex;
   double m = frexp(c, &ex);          // c = m 2^ex, m in [0.5, 1)
   m = floor(m * 4096.0) / 4096.0;    // 12 significant bits
@@ -226,14 +231,16 @@ __global__ void cell_bounds(const int* __restrict__ keys, int n, int ncells, int
   for (int c = lo + 1; c <= hi; ++c) start[c] = p;
 }
 
-__global__ void cell_bounds_dev(const int* __restrict__ keys, int n, const GridGeom* __restrict__ g,
+// start[c] = c0 + first sorted position of cell c (c0: the catalogue's first galaxy in the
+// concatenated arrays)
+__global__ void cell_bounds_dev(const int* __restrict__ keys, int n, int c0, const GridGeom* __restrict__ g,
                                 int* __restrict__ start) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p > n) return;
   const int ncells = g->ncx * g->ncy;
   int lo = (p == 0) ? -1 : keys[p - 1];
   int hi = (p == n) ? ncells : keys[p];
-  for (int c = lo + 1; c <= hi; ++c) start[c] = p;
+  for (int c = lo + 1; c <= hi; ++c) start[c] = c0 + p;
 }
 
 __global__ void fill_start_empty(int* start, int ncells) {
@@ -326,7 +333,7 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
   return cudaGetLastError();
 }
 
-cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n,
+cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n, int c0,
                              const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
                              GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s) {
   out.n = n;
@@ -339,7 +346,7 @@ cudaError_t grid_sort_device(const double* pos, const double* shear, const doubl
   out.px = gb.px; out.py = gb.py; out.xr = gb.xr; out.xi = gb.xi; out.w = gb.w;
   out.p4 = gb.p4; out.s4 = gb.s4;
   if (n == 0) return cudaSuccess;
-  grid_geom_kernel<<<1, 32, 0, s>>>(d_bbox, rmax, d_geom);
+  grid_geom_kernel<<<1, 32, 0, s>>>(d_bbox, rmax, n, d_geom);
   make_keys_dev<<<(n + 255) / 256, 256, 0, s>>>(pos, n, d_geom, gb.keys, gb.perm, status);
   g_launches += 2;
   // keys below kMaxCellsPerAxis^2 < 2^24: three 8-bit digits
@@ -358,7 +365,7 @@ cudaError_t grid_sort_device(const double* pos, const double* shear, const doubl
     t = vin; vin = vout; vout = t;
   }
   out.perm = vin;
-  cell_bounds_dev<<<(n + 1 + 255) / 256, 256, 0, s>>>(kin, n, d_geom, gb.cell_start);
+  cell_bounds_dev<<<(n + 1 + 255) / 256, 256, 0, s>>>(kin, n, c0, d_geom, gb.cell_start);
   build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, d_geom, 0, 0.0, 0.0, 1.0, 1.f,
                                                want_f32, gb.px, gb.py, gb.xr, gb.xi, gb.w, gb.p4, gb.s4);
   g_launches += 2;

@@ -64,6 +64,7 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Config)]
     lib.ext4pcf_destroy.argtypes = [P]
     lib.ext4pcf_measure.argtypes = [P, P, P, P, I64, P, I, I, P, I, P, P, P, ctypes.POINTER(Stats)]
+    lib.ext4pcf_measure_batch.argtypes = [P, P, P, P, I64, P, I, I, P, I, P, I, P, P, P, ctypes.POINTER(Stats)]
     lib.ext4pcf_to_real_space.argtypes = [P, P, I, I, I, P, P]
     lib.ext4pcf_to_map4.argtypes = [P, P, P, I, I, I, P, I, P, P, P, P]
     lib.ext4pcf_to_real_space_noalloc.argtypes = [P, I, I, I, P, P, P]
@@ -80,7 +81,7 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_synchronize.restype = I
     lib.ext4pcf_last_error.argtypes = [P]
     lib.ext4pcf_last_error.restype = ctypes.c_char_p
-    for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_to_real_space",
+    for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_measure_batch", "ext4pcf_to_real_space",
               "ext4pcf_to_map4", "ext4pcf_map_direct"):
         getattr(lib, f).restype = I
     _lib = lib
@@ -139,6 +140,18 @@ def ext4pcf_measure(ctx, positions, shears, weights, n_gal, radial_bins, n_bins,
                              _addr(radial_bins), int(n_bins), int(n_max), _addr(cat_offsets),
                              int(n_cat), _addr(centre_mask), _addr(upsilon), _addr(xi_acc),
                              ctypes.byref(stats) if stats is not None else None)
+    return _check(ctx, rc)
+
+
+def ext4pcf_measure_batch(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max,
+                          cat_offsets, n_cat, out_slot=None, n_out=0, centre_mask=None, upsilon=None,
+                          xi_acc=None, stats: Stats | None = None) -> int:
+    lib = load()
+    rc = lib.ext4pcf_measure_batch(ctx, _addr(positions), _addr(shears), _addr(weights), int(n_gal),
+                                   _addr(radial_bins), int(n_bins), int(n_max), _addr(cat_offsets),
+                                   int(n_cat), _addr(out_slot), int(n_out), _addr(centre_mask),
+                                   _addr(upsilon), _addr(xi_acc),
+                                   ctypes.byref(stats) if stats is not None else None)
     return _check(ctx, rc)
 
 

@@ -1,0 +1,57 @@
+"""Input generators of the batched and survey workloads (host code, no GPU): the patcher's
+cores partition the catalogue and every patch holds exactly its core grown by the margin;
+the mock suite's sizes and densities stay in their ranges; the lognormal field is skewed."""
+import numpy as np
+
+import synth
+
+
+def test_patch_cores_partition_the_catalogue_and_margins_are_complete():
+    side, n_side, margin = 90.0, 3, 12.0
+    pos, _, _ = synth.uniform_catalog(6000, side, seed=3)
+    pos[:3] = [[0.0, 0.0], [side - 1e-9, side - 1e-9], [30.0, 60.0]]  # corners and a core edge
+    idx, offs, mask = synth.flat_patches(pos, side, n_side, margin)
+    n = len(pos)
+    assert offs[0] == 0 and offs[-1] == len(idx) == len(mask)
+    assert np.array_equal(np.sort(idx[mask == 1]), np.arange(n))  # a centre exactly once
+    core = side / n_side
+    x, y = pos[:, 0], pos[:, 1]
+    cx = np.clip(np.floor(x / core), 0, n_side - 1)
+    cy = np.clip(np.floor(y / core), 0, n_side - 1)
+    for p in range(n_side * n_side):
+        qy, qx = divmod(p, n_side)
+        members = idx[offs[p]:offs[p + 1]]
+        grown = (x >= qx * core - margin) & (x < (qx + 1) * core + margin) & \
+                (y >= qy * core - margin) & (y < (qy + 1) * core + margin)
+        in_core = (cx == qx) & (cy == qy)
+        assert np.array_equal(np.sort(members), np.flatnonzero(grown | in_core))
+        assert np.array_equal(np.sort(members[mask[offs[p]:offs[p + 1]] == 1]), np.flatnonzero(in_core))
+        # every galaxy closer than the margin to a core galaxy of p is in p
+        cpos = pos[in_core]
+        if len(cpos):
+            d2 = ((pos[None, :, :] - cpos[:200, None, :]) ** 2).sum(-1)
+            near = np.flatnonzero((d2 < margin * margin).any(0))
+            assert np.isin(near, members).all()
+
+
+def test_mock_suite_sizes_and_densities():
+    pos, sh, w, offs, sides = synth.mock_suite(6, seed=9, grid=128, scale=0.01)
+    n = np.diff(offs)
+    assert len(n) == 6 and offs[-1] == len(pos) == len(sh) == len(w)
+    full = n / 0.01
+    assert np.all((full >= 5e5 * 0.999) & (full <= 5e6 * 1.001))
+    assert np.all((sides >= 300 * 0.1) & (sides <= 900 * 0.1))
+    for k in range(6):
+        p = pos[offs[k]:offs[k + 1]]
+        assert p.min() >= 0 and p.max() < sides[k]
+    assert len(set(np.round(sides, 6))) == 6
+
+
+def test_lognormal_convergence_is_skewed_zero_mean_and_scaled():
+    kap = synth.lognormal_convergence(256, 200.0, seed=4, sigma_kappa=0.02, sigma_g=1.0)
+    assert abs(kap.mean()) < 1e-12 and abs(kap.std() - 0.02) < 1e-12
+    z = (kap - kap.mean()) / kap.std()
+    assert (z ** 3).mean() > 1.0  # a Gaussian field has zero skewness
+    assert kap.min() > -3 * kap.std()  # bounded below (long tail upwards)
+    g1, g2 = synth.kaiser_squires_shear(kap, 200.0)
+    assert np.isfinite(g1).all() and np.isfinite(g2).all()
