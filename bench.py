@@ -235,8 +235,17 @@ def run_reference(args):
     world, rank, _ = dist_setup(False)
     if rank != 0:
         return
-    pos, sh, w, edges, nmax, c = make_workload(n=args.n_gal)
-    n_c = args.oracle_centres
+    if args.workload == "grf2e6":
+        pos, sh, w, edges, nmax, c = make_workload(n=args.n_gal)
+        n_c = args.oracle_centres
+        name = c["name"]
+    else:
+        # the first catalogue of the batched workload (its own galaxies as neighbours)
+        pos, sh, w, offs, _, _, _, edges, nmax, wc = batched_workload(args.workload, args)
+        pos, sh, w = pos[offs[0]:offs[1]], sh[offs[0]:offs[1]], w[offs[0]:offs[1]]
+        n_c = min(args.oracle_centres, 40 if args.workload == "batch64" else 12)
+        name = wc["workload"] + " (oracle on the first catalogue)"
+        c = {"nb": len(edges) - 1}
     mask, _, _ = oracle_sample(pos, sh, w, edges, nmax, n_c)  # warm-up build and page-in
     pairs = pairs_of_mask(pos, edges, mask)
     for _ in range(max(0, args.warmup - 1)):
@@ -252,7 +261,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": c["name"], "n_gal": len(w), "n_bins": c["nb"], "n_max": nmax,
+            "config": {"workload": name, "n_gal": len(w), "n_bins": c["nb"], "n_max": nmax,
                        "sample": sample},
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
@@ -555,6 +564,222 @@ def run_ours(args):
     est.close()
 
 
+# ------------------------------------------------------------------------------------------
+# Batched and survey workloads (ext4pcf_measure_batch, one captured CUDA graph per step)
+def batched_workload(kind, args, seed_offset=0):
+    """(pos, shear, w, cat_offsets, out_slot or None, n_out, centre mask, edges, n_max, config)
+    of the batched form (64 uneven GRF mocks, one slot each) or the survey (1e8 lognormal
+    galaxies in 10 x 10 patches with 120' margins, all patches in one slot).  The centres are
+    a seeded sample: per mock (or per patch core) `per_cat` of its galaxies."""
+    import synth
+    rng = np.random.default_rng(4321 + seed_offset)
+    if kind == "batch64":
+        c = synth.BATCH64
+        pos, sh, w, offs, edges, nmax = synth.batch64_workload(n_mocks=args.n_cat)
+        per_cat = args.centres_per_cat or 1024
+        mask = np.zeros(len(w), np.uint8)
+        for k in range(len(offs) - 1):
+            nk = int(offs[k + 1] - offs[k])
+            mask[offs[k] + rng.choice(nk, min(per_cat, nk), replace=False)] = 1
+        slots, n_out = None, len(offs) - 1
+        cfg = {"workload": c["name"], "n_cat": len(offs) - 1, "n_gal": len(w),
+               "galaxies_per_mock": [int(v) for v in (np.min(np.diff(offs)), np.max(np.diff(offs)))],
+               "centres_per_mock": per_cat}
+    else:
+        c = synth.SURVEY
+        n = args.n_gal or c["n"]
+        side = c["side"] * (n / c["n"]) ** 0.5
+        pos, sh, w, offs, core, edges, nmax = synth.survey_workload(n=n, side=side)
+        n_side = int(round((len(offs) - 1) ** 0.5))
+        per_cat = args.centres_per_cat or 128
+        mask = np.zeros(len(w), np.uint8)
+        for k in range(len(offs) - 1):
+            cidx = offs[k] + np.flatnonzero(core[offs[k]:offs[k + 1]])
+            mask[rng.choice(cidx, min(per_cat, len(cidx)), replace=False)] = 1
+        slots, n_out = np.zeros(len(offs) - 1, np.int32), 1
+        cfg = {"workload": c["name"] if n == c["n"] else "lognormal survey %.3g gal (same density), %.0f'x%.0f', "
+               "%dx%d patches + 120' margins, 12 log bins 0.5'-120', n_max=30" % (n, side, side, n_side, n_side),
+               "n_gal": int(n), "n_gal_patched": len(w), "n_cat": len(offs) - 1, "centres_per_patch": per_cat}
+    return pos, sh, w, offs, slots, n_out, mask, edges, nmax, cfg
+
+
+def run_batched(args, kind):
+    import torch
+
+    from paper_2509_07974_gb300 import build, ext4pcf
+
+    world, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    pk = peaks()
+    t_gen = time.perf_counter()
+    pos, sh, w, offs, slots, n_out, mask, edges, nmax, wcfg = batched_workload(kind, args, seed_offset=rank)
+    log("rank %d: workload generated in %.1f s (%d galaxies, %d catalogues)" % (rank, time.perf_counter() - t_gen,
+                                                                                len(w), len(offs) - 1))
+    nb = len(edges) - 1
+    n_cat = len(offs) - 1
+    tp = torch.tensor(pos, device=dev)
+    ts = torch.tensor(sh, device=dev)
+    tw = torch.tensor(w, device=dev)
+    hmask = torch.tensor(mask).pin_memory()  # pinned host mask: counts known on the host, copy in the graph
+    stream = torch.cuda.Stream(dev)
+    cfg = ext4pcf.Config(device=local, stream=stream.cuda_stream, precision=ext4pcf.PRECISION[args.precision],
+                         autotune=1, workspace_bytes=0, timeout_cycles=0, deterministic=1, wave_centres=0)
+    ctx = ext4pcf.ext4pcf_create(cfg)
+    shape = (n_out,) + tuple(ext4pcf.Estimator.ups_shape(nb, nmax)[1:])
+    ups = torch.zeros(shape, dtype=torch.float64, device=dev)
+    xia = torch.zeros((n_out, nb, 3, 2), dtype=torch.float64, device=dev)
+    edges_c = np.ascontiguousarray(edges)
+    offs_c = np.ascontiguousarray(offs, dtype=np.int64)
+    slots_c = None if slots is None else np.ascontiguousarray(slots, dtype=np.int32)
+    n_out_arg = n_out if slots is not None else 0
+    want_map4 = kind == "survey"
+    ap = np.ascontiguousarray(AP_RADII)
+    m4 = np.zeros((len(ap), 8, 2))
+    eb = np.zeros((len(ap), 16))
+    disc = np.zeros((len(ap), 16))
+
+    def measure(stats=None, p=tp, s=ts, ww=tw):
+        ext4pcf.ext4pcf_measure_batch(ctx, p, s, ww, len(w), edges_c, nb, nmax, offs_c, n_cat, slots_c, n_out_arg,
+                                      hmask, ups, xia, stats)
+
+    # the first call autotunes the wave size (timed trial waves) and sizes every buffer; the
+    # second gives the steady-state phase breakdown and the pair count
+    with torch.cuda.stream(stream):
+        st0 = ext4pcf.Stats()
+        measure(st0)
+        st = ext4pcf.Stats()
+        ups.zero_()
+        xia.zero_()
+        measure(st)
+    stream.synchronize()
+    bd = st.as_dict()
+    pairs = bd["pairs"]
+    log("rank %d: %s" % (rank, bd))
+    # one step = the captured graph (zero the outputs, the batched measure) [+ the FP64
+    # aperture measures of the survey's Upsilon, which read results back to the host]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+        ups.zero_()
+        xia.zero_()
+        measure()
+    if ext4pcf.ext4pcf_synchronize(ctx) != ext4pcf.EXT4PCF_OK:
+        raise RuntimeError("status after capture")
+
+    def step():
+        with torch.cuda.stream(stream):  # the graph replays on the current stream
+            g.replay()
+            if want_map4:
+                ext4pcf.ext4pcf_to_map4(ctx, ups[0], edges_c, nb, nmax, N_PHI, ap, len(ap), xia[0], m4, eb, disc)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+    if ext4pcf.ext4pcf_synchronize(ctx) != ext4pcf.EXT4PCF_OK:
+        raise RuntimeError("status after the timed steps")
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    dev_ms_max = max_over_ranks(dev_ms, world, dev)
+    pairs_all = sum_over_ranks(float(pairs) * args.steps, world, dev)
+    value = pairs_all / (dev_ms_max / 1e3)
+    clocks = cs.summary(pk.get("sm_max_mhz", 2070.0))
+
+    # end to end through the C ABI: inputs from pinned host buffers (copied inside the call),
+    # the xi accumulators (and the survey's aperture measures) read back to the host
+    hp = torch.tensor(pos).pin_memory()
+    hs = torch.tensor(sh).pin_memory()
+    hw = torch.tensor(w).pin_memory()
+    hxi = np.zeros((n_out, nb, 3, 2))
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            ups.zero_()
+            hxi[:] = 0
+            ext4pcf.ext4pcf_measure_batch(ctx, hp, hs, hw, len(w), edges_c, nb, nmax, offs_c, n_cat, slots_c,
+                                          n_out_arg, hmask, ups, hxi, None)
+            if want_map4:
+                ext4pcf.ext4pcf_to_map4(ctx, ups[0], edges_c, nb, nmax, N_PHI, ap, len(ap),
+                                        np.ascontiguousarray(hxi[0]), m4, eb, disc)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = sum(e2e_t) / len(e2e_t)
+    h2d = hp.numel() * 8 + hs.numel() * 8 + hw.numel() * 8 + hmask.numel()
+    d2h = hxi.nbytes + ((m4.nbytes + eb.nbytes + disc.nbytes) if want_map4 else 0)
+
+    # rooflines of the two dominant kernels from the steady-state call's phase times
+    waves = max(1, bd["waves"])
+    flop_pair = gather_flop_per_pair(nmax)
+    g_ms = bd["ms_gather"] / waves
+    g_ach = flop_pair * pairs / (bd["ms_gather"] / 1e3) / 1e12
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    c_flop = reduced_contraction_flop(bd["centres"], nmax, nb)
+    c_tflops = c_flop / (bd["ms_contract"] / 1e3) / 1e12 if bd["ms_contract"] > 0 else None
+    peak_c = pk.get("bf16_tflops_sustained", 1700.0)
+    roof_g = {"bound": "alu", "kernel": "gather", "achieved": g_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+              "frac": g_ach / fp32_peak, "traffic": None, "ms_per_launch": g_ms,
+              "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock",
+              "algorithmic_flop_per_pair": flop_pair}
+    roof_c = {"bound": "tensor", "kernel": "contraction", "achieved": c_tflops, "peak": peak_c, "unit": "TFLOP/s",
+              "frac": (c_tflops or 0.0) / peak_c, "frac_issued": 3 * (c_tflops or 0.0) / peak_c, "passes": 3,
+              "traffic": None, "ms_per_launch": bd["ms_contract"] / waves,
+              "peak_note": "kind::f16 dense: measured sustained bf16 (%s TFLOP/s, %s)"
+                           % (pk.get("bf16_tflops_sustained"), pk.get("source")),
+              "algorithmic_flop_per_centre": c_flop / max(1, bd["centres"])}
+    roof_main, roof_other = (roof_c, roof_g) if bd["ms_contract"] >= bd["ms_gather"] else (roof_g, roof_c)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_baselines:
+        # the oracle on a bounded sample: centres of the first catalogue (its galaxies only)
+        a, b = int(offs[0]), int(offs[1])
+        n_c = min(args.oracle_centres, 40 if kind == "batch64" else 12)
+        omask, odt, cores = oracle_sample(pos[a:b], sh[a:b], w[a:b], edges, nmax, n_c)
+        opairs = pairs_of_mask(pos[a:b], edges, omask)
+        cpu = {"value": opairs / odt, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": "%d random centres of the first catalogue (%d galaxies, all neighbours), %d pairs, %.1f s"
+                         % (n_c, b - a, opairs, odt)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(wcfg, **{"n_bins": nb, "n_max": nmax, "precision": args.precision,
+                                        "centres": int(bd["centres"]), "pairs_per_step": pairs,
+                                        "waves": int(bd["waves"]), "wave_centres": int(bd["wave_centres"]),
+                                        "wave_size": "autotuned over 2048, 4096, 8192, 16384 centres",
+                                        "graph": "one captured CUDA graph per step (grids, packed waves, "
+                                                 "expansion, corrections)",
+                                        "l2": "flushed between steps (256 MB write)",
+                                        "parallelism": "one workload per GPU" if world > 1 else "1 GPU"}),
+                "contraction_tflops": c_tflops,
+                "breakdown_ms": {k: bd[k] for k in ("ms_grid", "ms_gather", "ms_contract", "ms_correct", "ms_total")},
+                "wall_s": t_wall,
+                "e2e": {"value": pairs / e2e, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "roofline": roof_main, "roofline_secondary": roof_other, "cpu_baseline": cpu,
+                "clocks": clocks,
+                "gpu_launches": int(bd["launches"] * args.steps)}
+        if want_map4:
+            line["map4_by_radius"] = {"%.2f" % ap[i]: float(m4[i, 0, 0]) for i in (0, len(ap) // 2, len(ap) - 1)}
+        print(json.dumps(line), flush=True)
+    ext4pcf.ext4pcf_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,11 +792,19 @@ def main():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--centres", type=int, default=None,
                     help="profiling aid: only this many (seeded random) galaxies act as centres")
+    ap.add_argument("--workload", default="grf2e6", choices=["grf2e6", "batch64", "survey"],
+                    help="grf2e6: the 2e6-galaxy GRF mock (default); batch64: 64 uneven GRF mocks in one batched "
+                         "call; survey: 1e8 lognormal galaxies in 10x10 patches with 120' margins")
+    ap.add_argument("--centres-per-cat", type=int, default=None,
+                    help="batch64 / survey: sampled centres per mock (1024) or per patch core (128)")
+    ap.add_argument("--n-cat", type=int, default=64, help="batch64: number of mocks")
     ap.add_argument("--n-gal", type=int, default=None,
                     help="smaller catalogue at the same density (profiling); default 2e6")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "grf2e6":
+        run_batched(args, args.workload)
     else:
         run_ours(args)
 

@@ -87,6 +87,18 @@ typedef struct {
   int64_t timeout_cycles;  /* bound on every device-side wait (0 = default) */
   int deterministic;       /* 1: fixed summation order (always honoured at present) */
   int wave_centres;        /* centres per contraction wave (0 = autotuned or 8192, 4096 for FP64) */
+  /* Tree approximation of the neighbour multipoles (paper Sect. 3.4, App. F.3, Eq.
+   * NPCF_treeestimator): radial bins far from the centre take their neighbours from reduced
+   * catalogues, the galaxies of each cell of side Delta_d = tree_delta1 2^(d-1) (d = 1 ..
+   * tree_levels, grids anchored at each catalogue's lower bounding-box corner) replaced by one
+   * galaxy at their weighted centre of mass with the summed w and w gamma.  A bin uses the
+   * coarsest level with Theta_lo / Delta_d >= tree_rmin, the galaxies when none qualifies.  The
+   * centres stay the galaxies.  tree_delta1 = 0 (or tree_levels = 0): exact multipoles.  With
+   * the tree in use a measure call reads the reduced catalogues' sizes back (one
+   * synchronisation). */
+  double tree_delta1;
+  int tree_levels;         /* 0 .. 8 */
+  double tree_rmin;
 } ext4pcf_config;
 
 typedef struct {
@@ -162,6 +174,24 @@ EXT4PCF_API int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions,
                     int n_max, const int64_t* cat_offsets, int n_cat, const int* out_slot,
                     int n_out, const uint8_t* centre_mask, double* upsilon, double* xi_acc,
                     ext4pcf_stats* stats);
+
+/* Per-centre neighbour multipoles (the gather of ext4pcf_measure, its output kept): for each
+ * requested galaxy the record of sums over its neighbours j in each radial bin, u = e^{i phi_ij},
+ * x = w gamma_c, as complex FP64 pairs (the gather runs in FP64 for EXT4PCF_FP64, in FP32
+ * otherwise), with the tree approximation of the configuration if set:
+ *   G_n   = sum x u^n          n = -2N-3 .. 2N-1   [(4N+3)][n_bins]
+ *   W_m   = sum w u^m          m = 0 .. 2N         [(2N+1)][n_bins]   (W_-m = conj W_m)
+ *   XX_n  = sum x^2 u^n        n = -2N-6 .. 2N-2   [(4N+5)][n_bins]
+ *   XA_m  = sum |x|^2 u^m      m = 0 .. 2N+2       [(2N+3)][n_bins]
+ *   WW_m  = sum w^2 u^m        m = 0 .. 2N         [(2N+1)][n_bins]
+ *   TR    = sum x^3 u^-8, x^3 u^-4, x^2 x^* u^-4, x^2 x^*, w^3   [5][n_bins]
+ * concatenated in this order, the bin fastest: rec = (14N + 18) n_bins complex values a centre.
+ *   centres   host, int64 [n_centres]: indices into the catalogue (0 <= centre < n_gal)
+ *   records   device or host, double [n_centres][rec][2]
+ * One catalogue; synchronises when records is host memory. */
+EXT4PCF_API int ext4pcf_multipoles(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                    const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
+                    int n_max, const int64_t* centres, int64_t n_centres, double* records);
 
 /* Multipoles -> real space (paper Eq. Multipole2RealConversion, FP64).  The angular
  * density is integrated over n_phi uniform bins of [0, 2 pi) on each of phi_12, phi_13,

@@ -59,6 +59,22 @@ __global__ void mask_compact(const unsigned* __restrict__ flag_scan, const uint8
   if (p < n && (!mask || mask[perm[p]] != 0)) centres[flag_scan[p]] = c0 + p;
   if (p == n - 1) *count = (int)flag_scan[p] + ((!mask || mask[perm[p]] != 0) ? 1 : 0);
 }
+// inv[i] = sorted position of galaxy i (perm: sorted position -> galaxy)
+__global__ void inverse_perm(const int* __restrict__ perm, int n, int* __restrict__ inv) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) inv[perm[p]] = p;
+}
+__global__ void pick_centres(const int64_t* __restrict__ idx, int64_t n, const int* __restrict__ inv,
+                             int* __restrict__ centres) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) centres[j] = inv[idx[j]];
+}
+// a wave's records as FP64 complex pairs
+template <typename R>
+__global__ void records_out(const ext4pcf::cplx_t<R>* __restrict__ rec, size_t n, double2* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)rec[i].x, (double)rec[i].y);
+}
 __global__ void iota(int* a, int n, int c0) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) a[p] = c0 + p;
@@ -93,6 +109,13 @@ struct ext4pcf_ctx {
   size_t tc_items_bytes = 0;
   cudaEvent_t ev[8] = {};
   std::vector<cudaEvent_t> tev;  // per-phase timing events of one measure call (grown on demand)
+  // tree approximation: per level, the reduced catalogues (cell order, per catalogue at its
+  // galaxies' offsets), their sizes, and their sorted arrays and grids (at offsets by size)
+  struct Level {
+    DBuf rpos, rsh, rw, cnt, px, py, xr, xi, w, p4, s4, cells, geom;
+  };
+  Level lv[9];
+  DBuf inv, rec_idx, rec_out;  // ext4pcf_multipoles: inverse sort order, centre list, staged records
   // wave sizes chosen by the autotuner, per (precision, n_max, n_bins)
   std::map<std::tuple<int, int, int>, int> tuned;
   int64_t last_wave = 0;
@@ -219,6 +242,11 @@ int ext4pcf_destroy(ext4pcf_ctx* ctx) {
                  &ctx->tc_xb, &ctx->tc_red, &ctx->tc_rowmax, &ctx->status, &ctx->geom, &ctx->ap_cen, &ctx->ap_sums, &ctx->io_rec, &ctx->io_mom};
   for (DBuf* b : all)
     if (b->p) cudaFree(b->p);
+  for (auto& L : ctx->lv)
+    for (DBuf* b : {&L.rpos, &L.rsh, &L.rw, &L.cnt, &L.px, &L.py, &L.xr, &L.xi, &L.w, &L.p4, &L.s4, &L.cells, &L.geom})
+      if (b->p) cudaFree(b->p);
+  for (DBuf* b : {&ctx->inv, &ctx->rec_idx, &ctx->rec_out})
+    if (b->p) cudaFree(b->p);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto e : ctx->tev)
@@ -238,18 +266,33 @@ int ext4pcf_synchronize(ext4pcf_ctx* ctx) {
   return r != EXT4PCF_OK ? r : rc;
 }
 
-int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const double* shears,
-                          const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
-                          int n_max, const int64_t* cat_offsets, int n_cat, const int* out_slot, int n_out,
-                          const uint8_t* centre_mask, double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
+}  // extern "C"
+
+namespace {
+// The measure pipeline.  Records mode (rec_out non-null, one catalogue): the centres are the
+// galaxies rec_centres[0 .. n_rec) (indices into the catalogue) and their multipole records
+// are written to rec_out instead of being contracted.
+int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears, const double* weights,
+                 int64_t n_gal, const double* radial_bins, int n_bins, int n_max, const int64_t* cat_offsets,
+                 int n_cat, const int* out_slot, int n_out, const uint8_t* centre_mask, double* upsilon,
+                 double* xi_acc, ext4pcf_stats* stats, const int64_t* rec_centres, int64_t n_rec, double* rec_out) {
   if (!ctx) return EXT4PCF_E_INVALID_ARG;
+  const bool records = rec_out != nullptr;
   ctx->err.clear();
   if (std::getenv("EXT4PCF_FAULT") && std::strcmp(std::getenv("EXT4PCF_FAULT"), "arg") == 0)
     return fail(ctx, EXT4PCF_E_INVALID_ARG, "fault injection: argument check");
   if (n_gal < 0 || n_gal > (int64_t)2000000000) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_gal out of range");
   if (n_bins < 1 || n_bins > 32) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_bins must be in 1..32");
   if (n_max < 0 || n_max > 40) return fail(ctx, EXT4PCF_E_INVALID_ARG, "n_max must be in 0..40");
-  if (!radial_bins || !upsilon) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null radial_bins or upsilon");
+  if (!radial_bins || (!upsilon && !records)) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null radial_bins or upsilon");
+  if (records && (cat_offsets || centre_mask || n_rec < 0 || (n_rec > 0 && !rec_centres)))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "multipole records: one catalogue, centres by index");
+  for (int64_t i = 0; records && i < n_rec; ++i)
+    if (rec_centres[i] < 0 || rec_centres[i] >= n_gal)
+      return fail(ctx, EXT4PCF_E_INVALID_ARG, "centre index out of range");
+  const bool tree = ctx->cfg.tree_delta1 > 0.0 && ctx->cfg.tree_levels > 0;
+  if (tree && (!(ctx->cfg.tree_rmin > 0.0) || ctx->cfg.tree_levels > 8 || !std::isfinite(ctx->cfg.tree_delta1)))
+    return fail(ctx, EXT4PCF_E_INVALID_ARG, "tree approximation: 1 <= tree_levels <= 8, tree_rmin > 0");
   if (n_gal > 0 && (!positions || !shears || !weights)) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null input");
   if (!(radial_bins[0] > 0.0) || !std::isfinite(radial_bins[n_bins]))
     return fail(ctx, EXT4PCF_E_INVALID_ARG, "radial_bins[0] must be > 0 and finite");
@@ -289,7 +332,9 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
   const uint8_t* d_mask = centre_mask;
   double* d_ups = upsilon;
   double* d_xi = xi_acc;
-  const bool host_ups = !is_device_ptr(upsilon);
+  const bool host_ups = !records && !is_device_ptr(upsilon);
+  const bool rec_host = records && !is_device_ptr(rec_out);
+  if (rec_host) ENSURE(ctx->rec_out, (size_t)std::max<int64_t>(n_rec, 1) * Layout::make(n_max, n_bins).rec * 16);
   const bool host_xi = xi_acc && !is_device_ptr(xi_acc);
   if (n > 0 && !is_device_ptr(positions)) {
     ENSURE(ctx->in_pos, n * 16);
@@ -379,7 +424,9 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
   const bool host_mask = centre_mask && !is_device_ptr(centre_mask);
   for (int k = 0; k < n_cat; ++k) {
     const int64_t nk = c0v[k + 1] - c0v[k];
-    if (!centre_mask) {
+    if (records) {
+      ncent[k] = n_rec;
+    } else if (!centre_mask) {
       ncent[k] = nk;
     } else if (host_mask) {
       int64_t c = 0;
@@ -444,7 +491,18 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
                         bins.rmax, geoms + k, !f64, gb, sk, (int*)ctx->status.p, s));
     // centre list (concatenated sorted positions of the centres); with a mask the count goes
     // to ncen[k] on the device
-    if (mask_k) {
+    if (records) {  // the requested galaxies, through the inverse of the sort order
+      ENSURE(ctx->inv, (size_t)nk * 4);
+      ENSURE(ctx->rec_idx, (size_t)std::max<int64_t>(n_rec, 1) * 8);
+      inverse_perm<<<(nk + 255) / 256, 256, 0, s>>>(sk.perm, nk, (int*)ctx->inv.p);
+      if (n_rec > 0) {
+        CK(cudaMemcpyAsync(ctx->rec_idx.p, rec_centres, (size_t)n_rec * 8, cudaMemcpyHostToDevice, s));
+        pick_centres<<<(int)((n_rec + 255) / 256), 256, 0, s>>>((const int64_t*)ctx->rec_idx.p, n_rec,
+                                                               (const int*)ctx->inv.p, clist);
+      }
+      g_launches += 2;
+      CK(cudaGetLastError());
+    } else if (mask_k) {
       unsigned* flag = (unsigned*)ctx->flags.p;
       mask_flags<<<(nk + 255) / 256, 256, 0, s>>>(mask_k, sk.perm, nk, flag);
       g_launches += 2;  // flags + compaction
@@ -456,6 +514,124 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
       iota<<<(nk + 255) / 256, 256, 0, s>>>(clist + c0, nk, (int)c0);
       ++g_launches;
       CK(cudaGetLastError());
+    }
+  }
+  // ---- tree approximation: the level of every radial bin (the coarsest d with
+  // Theta_lo / Delta_d >= r_min, else 0: the galaxies), the reduced catalogues of the levels in
+  // use and their grids; the gather then runs one pass per level over that level's bins
+  struct Pass {
+    int level, blo, bhi;
+    SortedCat cat;
+    const GridGeom* geoms;
+    const int* cells;
+    std::vector<int64_t> coff;
+    Bins bins;
+  };
+  std::vector<Pass> passes;
+  {
+    std::vector<int> blev(n_bins, 0);
+    if (tree)
+      for (int b = 0; b < n_bins; ++b)
+        for (int d = ctx->cfg.tree_levels; d >= 1; --d)
+          if (radial_bins[b] / (ctx->cfg.tree_delta1 * std::ldexp(1.0, d - 1)) >= ctx->cfg.tree_rmin) {
+            blev[b] = d;
+            break;
+          }
+    for (int b = 0; b < n_bins;) {  // levels never decrease with the bin (its inner edge grows)
+      int e = b;
+      while (e < n_bins && blev[e] == blev[b]) ++e;
+      Pass P;
+      P.level = blev[b];
+      P.blo = b;
+      P.bhi = e;
+      P.bins = bins;
+      for (int q = 0; q <= n_bins; ++q) {  // bins outside [blo, bhi) get zero width
+        const int qq = q < b ? b : (q > e ? e : q);
+        P.bins.e2[q] = bins.e2[qq];
+        P.bins.e2f[q] = bins.e2f[qq];
+      }
+      P.bins.rmax = radial_bins[e];
+      passes.push_back(P);
+      b = e;
+    }
+  }
+  for (Pass& P : passes)
+    if (P.level == 0) {
+      P.cat = cat;
+      P.geoms = geoms;
+      P.cells = cells;
+      P.coff = cell_off;
+    }
+  if (tree) {
+    // reduced catalogues, per level in use and catalogue, at the galaxies' offsets
+    std::vector<int> lev_used;
+    for (const Pass& P : passes)
+      if (P.level > 0) lev_used.push_back(P.level);
+    ENSURE(ctx->flags, ((size_t)nk_max + (size_t)nk_max / 1000 + 4096) * 4);
+    for (int d : lev_used) {
+      ext4pcf_ctx::Level& V = ctx->lv[d];
+      ENSURE(V.rpos, n * 16); ENSURE(V.rsh, n * 16); ENSURE(V.rw, n * 8);
+      ENSURE(V.cnt, (size_t)n_cat * 4); ENSURE(V.geom, (size_t)std::max(n_cat, 1) * sizeof(GridGeom));
+      const double delta = ctx->cfg.tree_delta1 * std::ldexp(1.0, d - 1);
+      for (int k = 0; k < n_cat; ++k) {
+        const int64_t c0 = c0v[k];
+        const int nk = (int)(c0v[k + 1] - c0);
+        GridBuffers gb{};
+        gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+        gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+        gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+        CK(grid_bbox(d_pos + 2 * c0, nk, (double*)ctx->bbox.p, s));
+        CK(reduce_catalogue(d_pos + 2 * c0, d_sh + 2 * c0, d_w + c0, nk, (const double*)ctx->bbox.p, delta,
+                            (GridGeom*)V.geom.p + k, gb, (unsigned*)ctx->flags.p, (double*)V.rpos.p + 2 * c0,
+                            (double*)V.rsh.p + 2 * c0, (double*)V.rw.p + c0, (int*)V.cnt.p + k,
+                            (int*)ctx->status.p, s));
+      }
+    }
+    // their sizes (the one synchronisation of the tree approximation)
+    std::vector<std::vector<int>> m(9, std::vector<int>(n_cat, 0));
+    for (int d : lev_used) CK(cudaMemcpyAsync(m[d].data(), ctx->lv[d].cnt.p, (size_t)n_cat * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (Pass& P : passes) {
+      if (P.level == 0) continue;
+      const int d = P.level;
+      ext4pcf_ctx::Level& V = ctx->lv[d];
+      std::vector<int64_t> cm(n_cat + 1, 0);
+      P.coff.assign(n_cat + 1, 0);
+      for (int k = 0; k < n_cat; ++k) {
+        cm[k + 1] = cm[k] + m[d][k];
+        P.coff[k + 1] = P.coff[k] + (m[d][k] > 0 ? (int64_t)grid_cells_cap(m[d][k]) : 0);
+      }
+      const size_t nm = (size_t)std::max<int64_t>(cm[n_cat], 1);
+      ENSURE(V.px, nm * 8); ENSURE(V.py, nm * 8); ENSURE(V.xr, nm * 8); ENSURE(V.xi, nm * 8); ENSURE(V.w, nm * 8);
+      if (!f64) { ENSURE(V.p4, nm * 16); ENSURE(V.s4, nm * 16); }
+      ENSURE(V.cells, (size_t)std::max<int64_t>(P.coff[n_cat], 1) * 4);
+      for (int k = 0; k < n_cat; ++k) {
+        const int mk = m[d][k];
+        if (mk == 0) continue;
+        const int64_t c0 = c0v[k];
+        GridBuffers gb{};
+        gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+        gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+        gb.cell_start = (int*)V.cells.p + P.coff[k]; gb.cell_cap = (size_t)(P.coff[k + 1] - P.coff[k]);
+        gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+        gb.px = (double*)V.px.p + cm[k]; gb.py = (double*)V.py.p + cm[k];
+        gb.xr = (double*)V.xr.p + cm[k]; gb.xi = (double*)V.xi.p + cm[k]; gb.w = (double*)V.w.p + cm[k];
+        gb.p4 = f64 ? nullptr : (float4*)V.p4.p + cm[k]; gb.s4 = f64 ? nullptr : (float4*)V.s4.p + cm[k];
+        gb.bbox = (double*)ctx->bbox.p;
+        SortedCat sk;
+        const double* rp = (const double*)V.rpos.p + 2 * c0;
+        CK(grid_bbox(rp, mk, (double*)ctx->bbox.p, s));
+        CK(grid_sort_device(rp, (const double*)V.rsh.p + 2 * c0, (const double*)V.rw.p + c0, mk, (int)cm[k],
+                            (const double*)ctx->bbox.p, P.bins.rmax, (GridGeom*)V.geom.p + k, !f64, gb, sk,
+                            (int*)ctx->status.p, s));
+      }
+      P.cat = SortedCat{};
+      P.cat.n = (int)cm[n_cat];
+      P.cat.px = (const double*)V.px.p; P.cat.py = (const double*)V.py.p;
+      P.cat.xr = (const double*)V.xr.p; P.cat.xi = (const double*)V.xi.p; P.cat.w = (const double*)V.w.p;
+      P.cat.p4 = (const float4*)V.p4.p; P.cat.s4 = (const float4*)V.s4.p;
+      P.geoms = (const GridGeom*)V.geom.p;
+      P.cells = (const int*)V.cells.p;
     }
   }
   if (timing) marks.push_back({0, t_grid0, tmark()});
@@ -492,7 +668,7 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
   // repeated -- and are timed; the fastest per centre is kept for this shape.  These waves
   // synchronise.
   std::vector<int> trial;
-  if (ctx->cfg.autotune && ctx->cfg.wave_centres <= 0 && tit == ctx->tuned.end() && all_known) {
+  if (ctx->cfg.autotune && ctx->cfg.wave_centres <= 0 && tit == ctx->tuned.end() && all_known && !records) {
     const int cand[4] = {2048, 4096, 8192, 16384};
     int64_t need = 0;
     for (int c : cand)
@@ -554,6 +730,7 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
       g.t = take;
       g.off = fill;
       g.slot = slot_of(pk);
+      g.cat = pk;
       P.total = fill + take;
       pw0 += take;
       fill = (fill + take + 63) / 64 * 64;
@@ -574,12 +751,31 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
     largest_wave = std::max(largest_wave, P.total);
     if (tuning) CK(cudaEventRecord(ctx->ev[1], s));
     if (timing) t_w0 = tmark();
-    if (f64) {
-      CK(gather_wave<double>(cat, bins, L, P, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
-                             (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
-    } else {
-      CK(gather_wave<float>(cat, bins, L, P, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
-                            (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+    for (size_t pi = 0; pi < passes.size(); ++pi) {  // one pass per level: its bins, its neighbours
+      const Pass& G = passes[pi];
+      WavePlan Q = P;
+      for (int q = 0; q < Q.nseg; ++q) {
+        Q.seg[q].geom = G.geoms + Q.seg[q].cat;
+        Q.seg[q].cell_start = G.cells + G.coff[Q.seg[q].cat];
+      }
+      if (f64) {
+        CK(gather_wave<double>(G.cat, cat, G.bins, L, Q, pi > 0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      } else {
+        CK(gather_wave<float>(G.cat, cat, G.bins, L, Q, pi > 0, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+                              (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      }
+    }
+    if (records) {  // the wave's records to the output, at the centres' places in the request
+      const size_t nrec = (size_t)g0.t * L.rec;
+      double2* dst = (double2*)(rec_host ? ctx->rec_out.p : (void*)rec_out) + (size_t)g0.w0 * L.rec;
+      if (f64) records_out<double><<<1024, 256, 0, s>>>((const double2*)ctx->rec.p, nrec, dst);
+      else records_out<float><<<1024, 256, 0, s>>>((const float2*)ctx->rec.p, nrec, dst);
+      ++g_launches;
+      CK(cudaGetLastError());
+      ++wave_i;
+      ++tot_waves;
+      continue;
     }
     if (timing) t_w1 = tmark();
     if (f64) {
@@ -628,8 +824,10 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
     ++tot_waves;
   }
   ctx->last_wave = std::min(T, largest_wave);  // the wave size in use (trial waves aside)
+  if (records && rec_host && n_rec > 0)
+    CK(cudaMemcpyAsync(rec_out, ctx->rec_out.p, (size_t)n_rec * L.rec * 16, cudaMemcpyDeviceToHost, s));
   // ---- per output slot: every ordered triple from the reduced array, then the corrections
-  for (int o = 0; o < n_out; ++o) {
+  for (int o = 0; o < n_out && !records; ++o) {
     double* ups_o = d_ups + 2 * ups_elems * (size_t)o;
     if (tc) CK(tc_expand(L, red_base + red_doubles * (size_t)o, ups_o, s));
     CK(corrections_apply(L, corr_base + corr_doubles * (size_t)o, ups_o, s));
@@ -638,7 +836,7 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
   if (host_xi) CK(cudaMemcpyAsync(xi_acc, d_xi, xi_bytes * n_out, cudaMemcpyDeviceToHost, s));
   // a call that synchronises anyway (host outputs or statistics) reports the status word;
   // a device-only call returns after enqueueing and leaves it to ext4pcf_synchronize
-  if (host_ups || host_xi || timing) {
+  if (host_ups || host_xi || timing || rec_host) {
     int rc = EXT4PCF_OK;
     const int r = read_status(ctx, &rc);
     if (r != EXT4PCF_OK) return r;
@@ -679,13 +877,32 @@ int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const doubl
   CK(cudaGetLastError());
   return EXT4PCF_OK;
 }
+}  // namespace
+
+extern "C" {
+
+int ext4pcf_measure_batch(ext4pcf_ctx* ctx, const double* positions, const double* shears,
+                          const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
+                          int n_max, const int64_t* cat_offsets, int n_cat, const int* out_slot, int n_out,
+                          const uint8_t* centre_mask, double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
+  return measure_impl(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, cat_offsets, n_cat,
+                      out_slot, n_out, centre_mask, upsilon, xi_acc, stats, nullptr, 0, nullptr);
+}
 
 int ext4pcf_measure(ext4pcf_ctx* ctx, const double* positions, const double* shears,
                     const double* weights, int64_t n_gal, const double* radial_bins, int n_bins,
                     int n_max, const int64_t* cat_offsets, int n_cat, const uint8_t* centre_mask,
                     double* upsilon, double* xi_acc, ext4pcf_stats* stats) {
-  return ext4pcf_measure_batch(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, cat_offsets,
-                               n_cat, nullptr, 0, centre_mask, upsilon, xi_acc, stats);
+  return measure_impl(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, cat_offsets, n_cat,
+                      nullptr, 0, centre_mask, upsilon, xi_acc, stats, nullptr, 0, nullptr);
+}
+
+int ext4pcf_multipoles(ext4pcf_ctx* ctx, const double* positions, const double* shears, const double* weights,
+                       int64_t n_gal, const double* radial_bins, int n_bins, int n_max, const int64_t* centres,
+                       int64_t n_centres, double* records) {
+  if (!records) return fail(ctx, EXT4PCF_E_INVALID_ARG, "null records");
+  return measure_impl(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, nullptr, 1, nullptr, 0,
+                      nullptr, nullptr, nullptr, nullptr, centres, n_centres, records);
 }
 
 int ext4pcf_to_real_space(ext4pcf_ctx* ctx, const double* upsilon, int n_bins, int n_max, int n_phi,
@@ -836,8 +1053,8 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
     P.nseg = 1;
     P.total = Tw;
     P.seg[0] = WaveSeg{(const int*)ctx->centres.p, nullptr, (const GridGeom*)ctx->geom.p, (const int*)ctx->cell_start.p,
-                       w0, Tw, 0, 0};
-    CK(gather_wave<double>(cat, bins, L, P, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+                       w0, Tw, 0, 0, 0};
+    CK(gather_wave<double>(cat, cat, bins, L, P, false, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                            (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
     CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3, s));
   }

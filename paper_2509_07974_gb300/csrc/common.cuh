@@ -127,6 +127,7 @@ struct WaveSeg {
   int t;                  // centres of the segment at most
   int off;                // first record of the segment in the wave
   int slot;               // output slot the segment accumulates into
+  int cat;                // catalogue index
 };
 struct WavePlan {
   int nseg;
@@ -178,16 +179,28 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
 cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n, int c0,
                              const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
                              GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s);
+// Reduced catalogue of the tree approximation (Sect. 3.4, App. F.3): the galaxies of every
+// non-empty cell of side delta, anchored at the lower corner of the bounding box d_bbox
+// (grid_bbox), replaced by one galaxy at their weighted centre of mass carrying the summed w and
+// w gamma.  Writes rpos [m][2], rshear [m][2] (summed w gamma / summed w, so that w * shear is
+// the summed w gamma), rw [m] in cell order, and m to *count (device); head: n + 1 unsigned of
+// scratch; a grid of more than kMaxCellsPerAxis cells per axis sets bit 4 of *status
+cudaError_t reduce_catalogue(const double* pos, const double* shear, const double* wts, int n, const double* d_bbox,
+                             double delta, GridGeom* d_geom, GridBuffers& gb, unsigned* head, double* rpos,
+                             double* rshear, double* rw, int* count, int* status, cudaStream_t s);
 // entries of a cell list of the measure path for n galaxies (the device grid keeps at most
 // ~4n cells)
 inline size_t grid_cells_cap(int64_t n) { return (size_t)(4 * n + 2); }
 
 // gather.cu: per-centre multipole records of a wave (records of padding centres are left
-// untouched); cat holds the concatenated sorted arrays (its grid fields unused)
+// untouched).  cat: the neighbours' concatenated sorted arrays, whose grids the plan's segments
+// give; cen: the arrays the centre lists index (the same, or the galaxies when the neighbours
+// are a reduced catalogue); bins: the pass's bins (bins outside its range have zero width);
+// accumulate: add into the records instead of writing them (and the centres' x, w)
 template <typename R>
-cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L, const WavePlan& plan,
-                        cplx_t<R>* rec, cplx_t<R>* xw, unsigned long long* pair_count, int sm_count,
-                        cudaStream_t s);
+cudaError_t gather_wave(const SortedCat& cat, const SortedCat& cen, const Bins& bins, const Layout& L,
+                        const WavePlan& plan, bool accumulate, cplx_t<R>* rec, cplx_t<R>* xw,
+                        unsigned long long* pair_count, int sm_count, cudaStream_t s);
 
 // contract.cu
 template <typename R>

@@ -489,10 +489,14 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&ab_full[slot]);
       };
-      // the wave's segments in order; each one's sums go to its slot
-      for (int si = 0; si < args.plan.nseg; ++si) {
-      const WaveSeg& sgm = args.plan.seg[si];
-      const int nstage = (seg_live(sgm) + kHCentres - 1) / kHCentres;
+      // the wave's segments in order, runs of consecutive segments with the same output slot
+      // accumulated together (the patches of one survey form one run): one pipeline drain and
+      // one epilogue per run
+      for (int si = 0; si < args.plan.nseg;) {
+      const int slot = args.plan.seg[si].slot;
+      int nstage = 0;
+      for (; si < args.plan.nseg && args.plan.seg[si].slot == slot; ++si)
+        nstage += (seg_live(args.plan.seg[si]) + kHCentres - 1) / kHCentres;
 #pragma unroll
       for (int j = 0; j < 16; ++j) accD[j] = 0.f;
       int prev_slot = 0;
@@ -558,7 +562,7 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
       }
       gs += nstage;
       // ---------------------------------------------------------------- epilogue
-      if (row_ok && has_cols && nstage > 0) {  // (an empty segment adds nothing)
+      if (row_ok && has_cols && nstage > 0) {  // (an empty run adds nothing)
         const int pr = rr % npairs, nx = 2 * N + 3;
         const int kx = h_scale_exp(args.rowmax[g.bx.row0 + (eB - g.sx)]);
         const int kc = h_scale_exp(args.rowmax[g.bc.row0 + (eC - g.sc)]);
@@ -572,13 +576,13 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
                                 : g.ba0.row0 + hblk_index(g.ba0, kr.A[0], g.s, b1, nb);
             const double unscale = h_pow2d(-(kx + kc + h_scale_exp(args.rowmax[arow])));
             const size_t o = ((((size_t)mu * nx + (n2 + N + 1)) * nx + (n3 + N + 1)) * nb + b1) * npairs + pr;
-            double* p = args.red + (size_t)sgm.slot * args.red_stride + 2 * o;
+            double* p = args.red + (size_t)slot * args.red_stride + 2 * o;
             p[0] += (double)accD[j] * unscale;
             p[1] += (double)accD[j + 1] * unscale;
           }
         }
       }
-      }  // segments
+      }  // runs of segments
     }
   } else if (warp == kHWarpMma) {
     // ---------------------------------------------------------------------- MMA issuer

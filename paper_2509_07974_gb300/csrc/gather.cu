@@ -318,9 +318,16 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
       cell_w = cell;
     }
     const int pi = sg.centres[sg.w0 + j];
-    const double pxi = cat.px[pi], pyi = cat.py[pi];
+    const double pxi = args.cen.px[pi], pyi = args.cen.py[pi];
+    // the centre in the neighbours' grid frame: cell corner and offset as float, by the
+    // arithmetic that builds the neighbours' (cell corner, offset) pairs
     float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (sizeof(R) == 4) Pi = cat.p4[pi];
+    if (sizeof(R) == 4) {
+      const int ccx = min(max((int)floor((pxi - gx0) * gm.inv_cell), 0), gncx - 1);
+      const int ccy = min(max((int)floor((pyi - gy0) * gm.inv_cell), 0), gncy - 1);
+      Pi = make_float4((float)ccx * gm.cellf, (float)ccy * gm.cellf, (float)((pxi - gx0) - (double)ccx * cell),
+                       (float)((pyi - gy0) - (double)ccy * cell));
+    }
     if (tid == 0) {
       const double xc = pxi - gx0, yc = pyi - gy0;
       int cy0 = (int)floor((yc - rmax) / cell), cy1 = (int)floor((yc + rmax) / cell);
@@ -515,12 +522,18 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
     }
     // ---- (c) write the record
     Cx* dst = rec + (size_t)c * L.rec;
-    for (int k = tid; k < L.rec; k += kThreads) dst[k] = acc[k];
-    if (tid == 0) {
+    if (args.accumulate) {
+      for (int k = tid; k < L.rec; k += kThreads) dst[k] = cadd(dst[k], acc[k]);
+    } else {
+      for (int k = tid; k < L.rec; k += kThreads) dst[k] = acc[k];
+    }
+    if (tid == 0 && !args.accumulate) {
       R xr, xi, ww;
-      Pair<R>::load_x(cat, pi, xr, xi, ww);
+      Pair<R>::load_x(args.cen, pi, xr, xi, ww);
       xw[2 * (size_t)c] = cmk<Cx>(xr, xi);
       xw[2 * (size_t)c + 1] = cmk<Cx>(ww, R(0));
+    }
+    if (tid == 0) {
       atomicAdd(args.pair_count, pairs_here);
     }
     __syncthreads();
@@ -536,14 +549,15 @@ template <typename R> constexpr int kMinBlocks = sizeof(R) == 4 ? 2 : 1;
 }  // namespace
 
 template <typename R>
-cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L, const WavePlan& plan,
-                        cplx_t<R>* rec, cplx_t<R>* xw, unsigned long long* pair_count, int sm_count,
-                        cudaStream_t s) {
+cudaError_t gather_wave(const SortedCat& cat, const SortedCat& cen, const Bins& bins, const Layout& L,
+                        const WavePlan& plan, bool accumulate, cplx_t<R>* rec, cplx_t<R>* xw,
+                        unsigned long long* pair_count, int sm_count, cudaStream_t s) {
   if (plan.total <= 0) return cudaSuccess;
   constexpr int MB = kMB<R>;
   constexpr int MINB = kMinBlocks<R>;
   GatherArgs a;
-  a.cat = cat; a.bins = bins; a.L = L; a.plan = plan; a.pair_count = pair_count;
+  a.cat = cat; a.cen = cen; a.accumulate = accumulate ? 1 : 0;
+  a.bins = bins; a.L = L; a.plan = plan; a.pair_count = pair_count;
   const int npow = L.max_pow + 1;
   int nblk = (npow + MB - 1) / MB;
   nblk = (nblk + kWarps - 1) / kWarps * kWarps;
@@ -570,9 +584,11 @@ cudaError_t gather_wave(const SortedCat& cat, const Bins& bins, const Layout& L,
   return cudaGetLastError();
 }
 
-template cudaError_t gather_wave<float>(const SortedCat&, const Bins&, const Layout&, const WavePlan&,
-                                        float2*, float2*, unsigned long long*, int, cudaStream_t);
-template cudaError_t gather_wave<double>(const SortedCat&, const Bins&, const Layout&, const WavePlan&,
-                                         double2*, double2*, unsigned long long*, int, cudaStream_t);
+template cudaError_t gather_wave<float>(const SortedCat&, const SortedCat&, const Bins&, const Layout&,
+                                        const WavePlan&, bool, float2*, float2*, unsigned long long*, int,
+                                        cudaStream_t);
+template cudaError_t gather_wave<double>(const SortedCat&, const SortedCat&, const Bins&, const Layout&,
+                                         const WavePlan&, bool, double2*, double2*, unsigned long long*, int,
+                                         cudaStream_t);
 
 }  // namespace ext4pcf

@@ -104,6 +104,9 @@ struct GatherArgs {
   Bins bins;
   Layout L;
   WavePlan plan;       // the wave's segments (centre lists, grids, record offsets)
+  SortedCat cen;       // the galaxies' sorted arrays, where the centres are (cat: the neighbours,
+                       // the galaxies or a reduced catalogue of the tree approximation)
+  int accumulate;      // 0: write the records (and the centres' x, w); 1: add into them
   int cap;
   int mb;    // powers per warp block (<= MB)
   int nblk;  // power blocks

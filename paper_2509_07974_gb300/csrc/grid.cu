@@ -333,6 +333,114 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
   return cudaGetLastError();
 }
 
+namespace {
+// stable LSD radix sort of (gb.keys, gb.perm) by keys below kMaxCellsPerAxis^2 < 2^24 (three
+// 8-bit digits); *keys_out, *perm_out: where the sorted pairs ended up (ping-pong buffers)
+cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_out, cudaStream_t s) {
+  const int ntiles = (n + kTile - 1) / kTile;
+  int* kin = gb.keys; int* kout = gb.keys_alt;
+  int* vin = gb.perm; int* vout = gb.perm_alt;
+  unsigned* hist = gb.hist;
+  unsigned* tmp = gb.hist + (size_t)256 * ntiles;
+  for (int shift = 0; shift < 24; shift += 8) {
+    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
+    cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
+    g_launches += 2;
+    int* t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+  }
+  *keys_out = kin;
+  *perm_out = vin;
+  return cudaGetLastError();
+}
+
+// grid of side delta anchored at the bounding box's lower corner (the tree approximation's
+// resolution); more than kMaxCellsPerAxis cells per axis sets bit 4 of *status
+__global__ void coarse_geom_kernel(const double* __restrict__ bb, double delta, GridGeom* __restrict__ g,
+                                   int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  GridGeom r;
+  const bool finite = isfinite(bb[0]) && isfinite(bb[1]) && isfinite(bb[2]) && isfinite(bb[3]);
+  r.bad = finite ? 0 : 1;
+  r.x0 = finite ? bb[0] : 0.0;
+  r.y0 = finite ? bb[1] : 0.0;
+  const double wx = finite ? bb[2] - bb[0] : 0.0, wy = finite ? bb[3] - bb[1] : 0.0;
+  r.cell = delta;
+  r.inv_cell = 1.0 / delta;
+  r.cellf = (float)delta;
+  const double cx = floor(wx / delta) + 1, cy = floor(wy / delta) + 1;
+  if (cx > kMaxCellsPerAxis || cy > kMaxCellsPerAxis) atomicOr(status, 4);
+  r.ncx = (int)fmin(cx, (double)kMaxCellsPerAxis);
+  r.ncy = (int)fmin(cy, (double)kMaxCellsPerAxis);
+  *g = r;
+}
+
+// 1 at the first position of every run of equal sorted keys
+__global__ void run_heads(const int* __restrict__ keys, int n, unsigned* __restrict__ head) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) head[p] = (p == 0 || keys[p] != keys[p - 1]) ? 1u : 0u;
+}
+
+// one thread per run (cell): the members in sorted order (a fixed summation order), their
+// summed w, w gamma and w theta; the reduced galaxy sits at the weighted centre of mass
+__global__ void reduce_runs(const int* __restrict__ keys, const int* __restrict__ perm,
+                            const unsigned* __restrict__ head_scan, int n, const double* __restrict__ pos,
+                            const double* __restrict__ shear, const double* __restrict__ wts,
+                            double* __restrict__ rpos, double* __restrict__ rshear, double* __restrict__ rw,
+                            int* __restrict__ count) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (p == n - 1) *count = (int)head_scan[p] + ((p == 0 || keys[p] != keys[p - 1]) ? 1 : 0);
+  if (!(p == 0 || keys[p] != keys[p - 1])) return;
+  const int key = keys[p];
+  double W = 0.0, Xr = 0.0, Xi = 0.0, Sx = 0.0, Sy = 0.0;
+  for (int q = p; q < n && keys[q] == key; ++q) {
+    const int i = perm[q];
+    const double w = wts[i];
+    W += w;
+    Xr += w * shear[2 * i];
+    Xi += w * shear[2 * i + 1];
+    Sx += w * pos[2 * i];
+    Sy += w * pos[2 * i + 1];
+  }
+  const unsigned r = head_scan[p];
+  if (W != 0.0) {
+    rpos[2 * r] = Sx / W;
+    rpos[2 * r + 1] = Sy / W;
+    rshear[2 * r] = Xr / W;  // w * shear gives back the summed w gamma
+    rshear[2 * r + 1] = Xi / W;
+  } else {
+    const int i = perm[p];
+    rpos[2 * r] = pos[2 * i];
+    rpos[2 * r + 1] = pos[2 * i + 1];
+    rshear[2 * r] = 0.0;
+    rshear[2 * r + 1] = 0.0;
+  }
+  rw[r] = W;
+}
+}  // namespace
+
+cudaError_t reduce_catalogue(const double* pos, const double* shear, const double* wts, int n, const double* d_bbox,
+                             double delta, GridGeom* d_geom, GridBuffers& gb, unsigned* head, double* rpos,
+                             double* rshear, double* rw, int* count, int* status, cudaStream_t s) {
+  if (n == 0) return cudaMemsetAsync(count, 0, sizeof(int), s);
+  coarse_geom_kernel<<<1, 32, 0, s>>>(d_bbox, delta, d_geom, status);
+  make_keys_dev<<<(n + 255) / 256, 256, 0, s>>>(pos, n, d_geom, gb.keys, gb.perm, status);
+  g_launches += 2;
+  int* keys = nullptr;
+  int* perm = nullptr;
+  cudaError_t e = radix_sort_cells(gb, n, &keys, &perm, s);
+  if (e != cudaSuccess) return e;
+  run_heads<<<(n + 255) / 256, 256, 0, s>>>(keys, n, head);
+  e = scan_exclusive(head, (size_t)n, gb.hist, s);
+  if (e != cudaSuccess) return e;
+  reduce_runs<<<(n + 255) / 256, 256, 0, s>>>(keys, perm, head, n, pos, shear, wts, rpos, rshear, rw, count);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
 cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n, int c0,
                              const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
                              GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s) {
@@ -349,21 +457,10 @@ cudaError_t grid_sort_device(const double* pos, const double* shear, const doubl
   grid_geom_kernel<<<1, 32, 0, s>>>(d_bbox, rmax, n, d_geom);
   make_keys_dev<<<(n + 255) / 256, 256, 0, s>>>(pos, n, d_geom, gb.keys, gb.perm, status);
   g_launches += 2;
-  // keys below kMaxCellsPerAxis^2 < 2^24: three 8-bit digits
-  const int ntiles = (n + kTile - 1) / kTile;
-  int* kin = gb.keys; int* kout = gb.keys_alt;
-  int* vin = gb.perm; int* vout = gb.perm_alt;
-  unsigned* hist = gb.hist;
-  unsigned* tmp = gb.hist + (size_t)256 * ntiles;
-  for (int shift = 0; shift < 24; shift += 8) {
-    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
-    cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
-    if (e != cudaSuccess) return e;
-    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
-    g_launches += 2;
-    int* t = kin; kin = kout; kout = t;
-    t = vin; vin = vout; vout = t;
-  }
+  int* kin = nullptr;
+  int* vin = nullptr;
+  cudaError_t e0 = radix_sort_cells(gb, n, &kin, &vin, s);
+  if (e0 != cudaSuccess) return e0;
   out.perm = vin;
   cell_bounds_dev<<<(n + 1 + 255) / 256, 256, 0, s>>>(kin, n, c0, d_geom, gb.cell_start);
   build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, d_geom, 0, 0.0, 0.0, 1.0, 1.f,

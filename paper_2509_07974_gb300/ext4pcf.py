@@ -30,7 +30,8 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("workspace_bytes", ctypes.c_int64),
                 ("timeout_cycles", ctypes.c_int64), ("deterministic", ctypes.c_int),
-                ("wave_centres", ctypes.c_int)]
+                ("wave_centres", ctypes.c_int), ("tree_delta1", ctypes.c_double), ("tree_levels", ctypes.c_int),
+                ("tree_rmin", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -65,6 +66,7 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_destroy.argtypes = [P]
     lib.ext4pcf_measure.argtypes = [P, P, P, P, I64, P, I, I, P, I, P, P, P, ctypes.POINTER(Stats)]
     lib.ext4pcf_measure_batch.argtypes = [P, P, P, P, I64, P, I, I, P, I, P, I, P, P, P, ctypes.POINTER(Stats)]
+    lib.ext4pcf_multipoles.argtypes = [P, P, P, P, I64, P, I, I, P, I64, P]
     lib.ext4pcf_to_real_space.argtypes = [P, P, I, I, I, P, P]
     lib.ext4pcf_to_map4.argtypes = [P, P, P, I, I, I, P, I, P, P, P, P]
     lib.ext4pcf_to_real_space_noalloc.argtypes = [P, I, I, I, P, P, P]
@@ -81,7 +83,8 @@ def load(path: str = LIB_PATH):
     lib.ext4pcf_synchronize.restype = I
     lib.ext4pcf_last_error.argtypes = [P]
     lib.ext4pcf_last_error.restype = ctypes.c_char_p
-    for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_measure_batch", "ext4pcf_to_real_space",
+    for f in ("ext4pcf_create", "ext4pcf_destroy", "ext4pcf_measure", "ext4pcf_measure_batch", "ext4pcf_multipoles",
+              "ext4pcf_to_real_space",
               "ext4pcf_to_map4", "ext4pcf_map_direct"):
         getattr(lib, f).restype = I
     _lib = lib
@@ -153,6 +156,28 @@ def ext4pcf_measure_batch(ctx, positions, shears, weights, n_gal, radial_bins, n
                                    _addr(upsilon), _addr(xi_acc),
                                    ctypes.byref(stats) if stats is not None else None)
     return _check(ctx, rc)
+
+
+def ext4pcf_multipoles(ctx, positions, shears, weights, n_gal, radial_bins, n_bins, n_max, centres,
+                       n_centres, records) -> int:
+    rc = load().ext4pcf_multipoles(ctx, _addr(positions), _addr(shears), _addr(weights), int(n_gal),
+                                   _addr(radial_bins), int(n_bins), int(n_max), _addr(centres), int(n_centres),
+                                   _addr(records))
+    return _check(ctx, rc)
+
+
+def record_layout(n_bins, n_max):
+    """Offsets (complex elements) of the arrays of an ext4pcf_multipoles record:
+    {'G': (offset, first n, count), 'W': ..., 'XX', 'XA', 'WW', 'TR'}, each [count][n_bins]."""
+    N, nb = n_max, n_bins
+    parts = [("G", -2 * N - 3, 4 * N + 3), ("W", 0, 2 * N + 1), ("XX", -2 * N - 6, 4 * N + 5),
+             ("XA", 0, 2 * N + 3), ("WW", 0, 2 * N + 1), ("TR", 0, 5)]
+    out, off = {}, 0
+    for name, first, cnt in parts:
+        out[name] = (off, first, cnt)
+        off += cnt * nb
+    out["rec"] = off
+    return out
 
 
 def ext4pcf_to_real_space(ctx, upsilon, n_bins, n_max, n_phi, gamma, norm) -> int:

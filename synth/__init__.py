@@ -233,14 +233,21 @@ def batch64_workload(scale: float = 1.0, n_mocks: int | None = None):
     return pos, sh, w, offs, log_edges(c["lo"], c["hi"], c["nb"]), c["nmax"]
 
 
-def survey_workload(n: int | None = None, side: float | None = None, grid: int | None = None):
+def survey_workload(n: int | None = None, side: float | None = None, grid: int | None = None,
+                    n_side: int | None = None):
     """The survey catalogue and its patches: (pos, shear, w) of the patched catalogue (galaxies
-    in patch order, margins repeated), catalogue offsets, the core mask, edges, n_max."""
+    in patch order, margins repeated), catalogue offsets, the core mask, edges, n_max.  A
+    smaller n keeps the density (side scaled) and, unless n_side is given, patches of about
+    the survey's size (at least 2 x 2, each wider than the margin)."""
     c = SURVEY
     n = n or c["n"]
-    side = side or c["side"]
+    side = side or c["side"] * (n / c["n"]) ** 0.5
+    if n_side is None:
+        n_side = max(2, min(c["n_side"], int(side / (c["side"] / c["n_side"]) + 0.5)))
+        while side / n_side <= c["margin"] and n_side > 1:
+            n_side -= 1
     pos, sh, w = lognormal_catalog(n, side, c["seed"], grid=grid or c["grid"])
-    idx, offs, mask = flat_patches(pos, side, c["n_side"], c["margin"])
+    idx, offs, mask = flat_patches(pos, side, n_side, c["margin"])
     return pos[idx], sh[idx], w[idx], offs, mask, log_edges(c["lo"], c["hi"], c["nb"]), c["nmax"]
 
 

@@ -45,8 +45,8 @@ def test_binding_names_match_the_abi():
 
 def test_struct_layouts_match_header():
     from paper_2509_07974_gb300 import ext4pcf
-    # int, void*, int, int, int64, int64, int, int  (x86-64 / aarch64 LP64 alignment)
-    assert ctypes.sizeof(ext4pcf.Config) == 48
+    # int, void*, int, int, int64, int64, int, int, double, int, double  (LP64 alignment)
+    assert ctypes.sizeof(ext4pcf.Config) == 72
     assert ctypes.sizeof(ext4pcf.Stats) == 10 * 8
 
 
