@@ -371,6 +371,39 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
       // ---- pass 3: accumulate the power blocks
       for (int k = warp; k < args.nblk; k += kWarps) {
         const int m0 = k * mb;
+        // where this lane's reduced slots go, as the float index at bin 0 (every array of the
+        // record is [multipole][bin]: the index at bin b is that plus 2b): >= 0 a record entry,
+        // <= -2 triple-term slot (-2 - q) of trs, -1 nothing
+        int fidx[V / 32];
+        {
+          const int base = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
+                           (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
+#pragma unroll
+          for (int j = 0; j < V / 32; ++j) {
+            const int slot = base + j;
+            int idx = -1;
+            if (slot < 14 * MB) {
+              const int t = slot / 14, q = slot % 14, m = m0 + t;
+              if (t < mb) {
+                switch (q >> 1) {
+                  case 0: if (m <= 2 * L.N - 1) idx = L.G(m, 0); break;
+                  case 1: if (m >= 1 && m <= 2 * L.N + 3) idx = L.G(-m, 0); break;
+                  case 2: if (m <= 2 * L.N - 2) idx = L.XX(m, 0); break;
+                  case 3: if (m >= 1 && m <= 2 * L.N + 6) idx = L.XX(-m, 0); break;
+                  case 4: if (m <= 2 * L.N) idx = L.W(m, 0); break;
+                  case 5: if (m <= 2 * L.N + 2) idx = L.XA(m, 0); break;
+                  default: if (m <= 2 * L.N) idx = L.WW(m, 0); break;
+                }
+              }
+              fidx[j] = idx >= 0 ? 2 * idx + (slot & 1) : -1;
+            } else if (slot < 14 * MB + 10) {
+              if (kTrSplit) fidx[j] = -2 - (slot - 14 * MB);
+              else fidx[j] = m0 == 0 ? 2 * L.TR((slot - 14 * MB) >> 1, 0) + (slot & 1) : -1;
+            } else {
+              fidx[j] = -1;
+            }
+          }
+        }
         for (int b = 0; b < nb; ++b) {
           const int s0 = off[b], s1 = off[b + 1];
           if (s0 == s1) continue;
@@ -476,31 +509,12 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
             }
           }
           reduce_transpose<R, V>(a, lane);
-          const int base = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
-                           (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
           R* accr = reinterpret_cast<R*>(acc);
 #pragma unroll
           for (int j = 0; j < V / 32; ++j) {
-            const int slot = base + j;
-            int idx = -1, comp = slot & 1;
-            if (slot < 14 * MB) {
-              const int t = slot / 14, q = slot % 14, m = m0 + t;
-              if (t < mb) {
-                switch (q >> 1) {
-                  case 0: if (m <= 2 * L.N - 1) idx = L.G(m, b); break;
-                  case 1: if (m >= 1 && m <= 2 * L.N + 3) idx = L.G(-m, b); break;
-                  case 2: if (m <= 2 * L.N - 2) idx = L.XX(m, b); break;
-                  case 3: if (m >= 1 && m <= 2 * L.N + 6) idx = L.XX(-m, b); break;
-                  case 4: if (m <= 2 * L.N) idx = L.W(m, b); break;
-                  case 5: if (m <= 2 * L.N + 2) idx = L.XA(m, b); break;
-                  default: if (m <= 2 * L.N) idx = L.WW(m, b); break;
-                }
-              }
-            } else if (slot < 14 * MB + 10) {
-              if (kTrSplit) trs[(b * args.nblk + k) * 10 + (slot - 14 * MB)] = a[j];
-              else if (m0 == 0) idx = L.TR((slot - 14 * MB) >> 1, b);
-            }
-            if (idx >= 0) accr[2 * idx + comp] += a[j];
+            const int f = fidx[j];
+            if (f >= 0) accr[f + 2 * b] += a[j];
+            else if (kTrSplit && f <= -2) trs[(b * args.nblk + k) * 10 + (-2 - f)] = a[j];
           }
         }
       }
