@@ -5,18 +5,22 @@
 //
 // One CTA (8 warps) per centre:
 //   (a) the rows of cells that can hold partners are contiguous ranges of the cell-sorted
-//       catalogue; the CTA streams them, keeps pairs with Theta_lo^2 <= r^2 < Theta_hi^2,
-//       and buckets them by radial bin into a shared-memory chunk (stable order, so the
-//       summation order is deterministic).  Chunks hold up to `cap` pairs; long neighbour
-//       lists take several chunks.
-//   (b) warp k owns the powers m in [k*MB, k*MB+MB) of u = e^{i phi_ij}: each lane takes
-//       two pairs of a bin at a time, raises u to the block's first power (u^MB is stored
-//       per pair) and walks the block by recurrence in registers, accumulating seven real
-//       weights times u^m: Re x, Im x, Re x^2, Im x^2, w, |x|^2, w^2 (two FMAs each).  The
-//       complex sums x u^{+-m} and x^2 u^{+-m} follow from the first four at the end of the
-//       bin.  The 32 lanes' partial sums are then combined by a transposed butterfly (each
-//       lane ends with V/32 totals) and added to the centre's record in shared memory.
-//   (c) the record is written to the wave buffer.
+//       catalogue (found by one warp, a row per lane); the CTA streams them, keeps pairs
+//       with Theta_lo^2 <= r^2 < Theta_hi^2, and buckets them by radial bin into a
+//       shared-memory chunk (stable order, so the summation order is deterministic).  Chunks
+//       hold up to `cap` candidates; long neighbour lists take several chunks.
+//   (b) the work of a chunk is split into items (bin, power block): block k holds the powers
+//       m in [k*mb, k*mb+mb) of u = e^{i phi_ij}.  The warps take the items in turn, outer
+//       bins first.  For an item each lane walks pairs of the bin, raises u to the block's
+//       first power (u^mb is stored per pair) and steps through the block by recurrence in
+//       registers, accumulating seven real weights times u^m: Re x, Im x, Re x^2, Im x^2, w,
+//       |x|^2, w^2.  The complex sums x u^{+-m} and x^2 u^{+-m} follow from the first four.
+//       The 32 lanes' partial sums are combined by a transposed butterfly (each lane ends
+//       with V/32 totals) and added to the centre's record in shared memory; no two items
+//       of a chunk share a record entry.
+//   (c) the triple terms, split over the power blocks in FP32, are summed in block order,
+//       and the record is written to the wave buffer (or added to it, for the later passes
+//       of the tree approximation).
 // FP64 variant: positions and arithmetic in double; the bin decision r^2 = dx*dx + dy*dy is
 // evaluated with two rounded products and one rounded sum, as the FP64 definition reads.
 // FP32 variant: positions are cell-anchored floats (cell offset exact, in-cell offset
@@ -269,32 +273,77 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   extern __shared__ __align__(16) unsigned char smem[];
   const SortedCat& cat = args.cat;
   const Layout L = args.L;
-  const int nb = args.bins.nb, cap = args.cap, mb = args.mb;
+  const int nb = args.bins.nb, cap = args.cap, mb = args.mb, nblk = args.nblk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   using V4 = typename Vec4<R>::T;
   V4* euv = reinterpret_cast<V4*>(smem);
   Cx* ex = reinterpret_cast<Cx*>(euv + cap);
   R* ew = reinterpret_cast<R*>(ex + cap);
-  Cx* acc = reinterpret_cast<Cx*>(ew + cap);
-  double* e2 = reinterpret_cast<double*>(acc + L.rec);
+  double* e2 = reinterpret_cast<double*>(ew + cap);
   float* e2f = reinterpret_cast<float*>(e2 + 65);
   float* win = e2f + 65;
   int* off = reinterpret_cast<int*>(win + 65);  // [65] bin offsets of the chunk
   int* wcnt = off + 65;                          // [warps][64] per-warp bin counts / positions
   int* rstart = wcnt + kWarps * 64;
   int* rpre = rstart + kMaxRows;
-  int* misc = rpre + kMaxRows + 1;
+  int* misc = rpre + kMaxRows + 1;  // rows, candidates, work items taken
+  int* fidx = misc + 8;             // [nblk][V] where the reduced slots of each power block go
   // FP32 with 6-power blocks: the triple terms are split over the power blocks, whose
-  // partial sums wait in trs [nb][nblk][10] until the end of the chunk
+  // partial sums collect in trs [nb][nblk][10] until the end of the centre
   constexpr bool kTrSplit = sizeof(R) == 4 && MB >= 6;
-  R* trs = reinterpret_cast<R*>(misc + 8);
-  signed char* cbin = reinterpret_cast<signed char*>(trs + (kTrSplit ? nb * args.nblk * 10 : 0));  // bin of each candidate
+  R* trs = reinterpret_cast<R*>(fidx + nblk * V);
+  unsigned char* btab = reinterpret_cast<unsigned char*>(trs + (kTrSplit ? nb * nblk * 10 : 0));  // [256]
+  signed char* cbin = reinterpret_cast<signed char*>(btab + 256);  // bin of each candidate
+  Cx* accs = reinterpret_cast<Cx*>((reinterpret_cast<uintptr_t>(cbin + cap) + 15) & ~(uintptr_t)15);
 
   for (int b = tid; b <= nb; b += kThreads) {
     e2[b] = args.bins.e2[b]; e2f[b] = args.bins.e2f[b];
   }
   for (int k = tid; k < kWarps * 64; k += kThreads) wcnt[k] = 0;
+  // the lookup table of the FP32 bin decision
+  BinLookup lk;
+  lk.tab = btab;
+  lk.base = __float_as_uint(args.bins.e2f[0]);
+  lk.shift = 0;
+  while (((__float_as_uint(args.bins.e2f[nb]) - lk.base) >> lk.shift) >= 256u) ++lk.shift;
+  lk.out_lo = lk.out_hi = 0.f;  // set per chunk from the rounding windows
+  for (int i = tid; i < 256; i += kThreads) {
+    const float v = __uint_as_float(lk.base + ((unsigned)i << lk.shift));
+    int b = 0;
+    while (b + 1 < nb && args.bins.e2f[b + 1] <= v) ++b;
+    btab[i] = (unsigned char)b;
+  }
+  // Reduced slot s of power block k (slot order of the accumulation: 14 per power, then the
+  // 10 triple terms) goes to the record's float index fidx[k][s] + 2b for bin b (every array
+  // of the record is [multipole][bin]); <= -2: triple-term slot -2 - fidx of trs; -1: nowhere
+  for (int i = tid; i < nblk * V; i += kThreads) {
+    const int k = i / V, slot = i % V, m0 = k * mb;
+    int f = -1;
+    if (slot < 14 * MB) {
+      const int t = slot / 14, q = slot % 14, m = m0 + t;
+      int idx = -1;
+      if (t < mb) {
+        switch (q >> 1) {
+          case 0: if (m <= 2 * L.N - 1) idx = L.G(m, 0); break;
+          case 1: if (m >= 1 && m <= 2 * L.N + 3) idx = L.G(-m, 0); break;
+          case 2: if (m <= 2 * L.N - 2) idx = L.XX(m, 0); break;
+          case 3: if (m >= 1 && m <= 2 * L.N + 6) idx = L.XX(-m, 0); break;
+          case 4: if (m <= 2 * L.N) idx = L.W(m, 0); break;
+          case 5: if (m <= 2 * L.N + 2) idx = L.XA(m, 0); break;
+          default: if (m <= 2 * L.N) idx = L.WW(m, 0); break;
+        }
+      }
+      f = idx >= 0 ? 2 * idx + (slot & 1) : -1;
+    } else if (slot < 14 * MB + 10) {
+      if (kTrSplit) f = -2 - (slot - 14 * MB);
+      else f = m0 == 0 ? 2 * L.TR((slot - 14 * MB) >> 1, 0) + (slot & 1) : -1;
+    }
+    fidx[i] = f;
+  }
+  // the reduced slots this lane holds after the transposed butterfly: base + [0, V/32)
+  const int rbase = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
+                    (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
   const double rmax = args.bins.rmax * (1.0 + 1e-9) + 1e-12;
   double cell_w = -1.0;  // cell side the rounding windows were computed for
 
@@ -328,28 +377,56 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
       Pi = make_float4((float)ccx * gm.cellf, (float)ccy * gm.cellf, (float)((pxi - gx0) - (double)ccx * cell),
                        (float)((pyi - gy0) - (double)ccy * cell));
     }
-    if (tid == 0) {
+    if (warp == 0) {
+      // the rows of cells within rmax of the centre, one per lane (cells are at least rmax / 8
+      // wide, so there are at most 18), kept in row order when they hold galaxies
       const double xc = pxi - gx0, yc = pyi - gy0;
-      int cy0 = (int)floor((yc - rmax) / cell), cy1 = (int)floor((yc + rmax) / cell);
-      cy0 = max(cy0, 0); cy1 = min(cy1, gncy - 1);
+      const int cy0 = max((int)floor((yc - rmax) / cell), 0);
+      const int cy1 = min((int)floor((yc + rmax) / cell), gncy - 1);
       int nr = 0, tot = 0;
-      for (int cy = cy0; cy <= cy1 && nr < kMaxRows; ++cy) {
-        const double lo = cy * cell, hi = lo + cell;
-        const double gap = fmax(0.0, fmax(lo - yc, yc - hi));
-        if (gap > rmax) continue;
-        const double hw = sqrt(fmax(0.0, rmax * rmax - gap * gap));
-        int cx0 = (int)floor((xc - hw) / cell), cx1 = (int)floor((xc + hw) / cell);
-        cx0 = max(cx0, 0); cx1 = min(cx1, gncx - 1);
-        if (cx0 > cx1) continue;
-        const int a = sg.cell_start[cy * gncx + cx0];
-        const int b = sg.cell_start[cy * gncx + cx1 + 1];
-        if (b <= a) continue;
-        rstart[nr] = a; rpre[nr] = tot; tot += b - a; ++nr;
+      for (int cyb = cy0; cyb <= cy1; cyb += 32) {
+        const int cy = cyb + lane;
+        int a = 0, len = 0;
+        if (cy <= cy1) {
+          const double lo = cy * cell, hi = lo + cell;
+          const double gap = fmax(0.0, fmax(lo - yc, yc - hi));
+          if (gap <= rmax) {
+            const double hw = sqrt(fmax(0.0, rmax * rmax - gap * gap));
+            const int cx0 = max((int)floor((xc - hw) / cell), 0);
+            const int cx1 = min((int)floor((xc + hw) / cell), gncx - 1);
+            if (cx0 <= cx1) {
+              a = sg.cell_start[cy * gncx + cx0];
+              len = max(sg.cell_start[cy * gncx + cx1 + 1] - a, 0);
+            }
+          }
+        }
+        const unsigned ok = __ballot_sync(kFull, len > 0);
+        const int pos = nr + __popc(ok & ((1u << lane) - 1u));
+        const bool keep = len > 0 && pos < kMaxRows;
+        int inc = keep ? len : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(kFull, inc, o);
+          if (lane >= o) inc += v;
+        }
+        if (keep) {
+          rstart[pos] = a;
+          rpre[pos] = tot + inc - len;
+        }
+        nr = min(nr + __popc(ok), kMaxRows);
+        tot += __shfl_sync(kFull, inc, 31);
       }
-      rpre[nr] = tot;
-      misc[0] = nr; misc[1] = tot;
+      if (lane == 0) {
+        rpre[nr] = tot;
+        misc[0] = nr; misc[1] = tot;
+      }
     }
-    for (int k = tid; k < L.rec; k += kThreads) acc[k] = cmk<Cx>(R(0), R(0));
+    // the record collects in shared memory
+    Cx* dst = rec + (size_t)c * L.rec;
+    R* accf = reinterpret_cast<R*>(accs);
+    for (int k = tid; k < L.rec; k += kThreads) accs[k] = cmk<Cx>(R(0), R(0));
+    if (kTrSplit)
+      for (int i = tid; i < nb * nblk * 10; i += kThreads) trs[i] = R(0);
     __syncthreads();
     const int nr = misc[0], total = misc[1];
     unsigned long long pairs_here = 0;
@@ -357,56 +434,32 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
     for (int cpos = 0; cpos < total;) {
       // ---- classification and stable bucketing by bin of the next cap candidates
       const int cend = min(total, cpos + cap);
-      bucket_chunk<R, kWarps>(cat, rstart, rpre, nr, cpos, cend, pxi, pyi, Pi, e2, e2f, win, nb, cbin, wcnt, off,
+      if (tid == 0) misc[2] = 0;  // work items of this chunk taken so far (read after the barriers below)
+      bucket_chunk<R, kWarps>(cat, rstart, rpre, nr, cpos, cend, pxi, pyi, Pi, e2, e2f, win, lk, nb, cbin, wcnt, off,
                               [&](int dst, R ur, R ui, int q) {
                                 R xr, xi, ww, vr, vi;
                                 Pair<R>::load_x(cat, q, xr, xi, ww);
-                                cpow<R>(ur, ui, mb, vr, vi);
+                                cpow5<R>(ur, ui, mb, vr, vi);
                                 V4 e;
                                 e.x = ur; e.y = ui; e.z = vr; e.w = vi;
                                 euv[dst] = e;
                                 ex[dst] = cmk<Cx>(xr, xi);
                                 ew[dst] = ww;
                               });
-      // ---- pass 3: accumulate the power blocks
-      for (int k = warp; k < args.nblk; k += kWarps) {
-        const int m0 = k * mb;
-        // where this lane's reduced slots go, as the float index at bin 0 (every array of the
-        // record is [multipole][bin]: the index at bin b is that plus 2b): >= 0 a record entry,
-        // <= -2 triple-term slot (-2 - q) of trs, -1 nothing
-        int fidx[V / 32];
-        {
-          const int base = (lane & 16 ? V / 2 : 0) + (lane & 8 ? V / 4 : 0) + (lane & 4 ? V / 8 : 0) +
-                           (lane & 2 ? V / 16 : 0) + (lane & 1 ? V / 32 : 0);
-#pragma unroll
-          for (int j = 0; j < V / 32; ++j) {
-            const int slot = base + j;
-            int idx = -1;
-            if (slot < 14 * MB) {
-              const int t = slot / 14, q = slot % 14, m = m0 + t;
-              if (t < mb) {
-                switch (q >> 1) {
-                  case 0: if (m <= 2 * L.N - 1) idx = L.G(m, 0); break;
-                  case 1: if (m >= 1 && m <= 2 * L.N + 3) idx = L.G(-m, 0); break;
-                  case 2: if (m <= 2 * L.N - 2) idx = L.XX(m, 0); break;
-                  case 3: if (m >= 1 && m <= 2 * L.N + 6) idx = L.XX(-m, 0); break;
-                  case 4: if (m <= 2 * L.N) idx = L.W(m, 0); break;
-                  case 5: if (m <= 2 * L.N + 2) idx = L.XA(m, 0); break;
-                  default: if (m <= 2 * L.N) idx = L.WW(m, 0); break;
-                }
-              }
-              fidx[j] = idx >= 0 ? 2 * idx + (slot & 1) : -1;
-            } else if (slot < 14 * MB + 10) {
-              if (kTrSplit) fidx[j] = -2 - (slot - 14 * MB);
-              else fidx[j] = m0 == 0 ? 2 * L.TR((slot - 14 * MB) >> 1, 0) + (slot & 1) : -1;
-            } else {
-              fidx[j] = -1;
-            }
-          }
-        }
-        for (int b = 0; b < nb; ++b) {
-          const int s0 = off[b], s1 = off[b + 1];
-          if (s0 == s1) continue;
+      // ---- pass 3: the work items (bin, power block) of the chunk, outer bins (the fuller
+      // ones) first, each taken by the next free warp; an item's sums go straight into the
+      // record, whose entries no other item of the chunk touches
+      const int nitems = nb * nblk;
+      int item = 0;
+      if (lane == 0) item = atomicAdd(&misc[2], 1);
+      item = __shfl_sync(kFull, item, 0);
+      while (item < nitems) {
+        // the warp's next item is requested now and used at the end of this one
+        int next = 0;
+        if (lane == 0) next = atomicAdd(&misc[2], 1);
+        const int b = nb - 1 - item / nblk, k = item % nblk, m0 = k * mb;
+        const int s0 = off[b], s1 = off[b + 1];
+        if (s0 < s1) {
           R a[V];
 #pragma unroll
           for (int j = 0; j < V; ++j) a[j] = R(0);
@@ -495,6 +548,14 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
                                  s1, lane, k, mb, m0 == 0);
           else
             for (int e = s0 + lane; e < s1; e += 64) accumulate(e, e + 32);
+          // the item's record entries (their current values load while the lanes reduce)
+          int f[V / 32];
+          R cur[V / 32];
+#pragma unroll
+          for (int j = 0; j < V / 32; ++j) {
+            f[j] = fidx[k * V + rbase + j];
+            cur[j] = f[j] >= 0 ? accf[f[j] + 2 * b] : R(0);
+          }
           // with R = sum Re(x) u^m = (a0, a1) and I = sum Im(x) u^m = (a2, a3):
           //   sum x u^m = (a0 - a3, a1 + a2),  sum x conj(u^m) = (a0 + a3, a2 - a1)
 #pragma unroll
@@ -509,37 +570,32 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
             }
           }
           reduce_transpose<R, V>(a, lane);
-          R* accr = reinterpret_cast<R*>(acc);
 #pragma unroll
           for (int j = 0; j < V / 32; ++j) {
-            const int f = fidx[j];
-            if (f >= 0) accr[f + 2 * b] += a[j];
-            else if (kTrSplit && f <= -2) trs[(b * args.nblk + k) * 10 + (-2 - f)] = a[j];
+            if (f[j] >= 0) accf[f[j] + 2 * b] = cur[j] + a[j];
+            else if (kTrSplit && f[j] <= -2) trs[(b * nblk + k) * 10 + (-2 - f[j])] += a[j];
           }
         }
-      }
-      __syncthreads();
-      if (kTrSplit) {
-        // triple terms: the power blocks' partial sums, in block order
-        R* accr = reinterpret_cast<R*>(acc);
-        for (int i = tid; i < nb * 10; i += kThreads) {
-          const int b = i / 10, q = i % 10;
-          if (off[b + 1] == off[b]) continue;
-          R sum = R(0);
-          for (int k = 0; k < args.nblk; ++k) sum += trs[(b * args.nblk + k) * 10 + q];
-          accr[2 * L.TR(q >> 1, b) + (q & 1)] += sum;
-        }
+        item = __shfl_sync(kFull, next, 0);
       }
       pairs_here += (unsigned long long)off[nb];
       cpos = cend;
       __syncthreads();
     }
-    // ---- (c) write the record
-    Cx* dst = rec + (size_t)c * L.rec;
+    if (kTrSplit) {
+      // triple terms: the power blocks' sums, in block order
+      for (int i = tid; i < nb * 10; i += kThreads) {
+        const int b = i / 10, q = i % 10;
+        R sum = R(0);
+        for (int k = 0; k < nblk; ++k) sum += trs[(b * nblk + k) * 10 + q];
+        accf[2 * L.TR(q >> 1, b) + (q & 1)] += sum;
+      }
+    }
+    __syncthreads();
     if (args.accumulate) {
-      for (int k = tid; k < L.rec; k += kThreads) dst[k] = cadd(dst[k], acc[k]);
+      for (int k = tid; k < L.rec; k += kThreads) dst[k] = cadd(dst[k], accs[k]);
     } else {
-      for (int k = tid; k < L.rec; k += kThreads) dst[k] = acc[k];
+      for (int k = tid; k < L.rec; k += kThreads) dst[k] = accs[k];
     }
     if (tid == 0 && !args.accumulate) {
       R xr, xi, ww;
@@ -577,9 +633,9 @@ cudaError_t gather_wave(const SortedCat& cat, const SortedCat& cen, const Bins& 
   nblk = (nblk + kWarps - 1) / kWarps * kWarps;
   a.mb = (npow + nblk - 1) / nblk;
   a.nblk = (npow + a.mb - 1) / a.mb;
-  const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 65 * sizeof(double) + 130 * sizeof(float) +
-                       (65 + kWarps * 64 + 2 * kMaxRows + 1 + 8) * sizeof(int) + 64 +
-                       (sizeof(R) == 4 && MB >= 6 ? (size_t)bins.nb * a.nblk * 10 * sizeof(R) : 0);
+  const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 16 + 65 * sizeof(double) + 130 * sizeof(float) +
+                       (65 + kWarps * 64 + 2 * kMaxRows + 1 + 8 + (size_t)a.nblk * GCfg<R, MB>::V) * sizeof(int) + 256 +
+                       64 + (sizeof(R) == 4 && MB >= 6 ? (size_t)bins.nb * a.nblk * 10 * sizeof(R) : 0);
   const size_t budget = MINB == 1 ? 227 * 1024 : 113 * 1024;
   constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R) + 1;
   if (fixed + per_pair * kThreads > budget) return cudaErrorInvalidConfiguration;

@@ -16,14 +16,6 @@ __device__ __forceinline__ int bin_search(const double* e2, int nb, double r2) {
   }
   return lo;
 }
-__device__ __forceinline__ int bin_search_f(const float* e2, int nb, float r2) {
-  int lo = 0, hi = nb;
-  while (hi - lo > 1) {
-    int mid = (lo + hi) >> 1;
-    if (r2 >= e2[mid]) lo = mid; else hi = mid;
-  }
-  return lo;
-}
 
 // Exact FP64 decision, identical to the definition: two rounded products, one rounded sum.
 __device__ __forceinline__ int classify_f64(double dx, double dy, const double* e2, int nb) {
@@ -34,12 +26,24 @@ __device__ __forceinline__ int classify_f64(double dx, double dy, const double* 
 
 struct CentreF64 { double x, y; };
 
+// Bin lookup of the FP32 decision.  The squared edges e2f[0..nb] are floats >= 0, whose bit
+// patterns increase with their values; tab[i] is the bin of the float with bits
+// base + (i << shift) (the largest b < nb with e2f[b] <= it), so for r2 in [e2f[0], e2f[nb])
+// tab[(bits(r2) - base) >> shift] is at most the bin of r2, and a short forward walk over the
+// edges ends at it.
+struct BinLookup {
+  const unsigned char* tab;  // [256], shared memory
+  unsigned base;             // bits of e2f[0]
+  int shift;                 // (bits(e2f[nb]) - base) >> shift < 256
+  float out_lo, out_hi;      // r2 outside [out_lo, out_hi): no bin, whatever the rounding
+};
+
 // Returns the bin of candidate q (or -1) and u = e^{i phi}.
 template <typename R> struct Pair;
 
 template <> struct Pair<double> {
   __device__ static int classify(const SortedCat& cat, int q, double cx, double cy, const float4&,
-                                 const double* e2, const float*, const float*, int nb,
+                                 const double* e2, const float*, const float*, const BinLookup&, int nb,
                                  double& ur, double& ui) {
     double dx = cat.px[q] - cx, dy = cat.py[q] - cy;
     int b = classify_f64(dx, dy, e2, nb);
@@ -63,16 +67,23 @@ template <> struct Pair<double> {
 
 template <> struct Pair<float> {
   __device__ static int classify(const SortedCat& cat, int q, double cx, double cy, const float4& P,
-                                 const double* e2, const float* e2f, const float* win, int nb,
-                                 float& ur, float& ui) {
+                                 const double* e2, const float* e2f, const float* win, const BinLookup& lk,
+                                 int nb, float& ur, float& ui) {
     float4 Q = cat.p4[q];
     float dx = (Q.x - P.x) + (Q.z - P.z);
     float dy = (Q.y - P.y) + (Q.w - P.w);
     float r2 = dx * dx + dy * dy;
     int b;
     // the float decision stands unless r2 is within the edge's rounding window
-    if (r2 < e2f[0] - win[0] || r2 >= e2f[nb] + win[nb]) return -1;
-    b = (r2 >= e2f[0]) ? ((r2 >= e2f[nb]) ? nb : bin_search_f(e2f, nb, r2)) : -1;
+    if (r2 < lk.out_lo || r2 >= lk.out_hi) return -1;
+    if (r2 < e2f[0]) {
+      b = -1;
+    } else if (r2 >= e2f[nb]) {
+      b = nb;
+    } else {
+      b = lk.tab[min((__float_as_uint(r2) - lk.base) >> lk.shift, 255u)];
+      while (b + 1 < nb && r2 >= e2f[b + 1]) ++b;
+    }
     bool near = false;
     if (b < 0) near = true;  // within win[0] of the inner edge
     else if (b == nb) near = true;
@@ -130,8 +141,9 @@ namespace {
 template <typename R, int NW, typename Store>
 __device__ __forceinline__ void bucket_chunk(const SortedCat& cat, const int* rstart, const int* rpre, int nr,
                                              int cpos, int cend, double pxi, double pyi, const float4& Pi,
-                                             const double* e2, const float* e2f, const float* win, int nb,
-                                             signed char* cbin, int* wcnt, int* off, Store store) {
+                                             const double* e2, const float* e2f, const float* win,
+                                             BinLookup lk, int nb, signed char* cbin, int* wcnt, int* off,
+                                             Store store) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned full = 0xFFFFFFFFu, lt = (1u << lane) - 1u;
   const int ncand = cend - cpos;
@@ -149,6 +161,8 @@ __device__ __forceinline__ void bucket_chunk(const SortedCat& cat, const int* rs
   }
   if (lane < nb) wcnt[warp * 64 + lane] = 0;
   __syncwarp();
+  lk.out_lo = e2f[0] - win[0];
+  lk.out_hi = e2f[nb] + win[nb];
   // ---- pass 1: bin of every candidate, counts per (warp, bin)
   int r = r0;
   for (int t0 = w0; t0 < w1; t0 += 32) {
@@ -157,7 +171,7 @@ __device__ __forceinline__ void bucket_chunk(const SortedCat& cat, const int* rs
     if (t < w1) {
       while (r + 1 < nr && t >= rpre[r + 1]) ++r;
       R ur, ui;
-      b = Pair<R>::classify(cat, rstart[r] + (t - rpre[r]), pxi, pyi, Pi, e2, e2f, win, nb, ur, ui);
+      b = Pair<R>::classify(cat, rstart[r] + (t - rpre[r]), pxi, pyi, Pi, e2, e2f, win, lk, nb, ur, ui);
       cbin[t - cpos] = (signed char)b;
     }
     const unsigned peers = __match_any_sync(full, b);
