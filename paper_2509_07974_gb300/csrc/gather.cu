@@ -34,6 +34,9 @@ namespace ext4pcf {
 namespace {
 
 constexpr int kThreads = 256;
+// FP32 (6-power blocks) splits the triple terms over the power blocks: partial sums per
+// (bin, block) in shared memory, added in block order at the end of the centre
+template <typename R, int MB> constexpr bool kTrSplitOf = sizeof(R) == 4 && MB >= 6;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -289,9 +292,8 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
   int* rpre = rstart + kMaxRows;
   int* misc = rpre + kMaxRows + 1;  // rows, candidates, work items taken
   int* fidx = misc + 8;             // [nblk][V] where the reduced slots of each power block go
-  // FP32 with 6-power blocks: the triple terms are split over the power blocks, whose
-  // partial sums collect in trs [nb][nblk][10] until the end of the centre
-  constexpr bool kTrSplit = sizeof(R) == 4 && MB >= 6;
+  // partial sums of the split triple terms: trs [nb][nblk][10]
+  constexpr bool kTrSplit = kTrSplitOf<R, MB>;
   R* trs = reinterpret_cast<R*>(fidx + nblk * V);
   unsigned char* btab = reinterpret_cast<unsigned char*>(trs + (kTrSplit ? nb * nblk * 10 : 0));  // [256]
   signed char* cbin = reinterpret_cast<signed char*>(btab + 256);  // bin of each candidate
@@ -629,13 +631,12 @@ cudaError_t gather_wave(const SortedCat& cat, const SortedCat& cen, const Bins& 
   a.cat = cat; a.cen = cen; a.accumulate = accumulate ? 1 : 0;
   a.bins = bins; a.L = L; a.plan = plan; a.pair_count = pair_count;
   const int npow = L.max_pow + 1;
-  int nblk = (npow + MB - 1) / MB;
-  nblk = (nblk + kWarps - 1) / kWarps * kWarps;
+  const int nblk = (npow + MB - 1) / MB;  // the warps take (bin, block) items in turn
   a.mb = (npow + nblk - 1) / nblk;
   a.nblk = (npow + a.mb - 1) / a.mb;
   const size_t fixed = (size_t)L.rec * sizeof(cplx_t<R>) + 16 + 65 * sizeof(double) + 130 * sizeof(float) +
                        (65 + kWarps * 64 + 2 * kMaxRows + 1 + 8 + (size_t)a.nblk * GCfg<R, MB>::V) * sizeof(int) + 256 +
-                       64 + (sizeof(R) == 4 && MB >= 6 ? (size_t)bins.nb * a.nblk * 10 * sizeof(R) : 0);
+                       64 + (kTrSplitOf<R, MB> ? (size_t)bins.nb * a.nblk * 10 * sizeof(R) : 0);
   const size_t budget = MINB == 1 ? 227 * 1024 : 113 * 1024;
   constexpr size_t per_pair = sizeof(typename Vec4<R>::T) + sizeof(cplx_t<R>) + sizeof(R) + 1;
   if (fixed + per_pair * kThreads > budget) return cudaErrorInvalidConfiguration;
