@@ -269,6 +269,76 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def third_order(dev, stream, flush, args):
+    """The shear 3PCF (order 3 of App. F, ext4pcf_measure3) on a 2e5-galaxy GRF at the density
+    of the main workload (190' x 190'), its 10 log bins 0.5'-40' and n_max = 20, every galaxy a
+    centre: FP32 gather, FP64 contraction.  W warm-up calls, max(K, 3) timed calls with L2
+    flushed between them; pairs per call from one ext4pcf_measure call with statistics on the
+    same catalogue and bins (the same neighbour pairs), outside the timed region."""
+    import torch
+
+    import synth
+    from paper_2509_07974_gb300 import ext4pcf
+    c = synth.GRF2E6
+    n = 200_000
+    side = c["side"] * (n / c["n"]) ** 0.5
+    pos, sh, w = synth.grf_catalog(n, side, c["seed"] + 3, grid=1024)
+    edges = np.ascontiguousarray(synth.log_edges(c["lo"], c["hi"], c["nb"]))
+    nb, nmax = c["nb"], c["nmax"]
+    tp, ts, tw = (torch.tensor(a, device=dev) for a in (pos, sh, w))
+    est = ext4pcf.Estimator(0, "f16x3", stream=stream)
+    ups3 = torch.zeros((5, 2 * nmax + 1, nb, nb, 2), dtype=torch.float64, device=dev)
+    st = ext4pcf.Stats()
+    ups = torch.zeros(ext4pcf.Estimator.ups_shape(nb, nmax), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        ext4pcf.ext4pcf_measure(est.ctx, tp, ts, tw, n, edges, nb, nmax, None, 1, None, ups, None, st)
+    pairs = float(st.as_dict()["pairs"])
+    del ups
+
+    def call(p, s_, w_, out):
+        ext4pcf.ext4pcf_measure3(est.ctx, p, s_, w_, n, edges, nb, nmax, out)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 1)):
+            ups3.zero_()
+            call(tp, ts, tw, ups3)
+        torch.cuda.synchronize()
+        n_t = max(args.steps, 3)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_t)]
+        for k in range(n_t):
+            flush.fill_(float(k))
+            ups3.zero_()
+            evs[k][0].record(stream)
+            call(tp, ts, tw, ups3)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / n_t
+    # end to end through the user's calls: the catalogue from pinned host memory to the device,
+    # the measurement, the multipoles back to the host
+    hp, hs, hw = (torch.tensor(a).pin_memory() for a in (pos, sh, w))
+    host = torch.zeros(ups3.shape, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            dp, ds, dw = (x.to(dev, non_blocking=True) for x in (hp, hs, hw))
+            ups3.zero_()
+            call(dp, ds, dw, ups3)
+            host.copy_(ups3, non_blocking=True)
+        stream.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = sum(e2e_t) / len(e2e_t)
+    est.close()
+    return {"workload": "shear 3PCF: GRF 2e5 gal, %.0f'x%.0f' (the main density), 10 log bins 0.5'-40', n_max=20, "
+                        "every galaxy a centre" % (side, side),
+            "pairs_per_call": pairs, "value": pairs / (ms / 1e3), "unit": "pairs/s", "ms_per_call": ms,
+            "dtype": "f32 gather, f64 contraction", "l2": "flushed between calls (256 MB write)",
+            "e2e": {"value": pairs / e2e, "unit": "pairs/s", "h2d_bytes_per_step": int(3 * n * 8 + n * 8),
+                    "d2h_bytes_per_step": int(host.numel() * 8)},
+            "cpu_baseline": None}
+
+
 def direct_estimator(est, tp, ts, tw, pos, sh, w, side, dev, stream, flush, args, baselines):
     """Direct <M_ap^4> estimator (Sect. 5.2, Eq. MapDirectEstimator) on the same catalogue:
     24 log radii 1'-32', aperture lattices of spacing theta at least 4 theta inside the field,
@@ -441,10 +511,11 @@ def run_ours(args):
     h2d = hp.numel() * 8 + hs.numel() * 8 + hw.numel() * 8 + (hmask.numel() if hmask is not None else 0)
     d2h = m4.nbytes + eb.nbytes + disc.nbytes
 
-    direct = None
+    direct = third = None
     if rank == 0:
         direct = direct_estimator(est, tp, ts, tw, pos, sh, w, c["side"], dev, stream, flush, args,
                                   world == 1 and not args.no_baselines)
+        third = third_order(dev, stream, flush, args)
 
     # rooflines of the two dominant kernels, algorithmic FLOP per launch over the average
     # launch duration in the timed steps.  Gather: FP32 work on the CUDA cores against the
@@ -557,7 +628,7 @@ def run_ours(args):
                 "roofline_secondary": roof_other,
                 "fp64_form": fp64_info,
                 "cpu_baseline": cpu,
-                "next_rows": {"map_direct": direct},
+                "next_rows": {"map_direct": direct, "third_order": third},
                 "clocks": clocks,
                 "gpu_launches": int((bd["launches"] + map4_launches) * args.steps)}
         print(json.dumps(line), flush=True)

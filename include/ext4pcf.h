@@ -299,8 +299,10 @@ EXT4PCF_API int ext4pcf_nth_order_components(int order, int* beta, int cap);
  * Host only.  Returns the size, or EXT4PCF_E_INVALID_ARG. */
 EXT4PCF_API int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap);
 
-/* Multipoles of the shear 3PCF, the order-3 case of the N-th order estimator (paper App. F),
- * FP64.  The neighbour multipoles are gathered as for ext4pcf_measure; the contraction reads
+/* Multipoles of the shear 3PCF, the order-3 case of the N-th order estimator (paper App. F).
+ * The neighbour multipoles are gathered as for ext4pcf_measure, in FP64 when the context's
+ * precision is EXT4PCF_FP64 and in FP32 (cell-anchored positions) for every other precision;
+ * the contraction forms its products and sums in FP64 either way.  It reads
  * the tables of ext4pcf_nth_order_factors(3, mu), and when Theta1 = Theta2 it subtracts the
  * term in which both neighbours are the same galaxy, so that only triplets of distinct
  * galaxies remain:

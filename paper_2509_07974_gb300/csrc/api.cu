@@ -27,7 +27,9 @@ cudaError_t map4_finish_launch(const double* partial, int ntri, int n_ap, const 
 int map_direct_splits(int n_ap, int sm_count, double theta, double cell);
 size_t map_direct_scratch(int n_ap, int nsplit);
 bool contract3_supported(int N);
-cudaError_t contract3_wave(const Layout& L, const double2* rec, const double2* xw, int T, double* ups3,
+size_t contract3_scratch_bytes(const Layout& L, int T);
+template <typename Cx>
+cudaError_t contract3_wave(const Layout& L, const Cx* rec, const Cx* xw, int T, double* ups3, double2* scratch,
                            cudaStream_t s);
 cudaError_t map_direct_radius(const SortedCat& cat, const double* centres, int n_ap, double theta,
                               int nsplit, void* scratch, double* rec, double* mom, cudaStream_t s);
@@ -1028,6 +1030,9 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
   ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
   ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
+  // the gather runs in FP64 for EXT4PCF_FP64 and in FP32 (cell-anchored positions) otherwise
+  const bool f64 = ctx->cfg.precision == EXT4PCF_FP64;
+  if (!f64) { ENSURE(ctx->p4, n * 16); ENSURE(ctx->s4, n * 16); }
   GridBuffers gb;
   gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
   gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
@@ -1035,18 +1040,21 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
   gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
   gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
   gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
-  gb.p4 = nullptr; gb.s4 = nullptr; gb.bbox = (double*)ctx->bbox.p;
+  gb.p4 = f64 ? nullptr : (float4*)ctx->p4.p; gb.s4 = f64 ? nullptr : (float4*)ctx->s4.p;
+  gb.bbox = (double*)ctx->bbox.p;
   SortedCat cat;
   CK(grid_sort_device(positions, shears, weights, nk, 0, (const double*)ctx->bbox.p, bins.rmax,
-                      (GridGeom*)ctx->geom.p, false, gb, cat, (int*)ctx->status.p, s));
+                      (GridGeom*)ctx->geom.p, !f64, gb, cat, (int*)ctx->status.p, s));
   // ---- every galaxy a centre; waves of FP64 records, contracted with the order-3 tables
   ENSURE(ctx->centres, n * 4);
   iota<<<(nk + 255) / 256, 256, 0, s>>>((int*)ctx->centres.p, nk, 0);
   ++g_launches;
   CK(cudaGetLastError());
   const int T = std::min(ctx->cfg.wave_centres > 0 ? ctx->cfg.wave_centres : 4096, nk);
-  ENSURE(ctx->rec, (size_t)T * L.rec * sizeof(double2));
-  ENSURE(ctx->xw, (size_t)T * 2 * sizeof(double2));
+  const size_t cb = f64 ? sizeof(double2) : sizeof(float2);
+  ENSURE(ctx->rec, (size_t)T * L.rec * cb);
+  ENSURE(ctx->xw, (size_t)T * 2 * cb);
+  ENSURE(ctx->corr, contract3_scratch_bytes(L, T));  // partial sums of the centre slices
   for (int w0 = 0; w0 < nk; w0 += T) {
     const int Tw = std::min(T, nk - w0);
     WavePlan P;
@@ -1054,9 +1062,17 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
     P.total = Tw;
     P.seg[0] = WaveSeg{(const int*)ctx->centres.p, nullptr, (const GridGeom*)ctx->geom.p, (const int*)ctx->cell_start.p,
                        w0, Tw, 0, 0, 0};
-    CK(gather_wave<double>(cat, cat, bins, L, P, false, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
-                           (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
-    CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3, s));
+    if (f64) {
+      CK(gather_wave<double>(cat, cat, bins, L, P, false, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+                             (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3,
+                        (double2*)ctx->corr.p, s));
+    } else {
+      CK(gather_wave<float>(cat, cat, bins, L, P, false, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+                            (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
+      CK(contract3_wave(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, upsilon3,
+                        (double2*)ctx->corr.p, s));
+    }
   }
   CK(cudaGetLastError());
   return EXT4PCF_OK;

@@ -4,8 +4,9 @@
 //   Upsilon_{mu,n}(Theta1, Theta2) = sign sum_i t_i [F1(Theta1) F2(Theta2) - delta_{Theta1 Theta2} D],
 // F_l = G_m, conj(G_m) or W_m with m = a n + b, and D the product of the two factors' terms of
 // one and the same neighbour (their sum over the bin is XX, XA or WW of the record), which
-// removes the triplets whose two neighbours coincide.  FP64; one thread per
-// (component, n, Theta1, Theta2), the wave's centres summed in order.
+// removes the triplets whose two neighbours coincide.  Records in FP64 or FP32, products and
+// sums in FP64.  One thread per (component, n, Theta1, Theta2, slice of the wave's centres),
+// each slice's centres summed in order; the slices' partial sums are then added in slice order.
 #include <algorithm>
 #include <cstdlib>
 
@@ -32,37 +33,43 @@ struct Table3 {
 };
 
 __device__ __forceinline__ double2 cj(double2 v) { return make_double2(v.x, -v.y); }
+__device__ __forceinline__ double2 d2(float2 v) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ double2 d2(double2 v) { return v; }
 
-__device__ __forceinline__ double2 factor(const double2* __restrict__ r, const Layout& L, const F3& f, int n,
-                                          int b) {
+template <typename Cx>
+__device__ __forceinline__ double2 factor(const Cx* __restrict__ r, const Layout& L, const F3& f, int n, int b) {
   const int m = f.a * n + f.b;
   double2 v;
-  if (f.arr == 0) v = r[L.G(m, b)];
-  else v = m >= 0 ? r[L.W(m, b)] : cj(r[L.W(-m, b)]);  // W_{-m} = W_m^*
+  if (f.arr == 0) v = d2(r[L.G(m, b)]);
+  else v = m >= 0 ? d2(r[L.W(m, b)]) : cj(d2(r[L.W(-m, b)]));  // W_{-m} = W_m^*
   return f.conj ? cj(v) : v;
 }
 
-__device__ __forceinline__ double2 same_galaxy(const double2* __restrict__ r, const Layout& L, const D3& d,
-                                               int b) {
+template <typename Cx>
+__device__ __forceinline__ double2 same_galaxy(const Cx* __restrict__ r, const Layout& L, const D3& d, int b) {
   double2 v;
-  if (d.arr == 0) v = r[L.XX(d.idx, b)];
-  else if (d.arr == 1) v = d.idx >= 0 ? r[L.XA(d.idx, b)] : cj(r[L.XA(-d.idx, b)]);
-  else v = d.idx >= 0 ? r[L.WW(d.idx, b)] : cj(r[L.WW(-d.idx, b)]);
+  if (d.arr == 0) v = d2(r[L.XX(d.idx, b)]);
+  else if (d.arr == 1) v = d.idx >= 0 ? d2(r[L.XA(d.idx, b)]) : cj(d2(r[L.XA(-d.idx, b)]));
+  else v = d.idx >= 0 ? d2(r[L.WW(d.idx, b)]) : cj(d2(r[L.WW(-d.idx, b)]));
   return d.conj ? cj(v) : v;
 }
 
-__global__ void contract3_kernel(const Layout L, const Table3 tab, const double2* __restrict__ rec,
-                                 const double2* __restrict__ xw, int T, double* __restrict__ ups3) {
+// block = (component and n, slice of the centres); thread = (Theta1, Theta2)
+template <typename Cx>
+__global__ void contract3_kernel(const Layout L, const Table3 tab, const Cx* __restrict__ rec,
+                                 const Cx* __restrict__ xw, int T, int S, double2* __restrict__ part) {
   const int nn = 2 * L.N + 1, nb = L.nb;
-  const int mu = blockIdx.x / nn, n = blockIdx.x % nn - L.N;
+  const int comp = blockIdx.x / S, sl = blockIdx.x % S;
+  const int mu = comp / nn, n = comp % nn - L.N;
   const C3 c = tab.c[mu];
+  const int i0 = (int)((long long)T * sl / S), i1 = (int)((long long)T * (sl + 1) / S);
   for (int p = threadIdx.x; p < nb * nb; p += blockDim.x) {
     const int b1 = p / nb, b2 = p % nb;
     double2 acc = make_double2(0.0, 0.0);
-    for (int i = 0; i < T; ++i) {
-      const double2* r = rec + (size_t)i * L.rec;
-      const double2 x = xw[2 * (size_t)i];
-      const double2 t = c.centre == 2 ? xw[2 * (size_t)i + 1] : (c.centre == 1 ? cj(x) : x);
+    for (int i = i0; i < i1; ++i) {
+      const Cx* r = rec + (size_t)i * L.rec;
+      const double2 x = d2(xw[2 * (size_t)i]);
+      const double2 t = c.centre == 2 ? d2(xw[2 * (size_t)i + 1]) : (c.centre == 1 ? cj(x) : x);
       double2 v = cmul(factor(r, L, c.f[0], n, b1), factor(r, L, c.f[1], n, b2));
       if (b1 == b2) {
         const double2 d = same_galaxy(r, L, c.d, b1);
@@ -71,9 +78,25 @@ __global__ void contract3_kernel(const Layout L, const Table3 tab, const double2
       }
       acc = cadd(acc, cmul(t, v));
     }
-    double* o = ups3 + 2 * (((size_t)mu * nn + (n + L.N)) * nb * nb + p);
-    o[0] += c.sign * acc.x;
-    o[1] += c.sign * acc.y;
+    part[((size_t)sl * 5 * nn + comp) * nb * nb + p] = acc;
+  }
+}
+
+// thread = output entry: the slices' partial sums in slice order, with the component's sign
+__global__ void contract3_sum(const Layout L, const Table3 tab, int S, const double2* __restrict__ part,
+                              double* __restrict__ ups3) {
+  const int nn = 2 * L.N + 1, nb2 = L.nb * L.nb;
+  const size_t total = (size_t)5 * nn * nb2;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < total; o += (size_t)gridDim.x * blockDim.x) {
+    const int mu = (int)(o / ((size_t)nn * nb2));
+    double re = 0.0, im = 0.0;
+    for (int sl = 0; sl < S; ++sl) {
+      const double2 v = part[(size_t)sl * total + o];
+      re += v.x;
+      im += v.y;
+    }
+    ups3[2 * o] += tab.c[mu].sign * re;
+    ups3[2 * o + 1] += tab.c[mu].sign * im;
   }
 }
 
@@ -129,14 +152,26 @@ bool contract3_supported(int N) {
   return build_table3(N, t);
 }
 
-cudaError_t contract3_wave(const Layout& L, const double2* rec, const double2* xw, int T, double* ups3,
+int contract3_slices(int T) { return std::max(1, std::min(32, T / 128)); }
+size_t contract3_scratch_bytes(const Layout& L, int T) {
+  return (size_t)contract3_slices(T) * 5 * (2 * L.N + 1) * L.nb * L.nb * sizeof(double2);
+}
+
+template <typename Cx>
+cudaError_t contract3_wave(const Layout& L, const Cx* rec, const Cx* xw, int T, double* ups3, double2* scratch,
                            cudaStream_t s) {
   Table3 t;
   if (!build_table3(L.N, t)) return cudaErrorInvalidValue;
   if (T <= 0) return cudaSuccess;
-  contract3_kernel<<<5 * (2 * L.N + 1), 128, 0, s>>>(L, t, rec, xw, T, ups3);
-  ++g_launches;
+  const int S = contract3_slices(T);
+  contract3_kernel<Cx><<<5 * (2 * L.N + 1) * S, 128, 0, s>>>(L, t, rec, xw, T, S, scratch);
+  contract3_sum<<<64, 256, 0, s>>>(L, t, S, scratch, ups3);
+  g_launches += 2;
   return cudaGetLastError();
 }
+template cudaError_t contract3_wave<float2>(const Layout&, const float2*, const float2*, int, double*, double2*,
+                                            cudaStream_t);
+template cudaError_t contract3_wave<double2>(const Layout&, const double2*, const double2*, int, double*,
+                                             double2*, cudaStream_t);
 
 }  // namespace ext4pcf

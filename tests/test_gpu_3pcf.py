@@ -44,6 +44,31 @@ def test_third_order_matches_distinct_brute_force(torch_cuda, oracle, nmax, wave
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
 
 
+def test_third_order_fp32_gather_matches_distinct_brute_force(torch_cuda, oracle):
+    """Every precision but FP64 gathers in FP32 (products and sums of the contraction in FP64):
+    the same brute force within the FP32 records' rounding, on 600 galaxies in several waves."""
+    torch = torch_cuda
+    from paper_2509_07974_gb300 import ext4pcf
+    rng = np.random.default_rng(77)
+    n, nmax = 600, 6
+    pos = rng.uniform(0, 14.0, (n, 2))
+    sh = rng.normal(0, 0.3, (n, 2))
+    w = rng.uniform(0.5, 1.5, n)
+    edges = np.array((0.5, 1.0, 1.8, 2.6, 3.5))
+    nb = len(edges) - 1
+    dev = torch.device("cuda:0")
+    tp, ts, tw = (torch.tensor(a, dtype=torch.float64, device=dev) for a in (pos, sh, w))
+    est = ext4pcf.Estimator(0, "f16x3", wave_centres=256)
+    ups = torch.zeros((5, 2 * nmax + 1, nb, nb, 2), dtype=torch.float64, device=dev)
+    ext4pcf.ext4pcf_measure3(est.ctx, tp, ts, tw, n, edges, nb, nmax, ups)
+    torch.cuda.synchronize()
+    got = torch.view_as_complex(ups).cpu().numpy()
+    est.close()
+    ref = oracle.bruteforce_multipoles(3, pos, sh, w, edges, nmax, distinct=True)
+    scale = np.abs(ref).reshape(5, -1).max(axis=1).reshape(5, 1, 1, 1)
+    assert (np.abs(got - ref) <= 2e-5 * scale).all(), (np.abs(got - ref) / scale).max()
+
+
 def test_every_accepted_nmax_has_order3_tables(torch_cuda):
     """The generated order-3 tables stay inside the gathered multipole range for every n_max
     the entry point accepts (0..40): an empty catalogue returns EXT4PCF_OK, not
