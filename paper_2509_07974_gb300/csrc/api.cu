@@ -77,6 +77,23 @@ __global__ void records_out(const ext4pcf::cplx_t<R>* __restrict__ rec, size_t n
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = make_double2((double)rec[i].x, (double)rec[i].y);
 }
+// the centre lists of every catalogue of a set at once: catalogue k's centres at c0[k] on,
+// in sorted order, and their count (flag_scan: exclusive scan of the centre flags)
+__global__ void mask_compact_cats(const unsigned* __restrict__ flag_scan, const uint8_t* __restrict__ mask,
+                                  const int* __restrict__ perm, const CatSet cs, int* __restrict__ centres,
+                                  int* __restrict__ count) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cs.c0[cs.n]) return;
+  int lo = 0, hi = cs.n;  // the catalogue of sorted position p
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p >= cs.c0[mid]) lo = mid; else hi = mid;
+  }
+  const bool f = mask[perm[p]] != 0;
+  const unsigned base = flag_scan[cs.c0[lo]];
+  if (f) centres[cs.c0[lo] + (flag_scan[p] - base)] = (int)p;
+  if (p == cs.c0[lo + 1] - 1) count[lo] = (int)(flag_scan[p] + (f ? 1u : 0u) - base);
+}
 __global__ void iota(int* a, int n, int c0) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < n) a[p] = c0 + p;
@@ -447,22 +464,29 @@ int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears
 
   // ---- grids of all catalogues (device geometry, no host round trip), into the concatenated
   // sorted arrays; centre lists hold concatenated positions
+  // one batched build of every catalogue's grid when they fit one set (kMaxCatSet
+  // catalogues), else one build per catalogue; the two give the same arrays
+  CatSet cset;
+  const bool batched = make_catset(c0v.data(), n_cat, cset);
+  const int64_t nsort = batched ? (int64_t)n : nk_max;  // keys sorted at once
   ENSURE(ctx->ncen, (size_t)(n_cat + 1) * sizeof(int));
-  ENSURE(ctx->bbox, (4 + 4 * 512) * 8);
+  ENSURE(ctx->bbox, batched ? ((size_t)4 * n_cat + 4 * (size_t)cset.tile0[n_cat] + 4) * 8 : (4 + 4 * 512) * 8);
   ENSURE(ctx->geom, (size_t)std::max(n_cat, 1) * sizeof(GridGeom));
   ENSURE(ctx->cell_start, (size_t)std::max<int64_t>(cells_total, 1) * 4);
   if (centre_mask) CK(cudaMemsetAsync(ctx->ncen.p, 0, (size_t)(n_cat + 1) * sizeof(int), s));
   {
-    const int ntiles = (int)((nk_max + 2047) / 2048);
-    ENSURE(ctx->keys, (size_t)nk_max * 4); ENSURE(ctx->keys_alt, (size_t)nk_max * 4);
-    ENSURE(ctx->perm, (size_t)nk_max * 4); ENSURE(ctx->perm_alt, (size_t)nk_max * 4);
+    const size_t ntiles = (size_t)((nsort + 2047) / 2048);
+    ENSURE(ctx->keys, (size_t)nsort * 4); ENSURE(ctx->keys_alt, (size_t)nsort * 4);
+    ENSURE(ctx->perm, (size_t)nsort * 4); ENSURE(ctx->perm_alt, (size_t)nsort * 4);
     ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);
     ENSURE(ctx->px, n * 8); ENSURE(ctx->py, n * 8);
     ENSURE(ctx->xr, n * 8); ENSURE(ctx->xi, n * 8); ENSURE(ctx->w, n * 8);
     if (!f64) { ENSURE(ctx->p4, n * 16); ENSURE(ctx->s4, n * 16); }
     ENSURE(ctx->centres, n * 4);
-    if (centre_mask) ENSURE(ctx->flags, ((size_t)nk_max + (size_t)nk_max / 1000 + 4096) * 4);
+    if (centre_mask || tree) ENSURE(ctx->flags, ((size_t)nsort + (size_t)nsort / 1000 + 4096) * 4);
   }
+  double* cat_bbox = (double*)ctx->bbox.p;        // batched: [n_cat][4], then the tiles' partials
+  double* bbox_part = cat_bbox + 4 * (size_t)n_cat;
   SortedCat cat{};
   cat.n = (int)n;
   cat.px = (const double*)ctx->px.p; cat.py = (const double*)ctx->py.p;
@@ -473,7 +497,46 @@ int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears
   int* clist = (int*)ctx->centres.p;
   int* ncen_d = (int*)ctx->ncen.p;
   if (timing) t_grid0 = tmark();
-  for (int k = 0; k < n_cat; ++k) {
+  if (batched) {
+    GridBuffers gb{};
+    gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+    gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+    gb.cell_start = cells; gb.cell_cap = (size_t)cells_total;
+    gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+    gb.px = (double*)ctx->px.p; gb.py = (double*)ctx->py.p;
+    gb.xr = (double*)ctx->xr.p; gb.xi = (double*)ctx->xi.p; gb.w = (double*)ctx->w.p;
+    gb.p4 = f64 ? nullptr : (float4*)ctx->p4.p; gb.s4 = f64 ? nullptr : (float4*)ctx->s4.p;
+    CK(bbox_batch(d_pos, cset, bbox_part, cat_bbox, s));
+    int* perm = nullptr;
+    CK(grid_sort_batch(d_pos, d_sh, d_w, cset, cat_bbox, bins.rmax, geoms, !f64, gb, &perm, (int*)ctx->status.p, s));
+    const int nn = (int)n;
+    if (nn == 0) {
+      // no galaxies: no centres (the counts were cleared above)
+    } else if (records) {  // one catalogue: the requested galaxies, through the inverse of the sort order
+      ENSURE(ctx->inv, (size_t)nn * 4);
+      ENSURE(ctx->rec_idx, (size_t)std::max<int64_t>(n_rec, 1) * 8);
+      inverse_perm<<<(nn + 255) / 256, 256, 0, s>>>(perm, nn, (int*)ctx->inv.p);
+      if (n_rec > 0) {
+        CK(cudaMemcpyAsync(ctx->rec_idx.p, rec_centres, (size_t)n_rec * 8, cudaMemcpyHostToDevice, s));
+        pick_centres<<<(int)((n_rec + 255) / 256), 256, 0, s>>>((const int64_t*)ctx->rec_idx.p, n_rec,
+                                                               (const int*)ctx->inv.p, clist);
+      }
+      g_launches += 2;
+      CK(cudaGetLastError());
+    } else if (d_mask) {  // every catalogue's centre list and count at once
+      unsigned* flag = (unsigned*)ctx->flags.p;
+      mask_flags<<<(nn + 255) / 256, 256, 0, s>>>(d_mask, perm, nn, flag);
+      CK(scan_exclusive(flag, (size_t)nn, (unsigned*)ctx->hist.p, s));
+      mask_compact_cats<<<(nn + 255) / 256, 256, 0, s>>>(flag, d_mask, perm, cset, clist, ncen_d);
+      g_launches += 2;
+      CK(cudaGetLastError());
+    } else {
+      iota<<<(nn + 255) / 256, 256, 0, s>>>(clist, nn, 0);
+      ++g_launches;
+      CK(cudaGetLastError());
+    }
+  }
+  for (int k = 0; k < n_cat && !batched; ++k) {
     const int64_t c0 = c0v[k];
     const int nk = (int)(c0v[k + 1] - c0);
     if (nk == 0) continue;
@@ -573,9 +636,18 @@ int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears
     for (int d : lev_used) {
       ext4pcf_ctx::Level& V = ctx->lv[d];
       ENSURE(V.rpos, n * 16); ENSURE(V.rsh, n * 16); ENSURE(V.rw, n * 8);
-      ENSURE(V.cnt, (size_t)n_cat * 4); ENSURE(V.geom, (size_t)std::max(n_cat, 1) * sizeof(GridGeom));
+      ENSURE(V.cnt, (size_t)(n_cat + 1) * 4); ENSURE(V.geom, (size_t)std::max(n_cat, 1) * sizeof(GridGeom));
       const double delta = ctx->cfg.tree_delta1 * std::ldexp(1.0, d - 1);
-      for (int k = 0; k < n_cat; ++k) {
+      if (batched) {  // every catalogue at once, concatenated in catalogue order
+        GridBuffers gb{};
+        gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+        gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+        gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+        CK(reduce_batch(d_pos, d_sh, d_w, cset, cat_bbox, delta, (GridGeom*)V.geom.p, gb, (unsigned*)ctx->flags.p,
+                        (double*)V.rpos.p, (double*)V.rsh.p, (double*)V.rw.p, (int*)V.cnt.p, (int*)ctx->status.p,
+                        s));
+      }
+      for (int k = 0; k < n_cat && !batched; ++k) {
         const int64_t c0 = c0v[k];
         const int nk = (int)(c0v[k + 1] - c0);
         GridBuffers gb{};
@@ -607,7 +679,25 @@ int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears
       ENSURE(V.px, nm * 8); ENSURE(V.py, nm * 8); ENSURE(V.xr, nm * 8); ENSURE(V.xi, nm * 8); ENSURE(V.w, nm * 8);
       if (!f64) { ENSURE(V.p4, nm * 16); ENSURE(V.s4, nm * 16); }
       ENSURE(V.cells, (size_t)std::max<int64_t>(P.coff[n_cat], 1) * 4);
-      for (int k = 0; k < n_cat; ++k) {
+      CatSet csr;
+      if (batched && !make_catset(cm.data(), n_cat, csr))  // (fewer galaxies and cells than the set's)
+        return fail(ctx, EXT4PCF_E_UNSUPPORTED, "reduced catalogues beyond one set");
+      if (batched) {  // the reduced catalogues are concatenated
+        GridBuffers gb{};
+        gb.keys = (int*)ctx->keys.p; gb.keys_alt = (int*)ctx->keys_alt.p;
+        gb.perm = (int*)ctx->perm.p; gb.perm_alt = (int*)ctx->perm_alt.p;
+        gb.cell_start = (int*)V.cells.p; gb.cell_cap = (size_t)P.coff[n_cat];
+        gb.hist = (unsigned*)ctx->hist.p; gb.hist_cap = ctx->hist.bytes / 4;
+        gb.px = (double*)V.px.p; gb.py = (double*)V.py.p;
+        gb.xr = (double*)V.xr.p; gb.xi = (double*)V.xi.p; gb.w = (double*)V.w.p;
+        gb.p4 = f64 ? nullptr : (float4*)V.p4.p; gb.s4 = f64 ? nullptr : (float4*)V.s4.p;
+        const double* rp = (const double*)V.rpos.p;
+        CK(bbox_batch(rp, csr, bbox_part, cat_bbox, s));  // the galaxies' boxes are no longer needed
+        int* perm = nullptr;
+        CK(grid_sort_batch(rp, (const double*)V.rsh.p, (const double*)V.rw.p, csr, cat_bbox, P.bins.rmax,
+                           (GridGeom*)V.geom.p, !f64, gb, &perm, (int*)ctx->status.p, s));
+      }
+      for (int k = 0; k < n_cat && !batched; ++k) {
         const int mk = m[d][k];
         if (mk == 0) continue;
         const int64_t c0 = c0v[k];

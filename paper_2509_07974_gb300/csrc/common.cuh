@@ -192,6 +192,37 @@ cudaError_t reduce_catalogue(const double* pos, const double* shear, const doubl
 // ~4n cells)
 inline size_t grid_cells_cap(int64_t n) { return (size_t)(4 * n + 2); }
 
+// Batched grid building: the catalogues of one measurement at once, concatenated.  c0[k] is
+// the first galaxy of catalogue k (in the input and in the sorted arrays), coff[k] its first
+// entry of the concatenated cell lists (grid_cells_cap entries each), tile0[k] its first
+// bounding-box tile; c0[0] = coff[0] = tile0[0] = 0.
+constexpr int kMaxCatSet = 128;
+constexpr int kBBoxTile = 8192;  // galaxies per bounding-box tile
+struct CatSet {
+  int n;
+  int64_t c0[kMaxCatSet + 1];
+  int64_t coff[kMaxCatSet + 1];
+  int tile0[kMaxCatSet + 1];
+};
+// fills cs from the catalogue offsets (host); false if there are too many catalogues or cells
+// for one set (then each catalogue is built on its own)
+bool make_catset(const int64_t* c0, int n_cat, CatSet& cs);
+// bounding boxes of every catalogue into bbox [n][4] (part: 4 doubles per tile of scratch)
+cudaError_t bbox_batch(const double* pos, const CatSet& cs, double* part, double* bbox, cudaStream_t s);
+// every catalogue's grid (the rule of grid_sort_device) and sorted arrays: gb's keys, perm and
+// their alternates hold c0[n] entries, gb.cell_start the concatenated cell lists (coff), the
+// sorted arrays c0[n] galaxies; perm (returned in *perm_out) maps a sorted position to its
+// galaxy, both counted from the first galaxy of the set
+cudaError_t grid_sort_batch(const double* pos, const double* shear, const double* wts, const CatSet& cs,
+                            const double* bbox, double rmax, GridGeom* geoms, bool want_f32, GridBuffers& gb,
+                            int** perm_out, int* status, cudaStream_t s);
+// reduced catalogues (the rule of reduce_catalogue) of every catalogue, concatenated in
+// catalogue order: catalogue k's m[k] reduced galaxies start at sum_{j<k} m[j]; counts[k] = m[k]
+// (device); head: c0[n] + 1 unsigned of scratch
+cudaError_t reduce_batch(const double* pos, const double* shear, const double* wts, const CatSet& cs,
+                         const double* bbox, double delta, GridGeom* geoms, GridBuffers& gb, unsigned* head,
+                         double* rpos, double* rshear, double* rw, int* counts, int* status, cudaStream_t s);
+
 // gather.cu: per-centre multipole records of a wave (records of padding centres are left
 // untouched).  cat: the neighbours' concatenated sorted arrays, whose grids the plan's segments
 // give; cen: the arrays the centre lists index (the same, or the galaxies when the neighbours

@@ -53,8 +53,7 @@ __global__ void bbox_final(const double* __restrict__ part, int np, double* __re
 // cell side: about an eighth of the largest separation, at most ~4000 cells per axis and
 // about sqrt(n) per axis (so that the cells number at most 4n: grid_cells_cap), and with 12
 // significant bits so that (cell index) * cell is exact in float
-__global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, int n, GridGeom* __restrict__ g) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ GridGeom make_geom(const double* __restrict__ bb, double rmax, int n) {
   GridGeom r;
   const bool finite = isfinite(bb[0]) && isfinite(bb[1]) && isfinite(bb[2]) && isfinite(bb[3]);
   r.bad = finite ? 0 : 1;
@@ -78,7 +77,21 @@ __global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, int
   r.cellf = (float)c;
   r.ncx = min((int)floor(wx / c) + 1, kMaxCellsPerAxis);
   r.ncy = min((int)floor(wy / c) + 1, kMaxCellsPerAxis);
-  *g = r;
+  return r;
+}
+
+__global__ void grid_geom_kernel(const double* __restrict__ bb, double rmax, int n, GridGeom* __restrict__ g) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  *g = make_geom(bb, rmax, n);
+}
+
+// the cell of a position in grid G (clamped into the grid)
+__device__ __forceinline__ int cell_key(const GridGeom& G, double x, double y) {
+  int cx = (int)floor((x - G.x0) * G.inv_cell);
+  int cy = (int)floor((y - G.y0) * G.inv_cell);
+  cx = min(max(cx, 0), G.ncx - 1);
+  cy = min(max(cy, 0), G.ncy - 1);
+  return cy * G.ncx + cx;
 }
 
 // a position that is not finite (NaN, which the bounding box's fmin/fmax skip, or +-inf)
@@ -90,11 +103,7 @@ __global__ void make_keys_dev(const double* __restrict__ pos, int n, const GridG
   const GridGeom G = *g;
   const double x = pos[2 * i], y = pos[2 * i + 1];
   if (!isfinite(x) || !isfinite(y)) atomicOr(status, 2);
-  int cx = (int)floor((x - G.x0) * G.inv_cell);
-  int cy = (int)floor((y - G.y0) * G.inv_cell);
-  cx = min(max(cx, 0), G.ncx - 1);
-  cy = min(max(cy, 0), G.ncy - 1);
-  keys[i] = cy * G.ncx + cx;
+  keys[i] = cell_key(G, x, y);
   idx[i] = i;
 }
 
@@ -336,13 +345,14 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
 namespace {
 // stable LSD radix sort of (gb.keys, gb.perm) by keys below kMaxCellsPerAxis^2 < 2^24 (three
 // 8-bit digits); *keys_out, *perm_out: where the sorted pairs ended up (ping-pong buffers)
-cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_out, cudaStream_t s) {
+// keys below 2^bits (bits <= 32), one 8-bit digit per pass
+cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_out, cudaStream_t s, int bits = 24) {
   const int ntiles = (n + kTile - 1) / kTile;
   int* kin = gb.keys; int* kout = gb.keys_alt;
   int* vin = gb.perm; int* vout = gb.perm_alt;
   unsigned* hist = gb.hist;
   unsigned* tmp = gb.hist + (size_t)256 * ntiles;
-  for (int shift = 0; shift < 24; shift += 8) {
+  for (int shift = 0; shift < bits; shift += 8) {
     radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
     cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
     if (e != cudaSuccess) return e;
@@ -358,9 +368,7 @@ cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_
 
 // grid of side delta anchored at the bounding box's lower corner (the tree approximation's
 // resolution); more than kMaxCellsPerAxis cells per axis sets bit 4 of *status
-__global__ void coarse_geom_kernel(const double* __restrict__ bb, double delta, GridGeom* __restrict__ g,
-                                   int* __restrict__ status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ GridGeom make_coarse_geom(const double* __restrict__ bb, double delta, int* __restrict__ status) {
   GridGeom r;
   const bool finite = isfinite(bb[0]) && isfinite(bb[1]) && isfinite(bb[2]) && isfinite(bb[3]);
   r.bad = finite ? 0 : 1;
@@ -374,7 +382,13 @@ __global__ void coarse_geom_kernel(const double* __restrict__ bb, double delta, 
   if (cx > kMaxCellsPerAxis || cy > kMaxCellsPerAxis) atomicOr(status, 4);
   r.ncx = (int)fmin(cx, (double)kMaxCellsPerAxis);
   r.ncy = (int)fmin(cy, (double)kMaxCellsPerAxis);
-  *g = r;
+  return r;
+}
+
+__global__ void coarse_geom_kernel(const double* __restrict__ bb, double delta, GridGeom* __restrict__ g,
+                                   int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  *g = make_coarse_geom(bb, delta, status);
 }
 
 // 1 at the first position of every run of equal sorted keys
@@ -466,6 +480,243 @@ cudaError_t grid_sort_device(const double* pos, const double* shear, const doubl
   build_sorted<<<(n + 255) / 256, 256, 0, s>>>(pos, shear, wts, vin, kin, n, d_geom, 0, 0.0, 0.0, 1.0, 1.f,
                                                want_f32, gb.px, gb.py, gb.xr, gb.xi, gb.w, gb.p4, gb.s4);
   g_launches += 2;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------ batched forms
+namespace {
+
+// largest k < n with v[k] <= x (the catalogue holding galaxy, tile or cell x: empty
+// catalogues share their start with the next one, which the search passes over)
+__device__ __forceinline__ int seg_find(const int64_t* v, int n, int64_t x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (x >= v[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int seg_find(const int* v, int n, int x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (x >= v[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// one block per tile of kBBoxTile galaxies of one catalogue
+__global__ void bbox_tiles(const double* __restrict__ pos, const CatSet cs, double* __restrict__ part) {
+  __shared__ double sm[4][256];
+  const int t = blockIdx.x, k = seg_find(cs.tile0, cs.n, t);
+  const int64_t a = cs.c0[k] + (int64_t)(t - cs.tile0[k]) * kBBoxTile;
+  const int64_t b = min(a + kBBoxTile, cs.c0[k + 1]);
+  double mnx = DBL_MAX, mny = DBL_MAX, mxx = -DBL_MAX, mxy = -DBL_MAX;
+  for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+    const double x = pos[2 * i], y = pos[2 * i + 1];
+    mnx = fmin(mnx, x); mxx = fmax(mxx, x);
+    mny = fmin(mny, y); mxy = fmax(mxy, y);
+  }
+  sm[0][threadIdx.x] = mnx; sm[1][threadIdx.x] = mny; sm[2][threadIdx.x] = mxx; sm[3][threadIdx.x] = mxy;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sm[0][threadIdx.x] = fmin(sm[0][threadIdx.x], sm[0][threadIdx.x + st]);
+      sm[1][threadIdx.x] = fmin(sm[1][threadIdx.x], sm[1][threadIdx.x + st]);
+      sm[2][threadIdx.x] = fmax(sm[2][threadIdx.x], sm[2][threadIdx.x + st]);
+      sm[3][threadIdx.x] = fmax(sm[3][threadIdx.x], sm[3][threadIdx.x + st]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) part[4 * (size_t)t + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// thread k: catalogue k's bounding box from its tiles
+__global__ void bbox_cats(const CatSet cs, const double* __restrict__ part, double* __restrict__ bbox) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cs.n) return;
+  double v[4] = {DBL_MAX, DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int t = cs.tile0[k]; t < cs.tile0[k + 1]; ++t) {
+    v[0] = fmin(v[0], part[4 * (size_t)t + 0]);
+    v[1] = fmin(v[1], part[4 * (size_t)t + 1]);
+    v[2] = fmax(v[2], part[4 * (size_t)t + 2]);
+    v[3] = fmax(v[3], part[4 * (size_t)t + 3]);
+  }
+  for (int q = 0; q < 4; ++q) bbox[4 * k + q] = v[q];
+}
+
+// thread k: catalogue k's grid, for separations up to rmax (rmax > 0) or of side delta (the
+// tree approximation's reduced catalogues: rmax <= 0)
+__global__ void geom_cats(const CatSet cs, const double* __restrict__ bbox, double rmax, double delta,
+                          GridGeom* __restrict__ geoms, int* __restrict__ status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cs.n) return;
+  const int n = (int)(cs.c0[k + 1] - cs.c0[k]);
+  if (n == 0) return;
+  geoms[k] = rmax > 0.0 ? make_geom(bbox + 4 * k, rmax, n) : make_coarse_geom(bbox + 4 * k, delta, status);
+}
+
+// keys of the set: the cell list entry coff[k] + cell (exact grid), or k * 2^24 + cell (the
+// tree approximation's reduction, where runs of equal keys are the reduced galaxies)
+__global__ void keys_cats(const double* __restrict__ pos, const CatSet cs, const GridGeom* __restrict__ geoms,
+                          bool coarse, int* __restrict__ keys, int* __restrict__ idx, int* __restrict__ status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cs.c0[cs.n]) return;
+  const int k = seg_find(cs.c0, cs.n, i);
+  const double x = pos[2 * i], y = pos[2 * i + 1];
+  if (!isfinite(x) || !isfinite(y)) atomicOr(status, 2);
+  const int c = cell_key(geoms[k], x, y);
+  keys[i] = coarse ? (k << 24) + c : (int)cs.coff[k] + c;
+  idx[i] = (int)i;
+}
+
+// cell lists of the set from the sorted keys: thread p fills the entries between the cells of
+// sorted positions p - 1 and p with p (the first galaxy at or after them), within the used
+// part of each catalogue's list (ncx * ncy cells and the end entry)
+__global__ void cell_bounds_cats(const int* __restrict__ keys, const CatSet cs, const GridGeom* __restrict__ geoms,
+                                 int* __restrict__ start) {
+  const int64_t n = cs.c0[cs.n];
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > n) return;
+  const int lo = p == 0 ? -1 : keys[p - 1];
+  const int hi = p == n ? -1 : keys[p];
+  const int kl = p == 0 ? -1 : seg_find(cs.coff, cs.n, lo);
+  const int kh = p == n ? cs.n : seg_find(cs.coff, cs.n, hi);
+  if (kl == kh) {
+    for (int c = lo + 1; c <= hi; ++c) start[c] = (int)p;
+    return;
+  }
+  if (kl >= 0) {  // the rest of catalogue kl's list, its end entry included
+    const int end = (int)cs.coff[kl] + geoms[kl].ncx * geoms[kl].ncy;
+    for (int c = lo + 1; c <= end; ++c) start[c] = (int)p;
+  }
+  if (kh < cs.n)  // catalogue kh's list up to its first galaxy's cell
+    for (int c = (int)cs.coff[kh]; c <= hi; ++c) start[c] = (int)p;
+}
+
+__global__ void build_sorted_cats(const double* __restrict__ pos, const double* __restrict__ shear,
+                                  const double* __restrict__ wts, const int* __restrict__ perm,
+                                  const int* __restrict__ keys, const CatSet cs, const GridGeom* __restrict__ geoms,
+                                  bool want_f32, double* __restrict__ px, double* __restrict__ py,
+                                  double* __restrict__ xr, double* __restrict__ xi, double* __restrict__ w,
+                                  float4* __restrict__ p4, float4* __restrict__ s4) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cs.c0[cs.n]) return;
+  const int i = perm[p];
+  const double x = pos[2 * (size_t)i], y = pos[2 * (size_t)i + 1], ww = wts[i];
+  const double gr = ww * shear[2 * (size_t)i], gi = ww * shear[2 * (size_t)i + 1];
+  px[p] = x; py[p] = y; xr[p] = gr; xi[p] = gi; w[p] = ww;
+  if (want_f32) {
+    const int k = seg_find(cs.c0, cs.n, p);
+    const GridGeom G = geoms[k];
+    const int key = keys[p] - (int)cs.coff[k];
+    const int cx = key % G.ncx, cy = key / G.ncx;
+    // cx*cell and cy*cell are exact in float (cell has few significant bits)
+    const float ax = (float)cx * G.cellf, ay = (float)cy * G.cellf;
+    const float lx = (float)((x - G.x0) - (double)cx * G.cell);
+    const float ly = (float)((y - G.y0) - (double)cy * G.cell);
+    p4[p] = make_float4(ax, ay, lx, ly);
+    s4[p] = make_float4((float)gr, (float)gi, (float)ww, 0.f);
+  }
+}
+
+// thread k: catalogue k's reduced galaxies, the runs of equal keys that start in its range of
+// sorted positions (head_scan: exclusive scan of the run heads)
+__global__ void run_counts(const unsigned* __restrict__ head_scan, const int* __restrict__ keys, const CatSet cs,
+                           int* __restrict__ counts) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= cs.n) return;
+  const int64_t n = cs.c0[cs.n], a = cs.c0[k], b = cs.c0[k + 1];
+  if (a == b) {
+    counts[k] = 0;
+    return;
+  }
+  auto runs_before = [&](int64_t p) -> int64_t {  // runs that start before sorted position p
+    if (p < n) return head_scan[p];
+    return (int64_t)head_scan[n - 1] + ((n == 1 || keys[n - 1] != keys[n - 2]) ? 1 : 0);
+  };
+  counts[k] = (int)(runs_before(b) - runs_before(a));
+}
+
+}  // namespace
+
+bool make_catset(const int64_t* c0, int n_cat, CatSet& cs) {
+  if (n_cat < 1 || n_cat > kMaxCatSet) return false;
+  cs.n = n_cat;
+  cs.c0[0] = 0;
+  cs.coff[0] = 0;
+  cs.tile0[0] = 0;
+  for (int k = 0; k < n_cat; ++k) {
+    const int64_t nk = c0[k + 1] - c0[k];
+    cs.c0[k + 1] = c0[k + 1] - c0[0];
+    cs.coff[k + 1] = cs.coff[k] + (nk > 0 ? (int64_t)grid_cells_cap(nk) : 0);
+    cs.tile0[k + 1] = cs.tile0[k] + (int)((nk + kBBoxTile - 1) / kBBoxTile);
+  }
+  // keys and positions stay below 2^31; the reduction's keys need k * 2^24 < 2^31
+  return cs.coff[n_cat] < ((int64_t)1 << 31) && cs.c0[n_cat] < ((int64_t)1 << 31) - 1;
+}
+
+cudaError_t bbox_batch(const double* pos, const CatSet& cs, double* part, double* bbox, cudaStream_t s) {
+  if (cs.tile0[cs.n] > 0) {
+    bbox_tiles<<<cs.tile0[cs.n], 256, 0, s>>>(pos, cs, part);
+    ++g_launches;
+  }
+  bbox_cats<<<(cs.n + 127) / 128, 128, 0, s>>>(cs, part, bbox);
+  ++g_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t grid_sort_batch(const double* pos, const double* shear, const double* wts, const CatSet& cs,
+                            const double* bbox, double rmax, GridGeom* geoms, bool want_f32, GridBuffers& gb,
+                            int** perm_out, int* status, cudaStream_t s) {
+  const int64_t n = cs.c0[cs.n];
+  geom_cats<<<(cs.n + 127) / 128, 128, 0, s>>>(cs, bbox, rmax, 0.0, geoms, status);
+  ++g_launches;
+  if (n == 0) {
+    *perm_out = gb.perm;
+    return cudaGetLastError();
+  }
+  const unsigned nblk = (unsigned)((n + 255) / 256);
+  keys_cats<<<nblk, 256, 0, s>>>(pos, cs, geoms, false, gb.keys, gb.perm, status);
+  ++g_launches;
+  int bits = 8;
+  while (bits < 32 && (cs.coff[cs.n] >> bits) > 0) bits += 8;
+  int* keys = nullptr;
+  int* perm = nullptr;
+  cudaError_t e = radix_sort_cells(gb, (int)n, &keys, &perm, s, bits);
+  if (e != cudaSuccess) return e;
+  cell_bounds_cats<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(keys, cs, geoms, gb.cell_start);
+  build_sorted_cats<<<nblk, 256, 0, s>>>(pos, shear, wts, perm, keys, cs, geoms, want_f32, gb.px, gb.py, gb.xr,
+                                         gb.xi, gb.w, gb.p4, gb.s4);
+  g_launches += 2;
+  *perm_out = perm;
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_batch(const double* pos, const double* shear, const double* wts, const CatSet& cs,
+                         const double* bbox, double delta, GridGeom* geoms, GridBuffers& gb, unsigned* head,
+                         double* rpos, double* rshear, double* rw, int* counts, int* status, cudaStream_t s) {
+  const int64_t n = cs.c0[cs.n];
+  geom_cats<<<(cs.n + 127) / 128, 128, 0, s>>>(cs, bbox, 0.0, delta, geoms, status);
+  ++g_launches;
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * cs.n, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  const unsigned nblk = (unsigned)((n + 255) / 256);
+  keys_cats<<<nblk, 256, 0, s>>>(pos, cs, geoms, true, gb.keys, gb.perm, status);
+  ++g_launches;
+  int* keys = nullptr;
+  int* perm = nullptr;
+  cudaError_t e = radix_sort_cells(gb, (int)n, &keys, &perm, s, 32);
+  if (e != cudaSuccess) return e;
+  run_heads<<<nblk, 256, 0, s>>>(keys, (int)n, head);
+  e = scan_exclusive(head, (size_t)n, gb.hist, s);
+  if (e != cudaSuccess) return e;
+  reduce_runs<<<nblk, 256, 0, s>>>(keys, perm, head, (int)n, pos, shear, wts, rpos, rshear, rw, counts + cs.n);
+  run_counts<<<(cs.n + 127) / 128, 128, 0, s>>>(head, keys, cs, counts);
+  g_launches += 3;
   return cudaGetLastError();
 }
 
