@@ -137,16 +137,24 @@ __global__ void radix_hist(const int* __restrict__ keys, int n, int shift,
 }
 
 // Stable scatter: warp w of a tile owns items [w*256, w*256+256) of the tile, visited in
-// order in rounds of 32, so ranks follow input order.
+// order in rounds of 32, so ranks follow input order.  The tile is first sorted by digit in
+// shared memory; each digit's run is then written to its place in one contiguous, coalesced
+// stretch (offs: exclusive scan of the digit counts, digit-major over the tiles).
 __global__ void radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ val_in,
                               int n, int shift, const unsigned* __restrict__ offs, int ntiles,
                               int* __restrict__ keys_out, int* __restrict__ val_out) {
   __shared__ unsigned wcnt[kTileThreads / 32][256];
+  __shared__ unsigned dstart[256];  // first position of each digit in the tile's sorted order
+  __shared__ unsigned wsum[kTileThreads / 32];
+  __shared__ int skey[kTile];
+  __shared__ int sval[kTile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int d = threadIdx.x; d < (kTileThreads / 32) * 256; d += kTileThreads)
     (&wcnt[0][0])[d] = 0;
   __syncthreads();
-  const int wbase = blockIdx.x * kTile + warp * (32 * kTileItems);
+  const int tbase = blockIdx.x * kTile;
+  const int tn = min(kTile, n - tbase);
+  const int wbase = tbase + warp * (32 * kTileItems);
   const unsigned lt = (1u << lane) - 1u;
   for (int r = 0; r < kTileItems; ++r) {
     int i = wbase + r * 32 + lane;
@@ -160,14 +168,27 @@ __global__ void radix_scatter(const int* __restrict__ keys_in, const int* __rest
     __syncwarp();
   }
   __syncthreads();
-  {  // exclusive prefix over warps, per digit
-    unsigned d = threadIdx.x;
+  {  // thread d: exclusive prefix over the warps of digit d, and the digit's tile total
+    const unsigned d = threadIdx.x;
     unsigned run = 0;
     for (int w = 0; w < kTileThreads / 32; ++w) {
-      unsigned t = wcnt[w][d];
+      const unsigned t = wcnt[w][d];
       wcnt[w][d] = run;
       run += t;
     }
+    // exclusive scan of the totals over the digits (one per thread)
+    unsigned inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    unsigned before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    dstart[d] = before + inc - run;
+    for (int w = 0; w < kTileThreads / 32; ++w) wcnt[w][d] += dstart[d];
   }
   __syncthreads();
   for (int r = 0; r < kTileItems; ++r) {
@@ -178,14 +199,21 @@ __global__ void radix_scatter(const int* __restrict__ keys_in, const int* __rest
       int key = keys_in[i];
       unsigned d = ((unsigned)key >> shift) & 0xFFu;
       unsigned peers = __match_any_sync(valid_mask, d);
-      unsigned rank = __popc(peers & lt);
-      unsigned pos = offs[(size_t)d * ntiles + blockIdx.x] + wcnt[warp][d] + rank;
-      keys_out[pos] = key;
-      val_out[pos] = val_in[i];
+      unsigned pos = wcnt[warp][d] + __popc(peers & lt);
+      skey[pos] = key;
+      sval[pos] = val_in[i];
       __syncwarp(valid_mask);
       if ((peers & lt) == 0) wcnt[warp][d] += __popc(peers);
     }
     __syncwarp();
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < tn; j += kTileThreads) {
+    const int key = skey[j];
+    const unsigned d = ((unsigned)key >> shift) & 0xFFu;
+    const unsigned pos = offs[(size_t)d * ntiles + blockIdx.x] + ((unsigned)j - dstart[d]);
+    keys_out[pos] = key;
+    val_out[pos] = sval[j];
   }
 }
 
