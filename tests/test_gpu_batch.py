@@ -141,3 +141,26 @@ def test_out_slot_out_of_range_is_an_argument_error(torch_cuda):
     with pytest.raises(ext4pcf.Ext4pcfError) as e:
         _run(torch_cuda, "fp64", pos, sh, w, offs, edges, nmax, slots=np.array([0, 1, 2, 3, 7]), n_out=4)
     assert e.value.code == ext4pcf.EXT4PCF_E_INVALID_ARG
+
+
+def test_batched_grid_build_equals_per_catalogue_build(torch_cuda):
+    """Up to 128 catalogues a call sorts them all at once; beyond that each is sorted on its
+    own.  130 small catalogues in one call (built one by one) and the same catalogues in two
+    calls of 65 (built at once) give the same FP64 sums bit for bit."""
+    rng = np.random.default_rng(21)
+    sizes = rng.integers(0, 60, 130)
+    sizes[7] = 0  # an empty catalogue
+    cats = [synth.uniform_catalog(int(m), 12.0, seed=300 + k, weights="uniform") if m > 0
+            else (np.zeros((0, 2)), np.zeros((0, 2)), np.zeros(0)) for k, m in enumerate(sizes)]
+    pos = np.concatenate([c[0] + 100.0 * k for k, c in enumerate(cats)])
+    sh = np.concatenate([c[1] for c in cats])
+    w = np.concatenate([c[2] for c in cats])
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    edges, nmax = synth.log_edges(0.8, 6.0, 4), 3
+    one = _run(torch_cuda, "fp64", pos, sh, w, offs, edges, nmax)
+    a, b = offs[65], offs[130]
+    first = _run(torch_cuda, "fp64", pos[:a], sh[:a], w[:a], offs[:66], edges, nmax)
+    second = _run(torch_cuda, "fp64", pos[a:b], sh[a:b], w[a:b], offs[65:] - a, edges, nmax)
+    assert np.array_equal(one[:65], first)
+    assert np.array_equal(one[65:], second)
+    assert np.abs(one).max() > 0
