@@ -460,8 +460,9 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
       float accD[16];  // FP32 sums of the promoted partials: this row, 16 columns
       const bool has_cols = qq * 16 < npad;
       // Software pipeline over the stages (k = this stage):
-      //  * the partial sum of stage k - 2 is read out of TMEM (tcgen05.ld issued mid-stage,
-      //    waited for at its end), then its D buffer is released;
+      //  * the partial sum of stage k - 2 is read out of TMEM at the end of this stage
+      //    (tcgen05.ld issued there, waited for after the first half of the next stage's rows),
+      //    then its D buffer is released, before the MMAs of stage k are signalled;
       //  * the rows of stage k - 1 were stored into TMEM at the end of the previous iteration;
       //    their completion is awaited (and the MMA warp signalled) only after the first half
       //    of this stage's rows is formed, so the store latency is hidden behind that work.
@@ -500,6 +501,8 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) accD[j] = 0.f;
       int prev_slot = 0;
+      uint32_t pv[16];  // a partial sum on its way out of TMEM: read at the end of one stage,
+                        // added in the middle of the next
       for (int k = 0; k < nstage; ++k) {
         wait(&in_full[islot], iph);
         wait(&ab_empty[aslot], aph ^ 1u);
@@ -532,12 +535,11 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
           uint32_t hi[8], lo[8];
           if (cjC) kr_group<true>(PB, PC, 0, hi, lo);
           else kr_group<false>(PB, PC, 0, hi, lo);
+          if (k >= 3) promote_finish(gs + k - 3, pv);
           if (k >= 1) publish(prev_slot);
           tmem_st8(acol, hi);
           tmem_st8(acol + 64, lo);
         }
-        uint32_t pv[16];
-        if (k >= 2) promote_issue(gs + k - 2, pv);
         {
           uint32_t hi[8], lo[8];
           if (cjC) kr_group<true>(PB, PC, 1, hi, lo);
@@ -548,15 +550,16 @@ contract_h16_kernel(const __grid_constant__ HArgs args) {
           tmem_st8(acol + 8, hi);
           tmem_st8(acol + 64 + 8, lo);
         }
-        if (k >= 2) promote_finish(gs + k - 2, pv);
+        if (k >= 2) promote_issue(gs + k - 2, pv);
         prev_slot = aslot;
         if (++islot == S_in) { islot = 0; iph ^= 1u; }
         if (++aslot == kHSlots) { aslot = 0; aph ^= 1u; }
       }
-      // drain the pipeline: the last stage's rows, then the last two partial sums
+      // drain the pipeline: the partial sum read at the end of the last stage, the last
+      // stage's rows, then the last two partial sums
+      if (nstage >= 3) promote_finish(gs + nstage - 3, pv);
       if (nstage >= 1) publish(prev_slot);
       for (long long gg = gs + (nstage >= 2 ? nstage - 2 : 0); gg < gs + nstage; ++gg) {
-        uint32_t pv[16];
         promote_issue(gg, pv);
         promote_finish(gg, pv);
       }
