@@ -380,8 +380,8 @@ gather_kernel(const GatherArgs args, cplx_t<R>* __restrict__ rec, cplx_t<R>* __r
                        (float)((pyi - gy0) - (double)ccy * cell));
     }
     if (warp == 0) {
-      // the rows of cells within rmax of the centre, one per lane (cells are at least rmax / 8
-      // wide, so there are at most 18), kept in row order when they hold galaxies
+      // the rows of cells within rmax of the centre, one per lane (cells are at least rmax / 16
+      // wide, so there are at most 34), kept in row order when they hold galaxies
       const double xc = pxi - gx0, yc = pyi - gy0;
       const int cy0 = max((int)floor((yc - rmax) / cell), 0);
       const int cy1 = min((int)floor((yc + rmax) / cell), gncy - 1);

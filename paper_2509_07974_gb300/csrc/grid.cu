@@ -50,7 +50,8 @@ __global__ void bbox_final(const double* __restrict__ part, int np, double* __re
 }
 
 // ------------------------------------------------------------------------ device grid
-// cell side: about an eighth of the largest separation, at most ~4000 cells per axis and
+// cell side: about a sixteenth of the largest separation (finer cells leave fewer candidates
+// outside the largest separation; 34 rows of cells at most), at most ~4000 cells per axis and
 // about sqrt(n) per axis (so that the cells number at most 4n: grid_cells_cap), and with 12
 // significant bits so that (cell index) * cell is exact in float
 __device__ GridGeom make_geom(const double* __restrict__ bb, double rmax, int n) {
@@ -60,7 +61,7 @@ __device__ GridGeom make_geom(const double* __restrict__ bb, double rmax, int n)
   const double x0 = finite ? bb[0] : 0.0, y0 = finite ? bb[1] : 0.0;
   const double wx = finite ? bb[2] - bb[0] : 0.0, wy = finite ? bb[3] - bb[1] : 0.0;
   const double extent = fmax(wx, wy);
-  double c = rmax / 8.0;
+  double c = rmax / 16.0;
   if (extent / 4000.0 > c) c = extent / 4000.0;
   // 1.01: the rounding to 12 bits below lowers c by less than 2^-12, so floor(extent / c)
   // stays below sqrt(n) and (sqrt(n) + 1)^2 <= 4n cells
