@@ -475,7 +475,9 @@ int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears
   ENSURE(ctx->cell_start, (size_t)std::max<int64_t>(cells_total, 1) * 4);
   if (centre_mask) CK(cudaMemsetAsync(ctx->ncen.p, 0, (size_t)(n_cat + 1) * sizeof(int), s));
   {
-    const size_t ntiles = (size_t)((nsort + 2047) / 2048);
+    // sort tiles: a batched sort's tiles never span two catalogues (at most one partial
+    // tile per catalogue more than one array needs)
+    const size_t ntiles = (size_t)((nsort + 2047) / 2048) + (size_t)n_cat + 1;
     ENSURE(ctx->keys, (size_t)nsort * 4); ENSURE(ctx->keys_alt, (size_t)nsort * 4);
     ENSURE(ctx->perm, (size_t)nsort * 4); ENSURE(ctx->perm_alt, (size_t)nsort * 4);
     ENSURE(ctx->hist, ((size_t)256 * ntiles * 2 + 4096) * 4);

@@ -194,15 +194,18 @@ inline size_t grid_cells_cap(int64_t n) { return (size_t)(4 * n + 2); }
 
 // Batched grid building: the catalogues of one measurement at once, concatenated.  c0[k] is
 // the first galaxy of catalogue k (in the input and in the sorted arrays), coff[k] its first
-// entry of the concatenated cell lists (grid_cells_cap entries each), tile0[k] its first
-// bounding-box tile; c0[0] = coff[0] = tile0[0] = 0.
+// entry of the concatenated cell lists (grid_cells_cap entries each), tile0[k] / stile0[k] its
+// first bounding-box / sort tile; c0[0] = coff[0] = tile0[0] = stile0[0] = 0.  The sort is
+// segmented: every catalogue's keys are sorted in place within its range of positions.
 constexpr int kMaxCatSet = 128;
 constexpr int kBBoxTile = 8192;  // galaxies per bounding-box tile
+constexpr int kSortTile = 2048;  // keys per radix-sort tile
 struct CatSet {
   int n;
   int64_t c0[kMaxCatSet + 1];
   int64_t coff[kMaxCatSet + 1];
-  int tile0[kMaxCatSet + 1];
+  int tile0[kMaxCatSet + 1];   // bounding-box tiles
+  int stile0[kMaxCatSet + 1];  // radix-sort tiles (a tile never spans two catalogues)
 };
 // fills cs from the catalogue offsets (host); false if there are too many catalogues or cells
 // for one set (then each catalogue is built on its own)

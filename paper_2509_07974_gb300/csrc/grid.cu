@@ -123,27 +123,75 @@ __global__ void make_keys(const double* __restrict__ pos, int n, double x0, doub
 }
 
 // ------------------------------------------------------------------------ radix sort
-__global__ void radix_hist(const int* __restrict__ keys, int n, int shift,
-                           unsigned* __restrict__ hist, int ntiles) {
+static_assert(kTile == kSortTile, "sort tile");
+
+// Tiles of a radix pass: tile t covers keys [base, base + cnt) and its count of digit d sits at
+// hist[h0 + d * hstride] of the digit-major counts whose exclusive scan gives every digit run's
+// first position.  One array: h0 = t, hstride = the tile count.  A catalogue set (segmented
+// sort): the counts of catalogue k, digit-major over its own tiles, start at 256 stile0[k], so
+// that the scan's offsets are positions inside catalogue k's own range.
+struct PlainTiles {
+  int n, ntiles;
+  __device__ void tile(int t, int& base, int& cnt, size_t& h0, int& hstride) const {
+    base = t * kTile;
+    cnt = min(kTile, n - base);
+    h0 = (size_t)t;
+    hstride = ntiles;
+  }
+};
+// largest k < n with v[k] <= x (empty catalogues share their start with the next one, which the
+// search passes over)
+__device__ __forceinline__ int seg_find(const int64_t* v, int n, int64_t x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (x >= v[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int seg_find(const int* v, int n, int x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (x >= v[mid]) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+struct CatTiles {
+  CatSet cs;
+  __device__ void tile(int t, int& base, int& cnt, size_t& h0, int& hstride) const {
+    const int k = seg_find(cs.stile0, cs.n, t);
+    base = (int)cs.c0[k] + (t - cs.stile0[k]) * kTile;
+    cnt = min(kTile, (int)cs.c0[k + 1] - base);
+    hstride = cs.stile0[k + 1] - cs.stile0[k];
+    h0 = (size_t)256 * cs.stile0[k] + (t - cs.stile0[k]);
+  }
+};
+
+template <class Tiles>
+__global__ void radix_hist(const int* __restrict__ keys, const Tiles tl, int shift, unsigned* __restrict__ hist) {
   __shared__ unsigned h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
-  const int base = blockIdx.x * kTile;
+  int base, cnt, hs;
+  size_t h0;
+  tl.tile(blockIdx.x, base, cnt, h0, hs);
   for (int k = 0; k < kTileItems; ++k) {
-    int i = base + k * kTileThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[((unsigned)keys[i] >> shift) & 0xFFu], 1u);
+    const int j = k * kTileThreads + threadIdx.x;
+    if (j < cnt) atomicAdd(&h[((unsigned)keys[base + j] >> shift) & 0xFFu], 1u);
   }
   __syncthreads();
-  hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+  hist[h0 + (size_t)threadIdx.x * hs] = h[threadIdx.x];
 }
 
 // Stable scatter: warp w of a tile owns items [w*256, w*256+256) of the tile, visited in
 // order in rounds of 32, so ranks follow input order.  The tile is first sorted by digit in
 // shared memory; each digit's run is then written to its place in one contiguous, coalesced
 // stretch (offs: exclusive scan of the digit counts, digit-major over the tiles).
-__global__ void radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ val_in,
-                              int n, int shift, const unsigned* __restrict__ offs, int ntiles,
-                              int* __restrict__ keys_out, int* __restrict__ val_out) {
+template <class Tiles>
+__global__ void radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ val_in, const Tiles tl,
+                              int shift, const unsigned* __restrict__ offs, int* __restrict__ keys_out,
+                              int* __restrict__ val_out) {
   __shared__ unsigned wcnt[kTileThreads / 32][256];
   __shared__ unsigned dstart[256];  // first position of each digit in the tile's sorted order
   __shared__ unsigned wsum[kTileThreads / 32];
@@ -153,8 +201,10 @@ __global__ void radix_scatter(const int* __restrict__ keys_in, const int* __rest
   for (int d = threadIdx.x; d < (kTileThreads / 32) * 256; d += kTileThreads)
     (&wcnt[0][0])[d] = 0;
   __syncthreads();
-  const int tbase = blockIdx.x * kTile;
-  const int tn = min(kTile, n - tbase);
+  int tbase, tn, hs;
+  size_t h0;
+  tl.tile(blockIdx.x, tbase, tn, h0, hs);
+  const int n = tbase + tn;  // items of the tile: [tbase, n)
   const int wbase = tbase + warp * (32 * kTileItems);
   const unsigned lt = (1u << lane) - 1u;
   for (int r = 0; r < kTileItems; ++r) {
@@ -212,7 +262,7 @@ __global__ void radix_scatter(const int* __restrict__ keys_in, const int* __rest
   for (int j = threadIdx.x; j < tn; j += kTileThreads) {
     const int key = skey[j];
     const unsigned d = ((unsigned)key >> shift) & 0xFFu;
-    const unsigned pos = offs[(size_t)d * ntiles + blockIdx.x] + ((unsigned)j - dstart[d]);
+    const unsigned pos = offs[h0 + (size_t)d * hs] + ((unsigned)j - dstart[d]);
     keys_out[pos] = key;
     val_out[pos] = sval[j];
   }
@@ -353,11 +403,12 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
   int* vin = gb.perm; int* vout = gb.perm_alt;
   unsigned* hist = gb.hist;
   unsigned* tmp = gb.hist + (size_t)256 * ntiles;
+  const PlainTiles tl{n, ntiles};
   for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
+    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, tl, shift, hist);
     cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
     if (e != cudaSuccess) return e;
-    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
+    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, tl, shift, hist, kout, vout);
     g_launches += 2;  // histogram + scatter
     int* t = kin; kin = kout; kout = t;
     t = vin; vin = vout; vout = t;
@@ -381,11 +432,35 @@ cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_
   int* vin = gb.perm; int* vout = gb.perm_alt;
   unsigned* hist = gb.hist;
   unsigned* tmp = gb.hist + (size_t)256 * ntiles;
+  const PlainTiles tl{n, ntiles};
   for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, n, shift, hist, ntiles);
+    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, tl, shift, hist);
     cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
     if (e != cudaSuccess) return e;
-    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, n, shift, hist, ntiles, kout, vout);
+    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, tl, shift, hist, kout, vout);
+    g_launches += 2;
+    int* t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+  }
+  *keys_out = kin;
+  *perm_out = vin;
+  return cudaGetLastError();
+}
+
+// the segmented form: every catalogue of cs sorted within its own range of positions by
+// keys below 2^24 (three passes); gb.hist holds 2 x 256 x stile0[n] + 4096 counters
+cudaError_t radix_sort_cats(GridBuffers& gb, const CatSet& cs, int** keys_out, int** perm_out, cudaStream_t s) {
+  const int ntiles = cs.stile0[cs.n];
+  int* kin = gb.keys; int* kout = gb.keys_alt;
+  int* vin = gb.perm; int* vout = gb.perm_alt;
+  unsigned* hist = gb.hist;
+  unsigned* tmp = gb.hist + (size_t)256 * ntiles;
+  const CatTiles tl{cs};
+  for (int shift = 0; shift < 24 && ntiles > 0; shift += 8) {
+    radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, tl, shift, hist);
+    cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter<<<ntiles, kTileThreads, 0, s>>>(kin, vin, tl, shift, hist, kout, vout);
     g_launches += 2;
     int* t = kin; kin = kout; kout = t;
     t = vin; vin = vout; vout = t;
@@ -515,25 +590,6 @@ cudaError_t grid_sort_device(const double* pos, const double* shear, const doubl
 // ------------------------------------------------------------------------ batched forms
 namespace {
 
-// largest k < n with v[k] <= x (the catalogue holding galaxy, tile or cell x: empty
-// catalogues share their start with the next one, which the search passes over)
-__device__ __forceinline__ int seg_find(const int64_t* v, int n, int64_t x) {
-  int lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (x >= v[mid]) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-__device__ __forceinline__ int seg_find(const int* v, int n, int x) {
-  int lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (x >= v[mid]) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
 // one block per tile of kBBoxTile galaxies of one catalogue
 __global__ void bbox_tiles(const double* __restrict__ pos, const CatSet cs, double* __restrict__ part) {
   __shared__ double sm[4][256];
@@ -585,17 +641,16 @@ __global__ void geom_cats(const CatSet cs, const double* __restrict__ bbox, doub
   geoms[k] = rmax > 0.0 ? make_geom(bbox + 4 * k, rmax, n) : make_coarse_geom(bbox + 4 * k, delta, status);
 }
 
-// keys of the set: the cell list entry coff[k] + cell (exact grid), or k * 2^24 + cell (the
-// tree approximation's reduction, where runs of equal keys are the reduced galaxies)
+// keys of the set: every galaxy's cell in its catalogue's grid (below 2^24: at most
+// kMaxCellsPerAxis^2 cells), sorted within the catalogue's range of positions
 __global__ void keys_cats(const double* __restrict__ pos, const CatSet cs, const GridGeom* __restrict__ geoms,
-                          bool coarse, int* __restrict__ keys, int* __restrict__ idx, int* __restrict__ status) {
+                          int* __restrict__ keys, int* __restrict__ idx, int* __restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cs.c0[cs.n]) return;
   const int k = seg_find(cs.c0, cs.n, i);
   const double x = pos[2 * i], y = pos[2 * i + 1];
   if (!isfinite(x) || !isfinite(y)) atomicOr(status, 2);
-  const int c = cell_key(geoms[k], x, y);
-  keys[i] = coarse ? (k << 24) + c : (int)cs.coff[k] + c;
+  keys[i] = cell_key(geoms[k], x, y);
   idx[i] = (int)i;
 }
 
@@ -607,20 +662,24 @@ __global__ void cell_bounds_cats(const int* __restrict__ keys, const CatSet cs, 
   const int64_t n = cs.c0[cs.n];
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p > n) return;
+  const int kl = p == 0 ? -1 : seg_find(cs.c0, cs.n, p - 1);  // catalogues of positions p - 1, p
+  const int kh = p == n ? cs.n : seg_find(cs.c0, cs.n, p);
   const int lo = p == 0 ? -1 : keys[p - 1];
   const int hi = p == n ? -1 : keys[p];
-  const int kl = p == 0 ? -1 : seg_find(cs.coff, cs.n, lo);
-  const int kh = p == n ? cs.n : seg_find(cs.coff, cs.n, hi);
   if (kl == kh) {
-    for (int c = lo + 1; c <= hi; ++c) start[c] = (int)p;
+    int* st = start + cs.coff[kl];
+    for (int c = lo + 1; c <= hi; ++c) st[c] = (int)p;
     return;
   }
   if (kl >= 0) {  // the rest of catalogue kl's list, its end entry included
-    const int end = (int)cs.coff[kl] + geoms[kl].ncx * geoms[kl].ncy;
-    for (int c = lo + 1; c <= end; ++c) start[c] = (int)p;
+    int* st = start + cs.coff[kl];
+    const int end = geoms[kl].ncx * geoms[kl].ncy;
+    for (int c = lo + 1; c <= end; ++c) st[c] = (int)p;
   }
-  if (kh < cs.n)  // catalogue kh's list up to its first galaxy's cell
-    for (int c = (int)cs.coff[kh]; c <= hi; ++c) start[c] = (int)p;
+  if (kh < cs.n) {  // catalogue kh's list up to its first galaxy's cell
+    int* st = start + cs.coff[kh];
+    for (int c = 0; c <= hi; ++c) st[c] = (int)p;
+  }
 }
 
 __global__ void build_sorted_cats(const double* __restrict__ pos, const double* __restrict__ shear,
@@ -638,7 +697,7 @@ __global__ void build_sorted_cats(const double* __restrict__ pos, const double* 
   if (want_f32) {
     const int k = seg_find(cs.c0, cs.n, p);
     const GridGeom G = geoms[k];
-    const int key = keys[p] - (int)cs.coff[k];
+    const int key = keys[p];
     const int cx = key % G.ncx, cy = key / G.ncx;
     // cx*cell and cy*cell are exact in float (cell has few significant bits)
     const float ax = (float)cx * G.cellf, ay = (float)cy * G.cellf;
@@ -647,6 +706,52 @@ __global__ void build_sorted_cats(const double* __restrict__ pos, const double* 
     p4[p] = make_float4(ax, ay, lx, ly);
     s4[p] = make_float4((float)gr, (float)gi, (float)ww, 0.f);
   }
+}
+
+// 1 at the first position of every run of equal keys inside one catalogue
+__global__ void run_heads_cats(const int* __restrict__ keys, const CatSet cs, unsigned* __restrict__ head) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cs.c0[cs.n]) return;
+  head[p] = (p == 0 || keys[p] != keys[p - 1] || seg_find(cs.c0, cs.n, p) != seg_find(cs.c0, cs.n, p - 1)) ? 1u
+                                                                                                          : 0u;
+}
+
+// one thread per run (a cell of one catalogue): the rule of reduce_runs within the catalogue
+__global__ void reduce_runs_cats(const int* __restrict__ keys, const int* __restrict__ perm,
+                                 const unsigned* __restrict__ head_scan, const CatSet cs,
+                                 const double* __restrict__ pos, const double* __restrict__ shear,
+                                 const double* __restrict__ wts, double* __restrict__ rpos,
+                                 double* __restrict__ rshear, double* __restrict__ rw) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cs.c0[cs.n]) return;
+  const int k = seg_find(cs.c0, cs.n, p);
+  if (!(p == cs.c0[k] || keys[p] != keys[p - 1])) return;
+  const int key = keys[p];
+  const int64_t end = cs.c0[k + 1];
+  double W = 0.0, Xr = 0.0, Xi = 0.0, Sx = 0.0, Sy = 0.0;
+  for (int64_t q = p; q < end && keys[q] == key; ++q) {
+    const int i = perm[q];
+    const double w = wts[i];
+    W += w;
+    Xr += w * shear[2 * (size_t)i];
+    Xi += w * shear[2 * (size_t)i + 1];
+    Sx += w * pos[2 * (size_t)i];
+    Sy += w * pos[2 * (size_t)i + 1];
+  }
+  const unsigned r = head_scan[p];
+  if (W != 0.0) {
+    rpos[2 * (size_t)r] = Sx / W;
+    rpos[2 * (size_t)r + 1] = Sy / W;
+    rshear[2 * (size_t)r] = Xr / W;  // w * shear gives back the summed w gamma
+    rshear[2 * (size_t)r + 1] = Xi / W;
+  } else {
+    const int i = perm[p];
+    rpos[2 * (size_t)r] = pos[2 * (size_t)i];
+    rpos[2 * (size_t)r + 1] = pos[2 * (size_t)i + 1];
+    rshear[2 * (size_t)r] = 0.0;
+    rshear[2 * (size_t)r + 1] = 0.0;
+  }
+  rw[r] = W;
 }
 
 // thread k: catalogue k's reduced galaxies, the runs of equal keys that start in its range of
@@ -662,7 +767,9 @@ __global__ void run_counts(const unsigned* __restrict__ head_scan, const int* __
   }
   auto runs_before = [&](int64_t p) -> int64_t {  // runs that start before sorted position p
     if (p < n) return head_scan[p];
-    return (int64_t)head_scan[n - 1] + ((n == 1 || keys[n - 1] != keys[n - 2]) ? 1 : 0);
+    const bool last_head = n == 1 || keys[n - 1] != keys[n - 2] ||
+                           seg_find(cs.c0, cs.n, n - 1) != seg_find(cs.c0, cs.n, n - 2);
+    return (int64_t)head_scan[n - 1] + (last_head ? 1 : 0);
   };
   counts[k] = (int)(runs_before(b) - runs_before(a));
 }
@@ -675,13 +782,15 @@ bool make_catset(const int64_t* c0, int n_cat, CatSet& cs) {
   cs.c0[0] = 0;
   cs.coff[0] = 0;
   cs.tile0[0] = 0;
+  cs.stile0[0] = 0;
   for (int k = 0; k < n_cat; ++k) {
     const int64_t nk = c0[k + 1] - c0[k];
     cs.c0[k + 1] = c0[k + 1] - c0[0];
     cs.coff[k + 1] = cs.coff[k] + (nk > 0 ? (int64_t)grid_cells_cap(nk) : 0);
     cs.tile0[k + 1] = cs.tile0[k] + (int)((nk + kBBoxTile - 1) / kBBoxTile);
+    cs.stile0[k + 1] = cs.stile0[k] + (int)((nk + kSortTile - 1) / kSortTile);
   }
-  // keys and positions stay below 2^31; the reduction's keys need k * 2^24 < 2^31
+  // positions and cell-list entries stay below 2^31
   return cs.coff[n_cat] < ((int64_t)1 << 31) && cs.c0[n_cat] < ((int64_t)1 << 31) - 1;
 }
 
@@ -706,13 +815,11 @@ cudaError_t grid_sort_batch(const double* pos, const double* shear, const double
     return cudaGetLastError();
   }
   const unsigned nblk = (unsigned)((n + 255) / 256);
-  keys_cats<<<nblk, 256, 0, s>>>(pos, cs, geoms, false, gb.keys, gb.perm, status);
+  keys_cats<<<nblk, 256, 0, s>>>(pos, cs, geoms, gb.keys, gb.perm, status);
   ++g_launches;
-  int bits = 8;
-  while (bits < 32 && (cs.coff[cs.n] >> bits) > 0) bits += 8;
   int* keys = nullptr;
   int* perm = nullptr;
-  cudaError_t e = radix_sort_cells(gb, (int)n, &keys, &perm, s, bits);
+  cudaError_t e = radix_sort_cats(gb, cs, &keys, &perm, s);
   if (e != cudaSuccess) return e;
   cell_bounds_cats<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(keys, cs, geoms, gb.cell_start);
   build_sorted_cats<<<nblk, 256, 0, s>>>(pos, shear, wts, perm, keys, cs, geoms, want_f32, gb.px, gb.py, gb.xr,
@@ -734,16 +841,16 @@ cudaError_t reduce_batch(const double* pos, const double* shear, const double* w
     return cudaGetLastError();
   }
   const unsigned nblk = (unsigned)((n + 255) / 256);
-  keys_cats<<<nblk, 256, 0, s>>>(pos, cs, geoms, true, gb.keys, gb.perm, status);
+  keys_cats<<<nblk, 256, 0, s>>>(pos, cs, geoms, gb.keys, gb.perm, status);
   ++g_launches;
   int* keys = nullptr;
   int* perm = nullptr;
-  cudaError_t e = radix_sort_cells(gb, (int)n, &keys, &perm, s, 32);
+  cudaError_t e = radix_sort_cats(gb, cs, &keys, &perm, s);
   if (e != cudaSuccess) return e;
-  run_heads<<<nblk, 256, 0, s>>>(keys, (int)n, head);
+  run_heads_cats<<<nblk, 256, 0, s>>>(keys, cs, head);
   e = scan_exclusive(head, (size_t)n, gb.hist, s);
   if (e != cudaSuccess) return e;
-  reduce_runs<<<nblk, 256, 0, s>>>(keys, perm, head, (int)n, pos, shear, wts, rpos, rshear, rw, counts + cs.n);
+  reduce_runs_cats<<<nblk, 256, 0, s>>>(keys, perm, head, cs, pos, shear, wts, rpos, rshear, rw);
   run_counts<<<(cs.n + 127) / 128, 128, 0, s>>>(head, keys, cs, counts);
   g_launches += 3;
   return cudaGetLastError();
