@@ -425,15 +425,14 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
 namespace {
 // stable LSD radix sort of (gb.keys, gb.perm) by keys below kMaxCellsPerAxis^2 < 2^24 (three
 // 8-bit digits); *keys_out, *perm_out: where the sorted pairs ended up (ping-pong buffers)
-// keys below 2^bits (bits <= 32), one 8-bit digit per pass
-cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_out, cudaStream_t s, int bits = 24) {
+cudaError_t radix_sort_cells(GridBuffers& gb, int n, int** keys_out, int** perm_out, cudaStream_t s) {
   const int ntiles = (n + kTile - 1) / kTile;
   int* kin = gb.keys; int* kout = gb.keys_alt;
   int* vin = gb.perm; int* vout = gb.perm_alt;
   unsigned* hist = gb.hist;
   unsigned* tmp = gb.hist + (size_t)256 * ntiles;
   const PlainTiles tl{n, ntiles};
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = 0; shift < 24; shift += 8) {
     radix_hist<<<ntiles, kTileThreads, 0, s>>>(kin, tl, shift, hist);
     cudaError_t e = scan_exclusive(hist, (size_t)256 * ntiles, tmp, s);
     if (e != cudaSuccess) return e;
