@@ -1,0 +1,70 @@
+"""Host logic of bench.py: the algorithmic work counts behind its roofline fractions and the
+DRAM traffic figures it takes from the committed profiles."""
+import hashlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from oracle import symmetry  # noqa: E402
+from paper_2509_07974_gb300 import ext4pcf  # noqa: E402
+
+
+def test_reduced_contraction_count_is_the_exchange_map_of_the_symmetry_table():
+    """The tensor-core contraction produces, per component mu', the multipoles that the
+    identity and the exchange of Theta2 and Theta3 (column 2 of Table tab:4PCFSymm) read:
+    counted here from the oracle's map, over the bin pairs Theta2 <= Theta3 and every Theta1."""
+    for N in (0, 1, 3, 20):
+        reached = 0
+        for mup in range(9):
+            need = set()
+            for mu in range(9):
+                for n2 in range(-N, N + 1):
+                    for n3 in range(-N, N + 1):
+                        if mu == mup:
+                            need.add((n2, n3))
+                        if symmetry.MU_MAP[mu][2] == mup:
+                            need.add(symmetry.n_map(mu, 2, n2, n3))
+            reached += len(need)
+        for nb in (1, 4, 10):
+            pairs = nb * (nb + 1) // 2
+            assert bench.reduced_contraction_flop(1, N, nb) == 8 * reached * pairs * nb
+    # at the bench's sizes (N = 20, 10 bins) the reduction does 1.74x less work than all ordered triples
+    assert abs(bench.contraction_flop(1, 20, 10) / bench.reduced_contraction_flop(1, 20, 10) - 1.7435) < 1e-3
+
+
+def test_gather_count_follows_the_record_layout():
+    """Per pair: one complex multiply-add (8 FLOP) per complex-weighted record entry (G, XX),
+    a real weight times a complex power (4 FLOP) per entry of W, XA and WW, one complex
+    multiplication (6 FLOP) per power of u up to the largest |n| of the record, and 40 for the
+    triple terms."""
+    for N in (0, 2, 20, 30):
+        lay = ext4pcf.record_layout(1, N)
+        top = max(-lay["G"][1], -lay["XX"][1], lay["W"][2] - 1, lay["XA"][2] - 1, lay["WW"][2] - 1)
+        want = (8 * (lay["G"][2] + lay["XX"][2]) + 4 * (lay["W"][2] + lay["XA"][2] + lay["WW"][2]) + 6 * top
+                + 40)
+        assert bench.gather_flop_per_pair(N) == want
+    assert bench.gather_flop_per_pair(20) == 2160
+
+
+def test_traffic_figure_is_used_only_while_the_kernel_source_is_unchanged(tmp_path, monkeypatch):
+    src_dir = tmp_path / "paper_2509_07974_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = src_dir / "k.cu"
+    src.write_text("__global__ void k_kernel() {}\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles" / "k.md").write_text("# a capture\n\n```\ntraffic k_kernel 1.5e9 k.cu %s\n```\n" % sha)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("k_kernel") == 1.5e9
+    assert bench.measured_traffic("other_kernel") is None
+    src.write_text("__global__ void k_kernel() { /* changed */ }\n")
+    assert bench.measured_traffic("k_kernel") is None
+
+
+def test_committed_traffic_lines_match_the_current_sources():
+    """Every traffic line under profiles/ for the default forms refers to the current source."""
+    for kernel in ("gather_kernel", "contract_h16_kernel"):
+        assert bench.measured_traffic(kernel) is not None, kernel
