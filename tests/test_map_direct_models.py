@@ -122,3 +122,26 @@ def test_fp32_terms_stay_well_inside_the_tolerance():
             sc = np.array([math.sqrt(p2a), p2a, p2a ** 2, math.sqrt(p2w), p2w, p2w ** 2])
             worst = max(worst, float((np.abs(g[:6] - o[:6]) / (np.abs(o[:6]) + sc)).max()))
     assert worst < 1e-6
+
+
+def test_model_constants_are_the_kernel_sources_constants():
+    """The coverage model above restates the kernel's slack, half-chord widening, row and chord
+    limits and the library's cell rule; a change to any of them in the CUDA sources fails here
+    until the model follows."""
+    import os
+    import re
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2509_07974_gb300", "csrc")
+    ap = open(os.path.join(csrc, "aperture.cu")).read()
+    api = open(os.path.join(csrc, "api.cu")).read()
+    assert re.search(r"constexpr float kSlack = 1e-3f;", ap)
+    assert "const float Rs = A.rc + kSlack;" in ap
+    assert "const float h2err = 1e-6f * (A.rc + 2.f) * (A.rc + 2.f);" in ap
+    assert "const int ylo = max(acy + (int)floorf(oy - Rs), 0);" in ap
+    assert "const int yhi = min(acy + (int)floorf(oy + Rs), A.ncy - 1);" in ap
+    assert "const float dymin = fmaxf(0.f, fmaxf(k - oy, oy - (k + 1.f)));" in ap
+    assert "const float h = sqrtf(fmaf(Rs, Rs, -dymin * dymin) + h2err) + kSlack;" in ap
+    assert "const int xl = max(acx + (int)floorf(ox - h), 0);" in ap
+    assert "const int xh = min(acx + (int)floorf(ox + h), A.ncx - 1);" in ap
+    assert "std::fmax(0.5 * tmin, std::fmax(extent / 2048.0, 4.0 * tmax / 2048.0))" in api
+    assert "cell = std::ldexp(1.0, ex - 1);" in api
+    assert "A.rc = (float)(4.0 * theta / cat.cell);" in ap
