@@ -817,7 +817,7 @@ def run_batched(args, kind):
 
     tree_info = None
     if kind == "survey" and rank == 0:
-        # the tree approximation (Sect. 3.4, App. F.3) with the paper's setting for its survey
+        # the tree approximation (Sect. 3.2, App. F.3) with the paper's setting for its survey
         # (resolutions 0.5', 1', 2', r_min = 40) on the same centres, against the exact result
         exact = torch.view_as_complex(ups[0]).cpu().numpy()
         tcfg = ext4pcf.Config(device=local, stream=stream.cuda_stream, precision=ext4pcf.PRECISION[args.precision],

@@ -87,7 +87,7 @@ typedef struct {
   int64_t timeout_cycles;  /* bound on every device-side wait (0 = default) */
   int deterministic;       /* 1: fixed summation order (always honoured at present) */
   int wave_centres;        /* centres per contraction wave (0 = autotuned or 8192, 4096 for FP64) */
-  /* Tree approximation of the neighbour multipoles (paper Sect. 3.4, App. F.3, Eq.
+  /* Tree approximation of the neighbour multipoles (paper Sect. 3.2, App. F.3, Eq.
    * NPCF_treeestimator): radial bins far from the centre take their neighbours from reduced
    * catalogues, the galaxies of each cell of side Delta_d = tree_delta1 2^(d-1) (d = 1 ..
    * tree_levels, grids anchored at each catalogue's lower bounding-box corner) replaced by one

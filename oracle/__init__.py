@@ -196,7 +196,7 @@ from .map_direct import (aperture_record, crittenden_q, elementary_symmetric,  #
 # N-th order natural components and multipoles by brute force (App. F); numpy only
 from .nth_order import beta_matrix, bruteforce_multipoles  # noqa: E402
 
-# tree approximation of the neighbour multipoles (Sect. 3.4, App. F.3); numpy only
+# tree approximation of the neighbour multipoles (Sect. 3.2, App. F.3); numpy only
 from .tree import bin_levels, neighbour_multipoles, reduced_catalogue, upsilon0_from_multipoles  # noqa: E402
 
 # symmetry-reduced storage of the multipoles (Table tab:4PCFSymm); numpy only

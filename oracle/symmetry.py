@@ -1,4 +1,4 @@
-"""Symmetry-reduced storage of the 4PCF multipoles (arXiv:2509.07974, Sect. 3.3, Table
+"""Symmetry-reduced storage of the 4PCF multipoles (arXiv:2509.07974, Sect. 3.1, Table
 tab:4PCFSymm) in FP64 numpy.
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``; the product library never uses it.

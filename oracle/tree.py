@@ -1,5 +1,5 @@
 """FP64 CPU oracle of the tree approximation of the neighbour multipoles (arXiv:2509.07974,
-Sect. 3.4 and App. F.3), and its error against the exact multipoles.
+Sect. 3.2 and App. F.3), and its error against the exact multipoles.
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``; the product library never uses it.
 

@@ -179,7 +179,7 @@ cudaError_t grid_sort(const double* pos, const double* shear, const double* wts,
 cudaError_t grid_sort_device(const double* pos, const double* shear, const double* wts, int n, int c0,
                              const double* d_bbox, double rmax, GridGeom* d_geom, bool want_f32,
                              GridBuffers& gb, SortedCat& out, int* status, cudaStream_t s);
-// Reduced catalogue of the tree approximation (Sect. 3.4, App. F.3): the galaxies of every
+// Reduced catalogue of the tree approximation (Sect. 3.2, App. F.3): the galaxies of every
 // non-empty cell of side delta, anchored at the lower corner of the bounding box d_bbox
 // (grid_bbox), replaced by one galaxy at their weighted centre of mass carrying the summed w and
 // w gamma.  Writes rpos [m][2], rshear [m][2] (summed w gamma / summed w, so that w * shear is

@@ -1,5 +1,5 @@
 """Neighbour multipole records (ext4pcf_multipoles) against the tree oracle: exact records, and
-the tree approximation of Sect. 3.4 / App. F.3 (reduced catalogues on cells of side
+the tree approximation of Sect. 3.2 / App. F.3 (reduced catalogues on cells of side
 Delta_d = Delta_1 2^(d-1), each bin from the coarsest level with Theta_lo / Delta_d >= r_min)
 against oracle/tree.py:neighbour_multipoles with the same setting."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the tree-approximation oracle (Sect. 3.4, App. F.3); no GPU."""
+"""Pins of the tree-approximation oracle (Sect. 3.2, App. F.3); no GPU."""
 import numpy as np
 import pytest
 
@@ -96,7 +96,7 @@ def test_error_shrinks_as_r_min_grows():
 
 
 def test_approximation_error_at_the_papers_setting():
-    """Error of the tree approximation against the exact multipoles (Sect. 3.4): a seeded
+    """Error of the tree approximation against the exact multipoles (Sect. 3.2): a seeded
     4000-galaxy GRF on 60' x 60', 8 log bins 1'-30', n_max = 5, grids of 0.125', 0.25', 0.5'.
     Bins kept exact stay exact; at the paper's r_min = 40 every approximated bin holds the
     largest error of G_n to 7%, of Upsilon_0 on diagonal triples to 5% and of N_n to 3e-4
