@@ -116,7 +116,7 @@ static void cell_list_free(cell_list* cl) {
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Per-centre multipoles (step A of App. A.3).  For centre i and radial bin b:            */
+/* Per-centre multipoles (step A of App. A.2).  For centre i and radial bin b:            */
 /*   G_n   = sum_j x_j e^{i n phi_ij},   x_j = w_j gamma_c,j       n in [-2N-3, 2N-1]      */
 /*   W_n   = sum_j w_j e^{i n phi_ij}                              n in [-2N,   2N  ]      */
 /* and the quantities that Table tab:4PCFMCCorr multiplies with g:                        */

@@ -67,7 +67,7 @@ def test_one_galaxy_per_cell_is_exact():
 
 
 def test_level_choice_of_the_paper_setting():
-    """Resolutions {0.5', 1', 2'} and r_min = 40 (Sect. 6.1): a bin uses the coarsest grid
+    """Resolutions {0.5', 1', 2'} and r_min = 40 (Sect. 6.2): a bin uses the coarsest grid
     with Theta_low / Delta >= 40, else the galaxies themselves."""
     lows = np.array([10.0, 19.9, 20.0, 39.9, 45.0, 79.9, 80.0, 166.0])
     edges = np.append(lows, 170.0)
