@@ -68,3 +68,29 @@ def test_committed_traffic_lines_match_the_current_sources():
     """Every traffic line under profiles/ for the default forms refers to the current source."""
     for kernel in ("gather_kernel", "contract_h16_kernel"):
         assert bench.measured_traffic(kernel) is not None, kernel
+
+
+def test_clock_summary_reads_median_clock_and_throttle_reasons(tmp_path):
+    """The clocks record of the bench line: median SM clock under load, the largest maximum
+    clock seen, and every throttle reason that was active in any sample."""
+    rows = ["0, 2070, 2070, 610.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1020.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active"]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(path)
+    s = cs.summary(2070.0)
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] == 4 and s["power_w_max"] == 1390.0
+    # a thermal slowdown in one sample is reported (such a run is re-measured)
+    path.write_text(rows[0] + "\n" + rows[0].replace("Not Active, Not Active, Not Active, Not Active",
+                                                     "Not Active, Active, Not Active, Not Active") + "\n")
+    cs.path = str(path)
+    assert bench.ClockSampler.summary(cs, 2070.0)["reasons"] == ["hw_thermal_slowdown"]
+    # no samples at all (nvidia-smi missing): the line says so instead of reporting a clock
+    cs.path = str(tmp_path / "absent.csv")
+    s = cs.summary(2070.0)
+    assert s["sm_mhz"] is None and s["reasons"] == ["unsampled"]
