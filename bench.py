@@ -620,6 +620,7 @@ def run_ours(args):
                            **({"centres": args.centres} if args.centres is not None else {}),
                            "parallelism": "one catalogue per GPU" if world > 1 else "1 GPU"},
                 "contraction_tflops": contraction_tflops,
+                "pairs_per_s_gather": pairs / (bd["ms_gather"] / 1e3) if bd["ms_gather"] > 0 else None,
                 "breakdown_ms": {k: bd[k] for k in ("ms_grid", "ms_gather", "ms_contract", "ms_correct", "ms_total")},
                 "wall_s": t_wall,
                 "e2e": {"value": pairs / e2e, "unit": "pairs/s", "h2d_bytes_per_step": int(h2d),
