@@ -79,3 +79,33 @@ def test_aperture_lattice_stays_four_radii_inside():
                 np.testing.assert_allclose(np.diff(a), sp, rtol=1e-12)
         # no room for another lattice column or row
         assert (xs.max() - xs.min()) + sp > (field[2] - field[0]) - 8 * theta
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    """Every field of the binding's ctypes structs sits at the offset the C compiler gives the
+    header's struct (and the sizes agree): a field added, dropped or reordered on one side
+    fails here."""
+    import shutil
+    import subprocess
+    from paper_2509_07974_gb300 import ext4pcf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ext4pcf.h"', "int main(void) {"]
+    for cname, cls in (("ext4pcf_config", ext4pcf.Config), ("ext4pcf_stats", ext4pcf.Stats)):
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        *key, val = line.split()
+        got[tuple(key)] = int(val)
+    for cname, cls in (("ext4pcf_config", ext4pcf.Config), ("ext4pcf_stats", ext4pcf.Stats)):
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
