@@ -109,3 +109,30 @@ def test_struct_offsets_match_the_c_compiler(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_status_codes_and_precisions_match_the_header(tmp_path):
+    """The binding's status codes and precision names carry the header's enum values."""
+    import shutil
+    import subprocess
+    from paper_2509_07974_gb300 import ext4pcf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    codes = [n for n in dir(ext4pcf) if re.fullmatch(r"EXT4PCF_(OK|E_\w+)", n)]
+    prec = {"fp64": "EXT4PCF_FP64", "fp32": "EXT4PCF_FP32", "tf32": "EXT4PCF_TF32", "3xtf32": "EXT4PCF_3XTF32",
+            "bf16x3": "EXT4PCF_SPLIT_BF16", "f16x3": "EXT4PCF_SPLIT_F16"}
+    assert sorted(prec) == sorted(ext4pcf.PRECISION)
+    body = ['  printf("%s %%d\\n", (int)%s);' % (n, n) for n in codes + sorted(prec.values())]
+    src = tmp_path / "codes.c"
+    src.write_text('#include <stdio.h>\n#include "ext4pcf.h"\nint main(void) {\n' + "\n".join(body)
+                   + "\n  return 0;\n}\n")
+    exe = tmp_path / "codes"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict((k, int(v)) for k, v in (line.split() for line in subprocess.run(
+        [str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()))
+    assert {"EXT4PCF_OK", "EXT4PCF_E_INVALID_ARG", "EXT4PCF_E_TIMEOUT"} <= set(codes)
+    for n in codes:
+        assert got[n] == getattr(ext4pcf, n), n
+    for name, cname in prec.items():
+        assert got[cname] == ext4pcf.PRECISION[name], name
