@@ -136,3 +136,38 @@ def test_status_codes_and_precisions_match_the_header(tmp_path):
         assert got[n] == getattr(ext4pcf, n), n
     for name, cname in prec.items():
         assert got[cname] == ext4pcf.PRECISION[name], name
+
+
+def _prototypes():
+    """{name: (return type, [argument declarations])} of every EXT4PCF_API function."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", " ", open(h).read(), flags=re.S)
+        for m in re.finditer(r"EXT4PCF_API\s+([\w\s\*]*?)\b(ext4pcf_\w+)\s*\(([^;]*?)\)\s*;", src):
+            args = [a.strip() for a in m.group(3).split(",") if a.strip() and a.strip() != "void"]
+            out[m.group(2)] = (" ".join(m.group(1).split()), args)
+    return out
+
+
+def test_binding_argtypes_follow_the_prototypes(lib):
+    """Every argument the binding declares has the width the C prototype gives it (int,
+    int64_t, double, or a pointer), in the same number and order, and the return types agree:
+    a scalar of the wrong width would pass garbage in the upper bits."""
+    from paper_2509_07974_gb300 import ext4pcf
+    bound = ext4pcf.load()
+    protos = _prototypes()
+    assert set(protos) == set(declared_symbols())
+    scalar = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+    for name, (ret, args) in protos.items():
+        fn = getattr(bound, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == len(args), name
+        for decl, t in zip(args, fn.argtypes):
+            if "*" in decl:
+                assert t is ctypes.c_void_p or issubclass(t, ctypes._Pointer), (name, decl, t)
+            else:
+                base = decl.replace("const", "").split()[0]
+                assert t is scalar[base], (name, decl, t)
+        if ret == "int":
+            assert fn.restype is ctypes.c_int, name
+        else:
+            assert "char" in ret and "*" in ret and fn.restype is ctypes.c_char_p, name
