@@ -94,3 +94,21 @@ def test_clock_summary_reads_median_clock_and_throttle_reasons(tmp_path):
     cs.path = str(tmp_path / "absent.csv")
     s = cs.summary(2070.0)
     assert s["sm_mhz"] is None and s["reasons"] == ["unsampled"]
+
+
+def test_pairs_of_mask_counts_the_binned_pairs_of_the_sampled_centres():
+    """The pair count behind the oracle's rate: (centre, neighbour) pairs with
+    Theta_0 <= separation < Theta_nb, centres the masked galaxies, every galaxy a neighbour,
+    against a brute-force count."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0, 20, (700, 2))
+    pos[5] = pos[4] + (0.5, 0.0)                 # a pair exactly on the inner edge (counted)
+    pos[7] = pos[6] + (0.0, 6.0)                 # a pair exactly on the outer edge (not counted)
+    edges = np.array([0.5, 1.0, 2.5, 6.0])
+    mask = np.zeros(len(pos), np.uint8)
+    mask[rng.choice(len(pos), 90, replace=False)] = 1
+    mask[[4, 6]] = 1
+    d = np.sqrt(((pos[mask.astype(bool)][:, None, :] - pos[None, :, :]) ** 2).sum(-1))
+    want = int(((d >= edges[0]) & (d < edges[-1])).sum())
+    assert bench.pairs_of_mask(pos, edges, mask) == want
