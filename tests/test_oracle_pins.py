@@ -344,3 +344,43 @@ def test_xi_plus_of_constant_shear(oracle):
     xi = oracle.xi_from_acc(acc)
     assert np.allclose(xi[:, 0], abs(g) ** 2, rtol=1e-12)
     assert np.allclose(xi[:, 1], 0, atol=1e-16)
+
+
+def test_xi_pm_against_tangential_and_cross_pair_sums(oracle):
+    """xi_+/- from the estimator's accumulators equal their definition as weighted pair means:
+    xi_+ = <gamma_t gamma_t + gamma_x gamma_x>, xi_- = <gamma_t gamma_t - gamma_x gamma_x>
+    (plus the imaginary parts <gamma_x gamma_t - gamma_t gamma_x> and
+    <gamma_x gamma_t + gamma_t gamma_x> up to sign), each galaxy's shear projected on the
+    direction of the pair (Eq. gammatx_def), over ordered pairs i != j in the bin.  A sign of
+    the phase, a conjugation or a bin index off by one fails it."""
+    rng = np.random.default_rng(31)
+    n = 120
+    pos = rng.uniform(0, 8, (n, 2))
+    sh = rng.normal(0, 0.3, (n, 2))
+    w = rng.uniform(0.5, 1.5, n)
+    _, acc = oracle.measure(pos, sh, w, EDGES, 4, with_xi=True)
+    xi = oracle.xi_from_acc(acc)
+    g = sh[:, 0] + 1j * sh[:, 1]
+    nb = len(EDGES) - 1
+    num_p = np.zeros(nb); num_m = np.zeros(nb); den = np.zeros(nb)
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            d = pos[j] - pos[i]
+            r2 = d @ d
+            b = np.searchsorted(EDGES ** 2, r2, side="right") - 1
+            if b < 0 or b >= nb:
+                continue
+            phi = np.arctan2(d[1], d[0])
+            ti, xi_i = (-(g[i] * np.exp(-2j * phi))).real, (-(g[i] * np.exp(-2j * phi))).imag
+            tj, xj = (-(g[j] * np.exp(-2j * phi))).real, (-(g[j] * np.exp(-2j * phi))).imag
+            num_p[b] += w[i] * w[j] * (ti * tj + xi_i * xj)
+            num_m[b] += w[i] * w[j] * (ti * tj - xi_i * xj)
+            den[b] += w[i] * w[j]
+    ok = den > 0
+    assert ok.sum() >= nb - 1
+    assert np.allclose(xi[ok, 0], num_p[ok] / den[ok], rtol=1e-10, atol=1e-14)
+    assert np.allclose(xi[ok, 2], num_m[ok] / den[ok], rtol=1e-10, atol=1e-14)
+    # the imaginary part of xi_+ vanishes over ordered pairs (i, j) and (j, i)
+    assert np.allclose(xi[ok, 1], 0.0, atol=1e-14)
