@@ -55,3 +55,21 @@ def test_lognormal_convergence_is_skewed_zero_mean_and_scaled():
     assert kap.min() > -3 * kap.std()  # bounded below (long tail upwards)
     g1, g2 = synth.kaiser_squires_shear(kap, 200.0)
     assert np.isfinite(g1).all() and np.isfinite(g2).all()
+
+
+def test_kaiser_squires_single_modes():
+    """Flat-sky Kaiser-Squires on single Fourier modes of the convergence: a mode along x
+    gives gamma_1 = kappa, gamma_2 = 0; along y gamma_1 = -kappa; along the diagonal
+    gamma_1 = 0, gamma_2 = kappa (gamma = (k1^2 - k2^2 + 2 i k1 k2) / k^2 kappa in Fourier
+    space); the mean of kappa carries no shear."""
+    grid, side = 64, 30.0
+    x = (np.arange(grid) * side / grid)[None, :]
+    y = (np.arange(grid) * side / grid)[:, None]
+    m = 3
+    for kap, want1, want2 in (
+            (np.cos(2 * np.pi * m * x / side) + 0 * y, 1.0, 0.0),
+            (np.cos(2 * np.pi * m * y / side) + 0 * x, -1.0, 0.0),
+            (np.cos(2 * np.pi * m * (x + y) / side), 0.0, 1.0)):
+        g1, g2 = synth.kaiser_squires_shear(kap + 0.25, side)
+        assert np.allclose(g1, want1 * kap, atol=2e-6)
+        assert np.allclose(g2, want2 * kap, atol=2e-6)
