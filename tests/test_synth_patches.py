@@ -73,3 +73,32 @@ def test_kaiser_squires_single_modes():
         g1, g2 = synth.kaiser_squires_shear(kap + 0.25, side)
         assert np.allclose(g1, want1 * kap, atol=2e-6)
         assert np.allclose(g2, want2 * kap, atol=2e-6)
+
+
+def test_grf_shear_field_power_law_pure_e_mode_and_scale():
+    """The GRF shear maps: pure E mode (inverse Kaiser-Squires gives no B-mode convergence),
+    pixel rms of the convergence sigma_kappa (|gamma_hat| = |kappa_hat| away from l = 0, so
+    <|gamma|^2> = sigma_kappa^2 by Parseval), and an azimuthally averaged power spectrum with
+    the requested slope."""
+    grid, side, slope, sk = 256, 100.0, -1.2, 0.02
+    g1, g2 = synth.grf_shear_field(grid, side, 4, slope=slope, sigma_kappa=sk)
+    gam = g1.astype(np.float64) + 1j * g2.astype(np.float64)
+    assert abs(np.mean(np.abs(gam) ** 2) - sk * sk) < 1e-6 * sk * sk + 1e-12
+    k = np.fft.fftfreq(grid, d=side / grid)
+    k1, k2 = np.meshgrid(k, k, indexing="xy")
+    ksq = k1 * k1 + k2 * k2
+    nz = ksq > 0
+    D = np.zeros(ksq.shape, dtype=np.complex128)
+    D[nz] = ((k1[nz] ** 2 - k2[nz] ** 2) + 2j * k1[nz] * k2[nz]) / ksq[nz]
+    kap = np.fft.ifft2(np.fft.fft2(gam) * np.conj(D))
+    assert np.abs(kap.imag).max() < 1e-5 * np.abs(kap.real).max()
+    p = np.abs(np.fft.fft2(kap.real)) ** 2
+    kk = np.sqrt(ksq)
+    bands = np.geomspace(4 / side, 0.3 * grid / side, 9)
+    lk, lp = [], []
+    for lo, hi in zip(bands[:-1], bands[1:]):
+        sel = (kk >= lo) & (kk < hi)
+        lk.append(np.log(np.sqrt(lo * hi)))
+        lp.append(np.log(p[sel].mean()))
+    fit = np.polyfit(lk, lp, 1)[0]
+    assert abs(fit - slope) < 0.15, fit
