@@ -138,7 +138,12 @@ EXT4PCF_API int ext4pcf_synchronize(ext4pcf_ctx* ctx);
  *   radial_bins host, double [n_bins+1], strictly increasing, radial_bins[0] > 0
  *   n_bins      1..32 (1..16 for the tensor-core precisions TF32, 3XTF32, SPLIT_BF16 and SPLIT_F16, whose
  *               B tile holds at most 64 columns, 4 per bin; larger n_bins return
- *               EXT4PCF_E_UNSUPPORTED before any work);  n_max >= 0 (<= 40)
+ *               EXT4PCF_E_UNSUPPORTED before any work);  n_max >= 0 (<= 40).  A centre's
+ *               record, n_bins (14 n_max + 18) complex values, must also fit the gather's
+ *               shared memory: every n_max up to n_bins = 16; at n_bins = 20, 24, 28, 32,
+ *               n_max <= 37, 31, 26, 23 (FP32 gather, every precision but FP64) or
+ *               n_max <= 40, 37, 31, 27 (FP64).  Larger records return
+ *               EXT4PCF_E_UNSUPPORTED when the first wave is gathered.
  *   cat_offsets host, int64 [n_cat+1] or NULL: catalogue k is galaxies
  *               [cat_offsets[k], cat_offsets[k+1]); NULL means one catalogue (n_cat = 1)
  *   centre_mask device or host, uint8 [n_gal] or NULL: only galaxies with a non-zero entry
@@ -310,7 +315,8 @@ EXT4PCF_API int ext4pcf_nth_order_factors(int order, int mu, int* table, int cap
  *   components Gamma_0..3 in the order of ext4pcf_nth_order_components(3)), and the
  *   normalisation N_n = sum_{i, j != k} w_i w_j w_k e^{i n (phi_ij - phi_ik)}.
  *   positions, shears, weights  device, as for ext4pcf_measure (one catalogue)
- *   radial_bins  host [n_bins+1] as for ext4pcf_measure;  n_bins 1..32;  n_max 0..40
+ *   radial_bins  host [n_bins+1] as for ext4pcf_measure;  n_bins 1..32;  n_max 0..40, with the
+ *                record limit of ext4pcf_measure (larger records: EXT4PCF_E_UNSUPPORTED)
  *   upsilon3     device, double [5][2 n_max + 1][n_bins][n_bins][2] (index 4 the
  *                normalisation; axes n + n_max, Theta1, Theta2), accumulated into
  * Stream-ordered, returns after enqueueing (see the conventions above).  Waves hold

@@ -157,6 +157,17 @@ int cuda_fail(ext4pcf_ctx* ctx, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
   } while (0)
+// the gather's launch: a centre's record (n_bins (14 n_max + 18) complex values) that does not
+// fit its shared memory next to the pair buffers is refused by gather_wave with
+// cudaErrorInvalidConfiguration, reported as an unsupported size
+#define GK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ == cudaErrorInvalidConfiguration)                                                         \
+      return fail(ctx, EXT4PCF_E_UNSUPPORTED, "the multipole record (n_bins x n_max) does not fit "  \
+                                              "the gather's shared memory");                         \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);                                         \
+  } while (0)
 
 int ensure(ext4pcf_ctx* ctx, DBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -853,10 +864,10 @@ int measure_impl(ext4pcf_ctx* ctx, const double* positions, const double* shears
         Q.seg[q].cell_start = G.cells + G.coff[Q.seg[q].cat];
       }
       if (f64) {
-        CK(gather_wave<double>(G.cat, cat, G.bins, L, Q, pi > 0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+        GK(gather_wave<double>(G.cat, cat, G.bins, L, Q, pi > 0, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                                (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       } else {
-        CK(gather_wave<float>(G.cat, cat, G.bins, L, Q, pi > 0, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+        GK(gather_wave<float>(G.cat, cat, G.bins, L, Q, pi > 0, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
                               (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       }
     }
@@ -1155,12 +1166,12 @@ int ext4pcf_measure3(ext4pcf_ctx* ctx, const double* positions, const double* sh
     P.seg[0] = WaveSeg{(const int*)ctx->centres.p, nullptr, (const GridGeom*)ctx->geom.p, (const int*)ctx->cell_start.p,
                        w0, Tw, 0, 0, 0};
     if (f64) {
-      CK(gather_wave<double>(cat, cat, bins, L, P, false, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
+      GK(gather_wave<double>(cat, cat, bins, L, P, false, (double2*)ctx->rec.p, (double2*)ctx->xw.p,
                              (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       CK(contract3_wave(L, (const double2*)ctx->rec.p, (const double2*)ctx->xw.p, Tw, upsilon3,
                         (double2*)ctx->corr.p, s));
     } else {
-      CK(gather_wave<float>(cat, cat, bins, L, P, false, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
+      GK(gather_wave<float>(cat, cat, bins, L, P, false, (float2*)ctx->rec.p, (float2*)ctx->xw.p,
                             (unsigned long long*)ctx->counter.p, ctx->sm_count, s));
       CK(contract3_wave(L, (const float2*)ctx->rec.p, (const float2*)ctx->xw.p, Tw, upsilon3,
                         (double2*)ctx->corr.p, s));
